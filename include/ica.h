@@ -1,0 +1,170 @@
+/*
+ * ordering-ica GB300 library: C ABI.
+ *
+ * Batched kurtosis fixed-point iteration of the ordering ICA in matrix form (Matsuda &
+ * Yamaguchi, "Efficient Estimation of Unique Components in Independent Component Analysis
+ * by Matrix Representation", arXiv 2408.17118), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major. X and its derived data are N x T with the sample index T
+ *     contiguous; "ld" arguments are row strides in elements.
+ *   - Every array argument is a DEVICE pointer unless a comment says "host".
+ *   - The caller owns every buffer, including the workspace (ica_set_workspace). After the
+ *     workspace is set the library allocates no device memory (the optional plain FP32
+ *     comparator creates a cuBLAS handle on first use, which allocates inside cuBLAS).
+ *   - Work is enqueued on the context's stream (ica_set_stream). ica_order_fit synchronises
+ *     that stream after every iteration (it reads the active-restart count); ica_whiten,
+ *     ica_deflation_basis, ica_fp_step and ica_kurtosis synchronise once at the end to read
+ *     the device status word; ica_init_restarts and ica_reduce only enqueue.
+ *   - The return value is an ica_status. Nothing is thrown across the ABI. After an error the
+ *     outputs are unspecified and the context stays usable.
+ *   - The paper writes samples as M and restarts as L; this interface writes samples as T
+ *     and restarts as M.
+ */
+#ifndef ORDERING_ICA_H
+#define ORDERING_ICA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ica_ctx ica_ctx;
+
+typedef enum {
+    ICA_OK = 0,
+    ICA_ERR_ARG = 1,          /* argument outside the documented range */
+    ICA_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+    ICA_ERR_NONFINITE = 3,    /* a restart row became NaN/Inf or zero, or every restart died */
+    ICA_ERR_ILLCOND = 4,      /* covariance or F~F~^T (Section 3.3) is numerically singular */
+    ICA_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out (kernel returned early) */
+    ICA_ERR_WORKSPACE = 6,    /* no workspace set, or smaller than ica_workspace_bytes() */
+    ICA_ERR_UNSUPPORTED = 7   /* precision or feature not available (e.g. no cuBLAS) */
+} ica_status;
+
+typedef enum {
+    ICA_FP32 = 0,        /* fused FP32 CUDA-core iteration (Z never stored) */
+    ICA_BF16 = 1,        /* fused tcgen05 iteration, BF16 operands, FP32 accumulate and cube,
+                            followed by FP32 refinement of the top distinct candidates */
+    ICA_PLAIN_FP32 = 3   /* Algorithm 2 written literally: Z = B X~ materialised in device
+                            memory, cube, second product (cuBLAS SGEMM, no TF32). The
+                            comparison baseline, not the fast path. */
+} ica_precision;
+
+/* Options of ica_order_fit. Fill with ica_default_opts, then override fields. */
+typedef struct {
+    int precision;         /* ica_precision (default ICA_BF16) */
+    int gauss_test;        /* 1: stop when Upsilon(alpha_i) < 2(N-i+2)(N-i+1)/T (Eq. 3) */
+    int refine_topk;       /* BF16: distinct candidates refined in FP32 per component (>= 1) */
+    int refine_iters;      /* BF16: maximum FP32 refinement iterations */
+    double stage_tol;      /* BF16: convergence tolerance of the BF16 stage */
+    double refine_tol;     /* BF16: convergence tolerance of the FP32 refinement */
+    double fp32_tol_floor; /* FP32 stages never use a tolerance below this (FP32 rounding) */
+    const float* B0;       /* optional: n_components x M x N initial restarts (device, FP32);
+                              component i uses the first N-i entries of each row. NULL: draw
+                              them from Philox4x32-10 keyed by the seed (ica_init_restarts). */
+    int max_splits;        /* 0: automatic split of the sample range; >0 caps it (tests) */
+    int profile;           /* 1: time every fused launch with CUDA events on the context stream
+                              and report per-kind totals (launches, ms, algorithmic FLOPs) in
+                              ica_last_stats */
+} ica_opts;
+
+/* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 100,
+   stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
+   no profiling. */
+void ica_default_opts(ica_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* ica_status_string(int status);
+
+/* Create a context bound to CUDA device `device` (host pointer *out receives it). Allocates a
+   small pinned host buffer for device->host counters. ICA_ERR_CUDA if the device is absent. */
+int ica_create(ica_ctx** out, int device);
+
+/* Destroy a context created by ica_create (NULL is accepted). Does not free caller buffers. */
+int ica_destroy(ica_ctx* ctx);
+
+/* Enqueue all further work on `stream` (a cudaStream_t; NULL = legacy default stream). */
+int ica_set_stream(ica_ctx* ctx, void* stream);
+
+/* Bytes of device workspace ica_order_fit needs for these sizes and options (also enough for
+   every step entry point at the same or smaller sizes). Returns 0 for invalid sizes. */
+size_t ica_workspace_bytes(int N, int64_t T, int M, const ica_opts* opts);
+
+/* Hand the library a caller-allocated device workspace (256-byte aligned, `bytes` long). The
+   library keeps the pointer until the next call or ica_destroy; it never frees it. */
+int ica_set_workspace(ica_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Whitening ("X is whitened in advance", Section 2.2 and Theorem 1; symmetric form).
+   X: N x T FP32 (ld = T). Outputs: Xw N x T FP32 (ld = T; must not alias X), V N x N FP64 and
+   mean N FP64 with Xw = V (X - mean), V = C^(-1/2), C = (X - mean)(X - mean)^T / T. Means,
+   covariance and the Jacobi eigendecomposition run in FP64 on the GPU.
+   1 <= N <= 256, T >= 2N. ICA_ERR_ILLCOND if C has an eigenvalue <= 1e-12 * its largest. */
+int ica_whiten(ica_ctx* ctx, const float* X, int N, int64_t T, float* Xw, double* V, double* mean);
+
+/* Fast ordering ICA (Algorithm 2 with Section 3.1-3.3) on whitened Xw (N x T FP32, ld = T).
+   For each component i = 1..n_components: reduction basis G (Eq. 6-7) and X~ = G Xw (Eq. 8);
+   M restarts iterated in matrix form, Z = B X~, B <- (Z o Z o Z) X~^T / T - 3B, rows
+   normalised, converged rows removed (min(||b-b_prev||, ||b+b_prev||) <= tol); kurtosis
+   (Eq. 2) of every restart; p = argmax Upsilon (Eq. 1); w_i = b_p G appended.
+   Outputs (device): W_out n_components x N FP64 (row i = component i, rows orthonormal, sign
+   canonical: largest-magnitude entry positive), kurt_out n_components FP64 (alpha_i);
+   n_found (HOST int) = components returned (< n_components only when gauss_test stops).
+   1 <= N <= 256, T >= 2N, 1 <= M <= 65536, 1 <= n_components <= N, iters >= 1, tol > 0.
+   Synchronises the context stream once per iteration. */
+int ica_order_fit(ica_ctx* ctx, const float* Xw, int N, int64_t T, int M, int n_components,
+                  int iters, double tol, uint64_t seed, const ica_opts* opts,
+                  double* W_out, double* kurt_out, int* n_found);
+
+/* Per-phase statistics of the last ica_order_fit as a JSON object written to the HOST buffer
+   `buf` (NUL-terminated, at most `cap` bytes). Synchronises the context stream. */
+int ica_last_stats(ica_ctx* ctx, char* buf, size_t cap);
+
+/* ---------------------------------------------------------------------------------------
+ * Step entry points: one hot-path step each, in the launch configuration ica_order_fit
+ * uses. They need a workspace of ica_workspace_bytes(N or n, T, M, opts) at least.
+ * --------------------------------------------------------------------------------------- */
+
+/* Initial restarts of component `component` (Algorithm 2: random L x (N-i+1) matrix, rows
+   normalised). Entry (l, 2j) / (l, 2j+1) come from one Philox4x32-10 call with counter
+   (j, l, component, 0) and key (seed & 0xffffffff, seed >> 32): u = (k + 0.5) / 2^52 with
+   k = (w_a >> 6) * 2^26 + (w_b >> 6) from words (0,1) and (2,3), Box-Muller in FP64, rows
+   normalised in FP64. Output B: M x ldb FP32; columns n..ldb-1 are set to zero. */
+int ica_init_restarts(ica_ctx* ctx, uint64_t seed, int component, int M, int n, float* B, int ldb);
+
+/* Reduction basis (Section 3.3, Eq. 6-7): W k x N FP64 with orthonormal rows (ld = N),
+   0 <= k < N. Output G: (N-k) x N FP64 (ld = N), G = (F~F~^T)^(-1/2) F~, F~ = first N-k rows
+   of I - W^T W. ICA_ERR_ILLCOND if F~F~^T has an eigenvalue <= 1e-10. */
+int ica_deflation_basis(ica_ctx* ctx, const double* W, int k, int N, double* G);
+
+/* Reduction of signals (Eq. 8): X~ = G Xw. G: n x N FP64 (ld = N); Xw: N x T FP32 (ld = T).
+   Outputs (either may be NULL): Xt32 n_pad x ldx32 FP32 and Xt16 n_pad x ldx16 BF16 (raw
+   uint16 bits), n_pad = n rounded up to 16, rows n..n_pad-1 zero. ldx32, ldx16 >= T and
+   multiples of 8. */
+int ica_reduce(ica_ctx* ctx, const double* G, int n, int N, const float* Xw, int64_t T,
+               float* Xt32, int64_t ldx32, uint16_t* Xt16, int64_t ldx16);
+
+/* One matrix-form update (Eq. 4-5 as written in Algorithm 2) for M rows without
+   normalisation: Bnew = (Z o Z o Z) X~^T / T - 3 B with Z = B X~.
+   precision ICA_FP32: Xt is FP32 n_pad x ldx; ICA_BF16: Xt is BF16 bits n_pad x ldx and B is
+   rounded to BF16 for the products (FP32 accumulate, FP32 cube, BF16 cube operand).
+   B, Bnew: M x n_pad FP32 (ld = n_pad, columns >= n ignored / written as the update of the
+   zero padding, i.e. zero). moments (optional, M x 4 FP32): sum z^2 / T, sum z^4 / T. */
+int ica_fp_step(ica_ctx* ctx, int precision, const float* B, int M, int n, const void* Xt,
+                int64_t T, int64_t ldx, float* Bnew, float* moments);
+
+/* Kurtosis and objective of M rows (Eq. 2 and Eq. 1; alpha normalised by the row's own
+   second moment, alpha + 2 formed without cancellation):
+   z = b X~, m2 = mean z^2, m4 = mean z^4, q = mean (z^2 - 1)^2,
+   alpha = (q - (m2 - 1)^2) / m2^2 - 2, Upsilon = alpha - 2 log(alpha/2 + 1) (+inf if
+   alpha <= -2). Precision and layouts as ica_fp_step. Outputs alpha, ups: M FP64. */
+int ica_kurtosis(ica_ctx* ctx, int precision, const float* B, int M, int n, const void* Xt,
+                 int64_t T, int64_t ldx, double* alpha, double* ups);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORDERING_ICA_H */

@@ -1,0 +1,77 @@
+"""ctypes declarations of the C ABI in include/ica.h (loads libica.so; no fallback)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libica.so")
+
+# ica_status codes (include/ica.h)
+ICA_OK = 0
+ICA_ERR_ARG = 1
+ICA_ERR_CUDA = 2
+ICA_ERR_NONFINITE = 3
+ICA_ERR_ILLCOND = 4
+ICA_ERR_TIMEOUT = 5
+ICA_ERR_WORKSPACE = 6
+ICA_ERR_UNSUPPORTED = 7
+
+# ica_precision
+ICA_FP32 = 0
+ICA_BF16 = 1
+ICA_PLAIN_FP32 = 3
+
+
+class ica_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("gauss_test", C.c_int),
+        ("refine_topk", C.c_int),
+        ("refine_iters", C.c_int),
+        ("stage_tol", C.c_double),
+        ("refine_tol", C.c_double),
+        ("fp32_tol_floor", C.c_double),
+        ("B0", C.c_void_p),
+        ("max_splits", C.c_int),
+        ("profile", C.c_int),
+    ]
+
+
+vp, i32, i64, u64, f64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
+
+# name -> (restype, argtypes); exactly the functions declared in include/ica.h
+SIGNATURES = {
+    "ica_default_opts": (None, [C.POINTER(ica_opts)]),
+    "ica_status_string": (C.c_char_p, [i32]),
+    "ica_create": (i32, [C.POINTER(vp), i32]),
+    "ica_destroy": (i32, [vp]),
+    "ica_set_stream": (i32, [vp, vp]),
+    "ica_workspace_bytes": (sz, [i32, i64, i32, C.POINTER(ica_opts)]),
+    "ica_set_workspace": (i32, [vp, vp, sz]),
+    "ica_whiten": (i32, [vp, vp, i32, i64, vp, vp, vp]),
+    "ica_order_fit": (i32, [vp, vp, i32, i64, i32, i32, i32, f64, u64, C.POINTER(ica_opts), vp, vp, C.POINTER(i32)]),
+    "ica_last_stats": (i32, [vp, C.c_char_p, sz]),
+    "ica_init_restarts": (i32, [vp, u64, i32, i32, i32, vp, i32]),
+    "ica_deflation_basis": (i32, [vp, vp, i32, i32, vp]),
+    "ica_reduce": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, vp, i64]),
+    "ica_fp_step": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
+    "ica_kurtosis": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
+}
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libica.so (raises if it has not been built: there is no other implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,748 @@
+// Host driver and C ABI of the ordering-ICA library. Implements Algorithm 2 (fast ordering ICA
+// in matrix form, with removal of converged rows and reduction of signals) on one GPU:
+// every arithmetic step runs in this library's kernels; the host only orders launches, picks
+// launch shapes and reads back the active-restart count once per iteration.
+#include <dlfcn.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ica.h"
+#include "internal.h"
+
+using namespace ica;
+
+// ------------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+typedef int (*PFN_cublasCreate_t)(void**);
+typedef int (*PFN_cublasDestroy_t)(void*);
+typedef int (*PFN_cublasSetStream_t)(void*, cudaStream_t);
+typedef int (*PFN_cublasSgemm_t)(void*, int, int, int, int, int, const float*, const float*, int, const float*, int,
+                                 const float*, float*, int);
+
+struct ica_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint8_t* ws = nullptr;
+    size_t ws_bytes = 0;
+    int* host_i = nullptr;     // pinned: [0] count, [1] status, [2..65] candidate ids
+    double* host_d = nullptr;  // pinned: component stats
+    PFN_encodeTiled_t encode = nullptr;
+    void* cublas_lib = nullptr;
+    void* cublas = nullptr;
+    PFN_cublasSgemm_t sgemm = nullptr;
+    PFN_cublasSetStream_t cublas_set_stream = nullptr;
+    PFN_cublasDestroy_t cublas_destroy = nullptr;
+    std::string stats;
+    // launch accounting and optional per-launch timing of the fused kernels
+    long long launches = 0;        // kernels launched by the last ica_order_fit
+    long long launches_total = 0;  // kernels launched by this context since ica_create
+    std::vector<cudaEvent_t> ev;
+    struct Rec {
+        int kind;
+        double flops;
+        int e0, e1;
+    };
+    std::vector<Rec> recs;
+    double kind_ms[4] = {0, 0, 0, 0}, kind_flops[4] = {0, 0, 0, 0};
+    long long kind_n[4] = {0, 0, 0, 0};
+};
+
+// kinds of timed fused launches
+enum { K_ITER = 0, K_KURT = 1, K_REFINE = 2, K_REFKURT = 3 };
+static const char* kKindName[4] = {"iteration", "kurtosis", "refine", "refine_kurtosis"};
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t _e = (call);                      \
+        if (_e != cudaSuccess) return ICA_ERR_CUDA;   \
+    } while (0)
+// a launch of one of this library's kernels (counted)
+#define KL(call)             \
+    do {                     \
+        CK(call);            \
+        ++c->launches;       \
+        ++c->launches_total; \
+    } while (0)
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    int n_pad_max = 0, M_pad = 0, part_rows_max = 0;
+    int64_t ldx = 0;
+    size_t status, counts, Xt32, Xt16, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots,
+        part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, total;
+};
+
+Layout make_layout(int N, int64_t T, int M, int precision) {
+    Layout L;
+    L.n_pad_max = round_up(N, 16);
+    L.M_pad = round_up(M, kTcRows);
+    L.ldx = round_up64(T, 8);
+    L.part_rows_max = kMaxCTAs * kTcRows;
+    if (L.part_rows_max < L.M_pad) L.part_rows_max = L.M_pad;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t nN = static_cast<size_t>(N) * N;
+    L.status = take(16 * sizeof(int));
+    L.counts = take(16 * sizeof(int));
+    L.Xt32 = take(sizeof(float) * L.n_pad_max * static_cast<size_t>(L.ldx));
+    L.Xt16 = take(precision == ICA_BF16 ? sizeof(uint16_t) * L.n_pad_max * static_cast<size_t>(L.ldx) : 0);
+    L.Z = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(M) * L.ldx : 0);
+    L.B32 = take(sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max);
+    L.Bact = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max : 0);
+    L.act0 = take(sizeof(int) * L.M_pad);
+    L.act1 = take(sizeof(int) * L.M_pad);
+    L.cand = take(sizeof(int) * 64);
+    L.flags = take(sizeof(int) * L.M_pad);
+    L.iters = take(sizeof(int) * L.M_pad);
+    L.traj = take(sizeof(float) * L.M_pad * kTrajLen * 2);
+    L.alpha = take(sizeof(double) * L.M_pad);
+    L.ups = take(sizeof(double) * L.M_pad);
+    L.excl = take(sizeof(int) * L.M_pad);
+    L.slots = take(sizeof(int) * 64);
+    L.part_acc = take(sizeof(float) * static_cast<size_t>(L.part_rows_max) * L.n_pad_max);
+    L.part_mom = take(sizeof(float) * static_cast<size_t>(L.part_rows_max) * 4);
+    L.G = take(sizeof(double) * nN);
+    L.jA = take(sizeof(double) * nN);
+    L.jV = take(sizeof(double) * nN);
+    L.lam = take(sizeof(double) * N);
+    L.t1 = take(sizeof(double) * nN);
+    L.t2 = take(sizeof(double) * nN);
+    L.t3 = take(sizeof(double) * nN);
+    L.t4 = take(sizeof(double) * nN);
+    L.cov_part = take(sizeof(double) * nN * covariance_splits(N, T));
+    L.comp_stats = take(sizeof(double) * 4 * (N + 1));
+    L.total = off;
+    return L;
+}
+
+template <typename P>
+inline P* at(ica_ctx* c, size_t off) {
+    return reinterpret_cast<P*>(c->ws + off);
+}
+
+int map_device_status(int st) {
+    if (st & DEV_TIMEOUT) return ICA_ERR_TIMEOUT;
+    if (st & DEV_ILLCOND) return ICA_ERR_ILLCOND;
+    if (st & DEV_NONFINITE) return ICA_ERR_NONFINITE;
+    if (st & DEV_ALLDEAD) return ICA_ERR_NONFINITE;
+    return ICA_OK;
+}
+
+// Split of the sample range: about two waves of CTAs over the SMs, capped by kMaxCTAs.
+void choose_splits(int64_t total_chunks, int tiles, int waves_ctas, int max_splits, int* splits, int* cps) {
+    int s = (waves_ctas + tiles - 1) / tiles;
+    const int cap = kMaxCTAs / tiles > 0 ? kMaxCTAs / tiles : 1;
+    if (s > cap) s = cap;
+    if (max_splits > 0 && s > max_splits) s = max_splits;
+    if (s < 1) s = 1;
+    if (s > total_chunks) s = static_cast<int>(total_chunks);
+    const int64_t c = (total_chunks + s - 1) / s;
+    *cps = static_cast<int>(c);
+    *splits = static_cast<int>((total_chunks + c - 1) / c);
+}
+
+int encode_xmap(ica_ctx* c, CUtensorMap* map, const uint16_t* Xt16, int n_pad, int64_t T, int64_t ld) {
+    if (!c->encode) return ICA_ERR_UNSUPPORTED;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(T), static_cast<cuuint64_t>(n_pad)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+    cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(n_pad)};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = c->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(Xt16), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ICA_OK : ICA_ERR_CUDA;
+}
+
+int ensure_cublas(ica_ctx* c) {
+    if (c->cublas) return ICA_OK;
+    if (!c->cublas_lib) {
+        c->cublas_lib = dlopen("libcublas.so.13", RTLD_NOW | RTLD_LOCAL);
+        if (!c->cublas_lib) c->cublas_lib = dlopen("libcublas.so", RTLD_NOW | RTLD_LOCAL);
+        if (!c->cublas_lib) return ICA_ERR_UNSUPPORTED;
+    }
+    auto create = reinterpret_cast<PFN_cublasCreate_t>(dlsym(c->cublas_lib, "cublasCreate_v2"));
+    c->cublas_destroy = reinterpret_cast<PFN_cublasDestroy_t>(dlsym(c->cublas_lib, "cublasDestroy_v2"));
+    c->cublas_set_stream = reinterpret_cast<PFN_cublasSetStream_t>(dlsym(c->cublas_lib, "cublasSetStream_v2"));
+    c->sgemm = reinterpret_cast<PFN_cublasSgemm_t>(dlsym(c->cublas_lib, "cublasSgemm_v2"));
+    if (!create || !c->cublas_destroy || !c->cublas_set_stream || !c->sgemm) return ICA_ERR_UNSUPPORTED;
+    if (create(&c->cublas) != 0) {
+        c->cublas = nullptr;
+        return ICA_ERR_UNSUPPORTED;
+    }
+    return ICA_OK;
+}
+
+// One fused update of the active rows -> split partials. Returns the split count used.
+struct StepShape {
+    int splits = 1, cps = 1, part_rows = 0;
+};
+
+int run_fused(ica_ctx* c, const Layout& L, int precision, bool moments_only, const float* B32, int ldb,
+              const int* act, int M_act, int n_pad, int64_t T, const float* Xt32, const uint16_t* Xt16, int64_t ldx,
+              int max_splits, StepShape* shape) {
+    cudaStream_t s = c->stream;
+    float* pacc = at<float>(c, L.part_acc);
+    float* pmom = at<float>(c, L.part_mom);
+    int* status = at<int>(c, L.status);
+    if (precision == ICA_BF16) {
+        const int TC = tc_chunk(n_pad);
+        const int64_t total = (T + TC - 1) / TC;
+        const int tiles = (M_act + kTcRows - 1) / kTcRows;
+        choose_splits(total, tiles, 2 * 152, max_splits, &shape->splits, &shape->cps);
+        shape->part_rows = tiles * kTcRows;
+        CUtensorMap map;
+        int rc = encode_xmap(c, &map, Xt16, n_pad, T, ldx);
+        if (rc) return rc;
+        KL(launch_fused_tc(s, moments_only, map, B32, ldb, act, M_act, n_pad, T, shape->splits, shape->cps,
+                           static_cast<int>(total), pacc, pmom, shape->part_rows, status));
+        return ICA_OK;
+    }
+    if (precision == ICA_FP32) {
+        const int64_t total = (T + 63) / 64;
+        const int tiles = (M_act + kFp32Rows - 1) / kFp32Rows;
+        choose_splits(total, tiles, 4 * 152, max_splits, &shape->splits, &shape->cps);
+        shape->part_rows = tiles * kFp32Rows;
+        KL(launch_fused_fp32(s, moments_only, B32, ldb, act, M_act, Xt32, ldx, n_pad, T, shape->splits, shape->cps,
+                             pacc, pmom, shape->part_rows));
+        return ICA_OK;
+    }
+    // plain FP32 matrix form: Z = B X~ in device memory, cube, second product
+    int rc = ensure_cublas(c);
+    if (rc) return rc;
+    float* Bact = at<float>(c, L.Bact);
+    float* Z = at<float>(c, L.Z);
+    KL(launch_gather_rows(s, B32, ldb, act, M_act, n_pad, Bact));
+    if (c->cublas_set_stream(c->cublas, s) != 0) return ICA_ERR_CUDA;
+    const float one = 1.f, zero = 0.f;
+    if (c->sgemm(c->cublas, 0, 0, static_cast<int>(T), M_act, n_pad, &one, Xt32, static_cast<int>(ldx), Bact, n_pad,
+                 &zero, Z, static_cast<int>(ldx)) != 0)
+        return ICA_ERR_CUDA;
+    shape->splits = 1;
+    shape->cps = 1;
+    shape->part_rows = M_act;
+    if (moments_only) {
+        KL(launch_row_moments(s, Z, M_act, T, ldx, pmom));
+        return ICA_OK;
+    }
+    KL(launch_cube_inplace(s, Z, M_act, T, ldx));
+    if (c->sgemm(c->cublas, 1, 0, n_pad, M_act, static_cast<int>(T), &one, Xt32, static_cast<int>(ldx), Z,
+                 static_cast<int>(ldx), &zero, pacc, n_pad) != 0)
+        return ICA_ERR_CUDA;
+    return ICA_OK;
+}
+
+int check_ws(ica_ctx* c, const Layout& L) {
+    if (!c->ws || c->ws_bytes < L.total) return ICA_ERR_WORKSPACE;
+    return ICA_OK;
+}
+
+int read_status(ica_ctx* c, const Layout& L) {
+    CK(cudaMemcpyAsync(c->host_i + 1, at<int>(c, L.status), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return map_device_status(c->host_i[1]);
+}
+
+// Section 3.3: G = (F~F~^T)^(-1/2) F~ with F~ the first n = N - k rows of I - W^T W. With
+// U = W[:, :n], F~F~^T = I_n - U^T U; its eigenproblem is solved on the smaller of the two
+// Gram matrices:
+//   k <= n: U U^T = Q diag(mu) Q^T (k x k) and (I - U^T U)^(-1/2) = I + U^T H U with
+//           H = Q diag(f(mu)) Q^T, f(mu) = ((1 - mu)^(-1/2) - 1) / mu, so
+//           G = F~ + U^T H U F~ = E_n + U^T (H (U~ - U U^T W) - W), U~ = [U 0];
+//   k >  n: S = F~ F~^T = Q diag(l) Q^T (n x n, formed from the computed F~ so that G G^T = I
+//           holds to rounding), G = Q diag(l^(-1/2)) Q^T F~.
+int deflation_basis_impl(ica_ctx* c, const Layout& L, const double* W, int k, int N, double* G) {
+    cudaStream_t s = c->stream;
+    const int n = N - k;
+    double *A = at<double>(c, L.jA), *V = at<double>(c, L.jV), *lam = at<double>(c, L.lam);
+    double *T1 = at<double>(c, L.t1), *T2 = at<double>(c, L.t2), *T3 = at<double>(c, L.t3), *T4 = at<double>(c, L.t4);
+    int* status = at<int>(c, L.status);
+    if (k == 0) {
+        KL(launch_set_identity(s, G, N, N, N, 1.0));
+        return ICA_OK;
+    }
+    if (k <= n) {
+        KL(launch_gemm_f64(s, k, k, n, 1.0, W, N, 1, W, 1, N, 0.0, A, k));   // U U^T
+        KL(launch_gemm_f64(s, k, k, n, 1.0, W, N, 1, W, 1, N, 0.0, T4, k));  // kept copy
+        KL(launch_jacobi(s, A, V, lam, k, status, 60));
+        KL(launch_scale_cols_fn(s, V, lam, k, 1, T1, status, 1e-10));      // Q f(mu)
+        KL(launch_gemm_f64(s, k, k, k, 1.0, T1, k, 1, V, 1, k, 0.0, T2, k));  // H = Q f Q^T
+        KL(launch_pad_cols(s, W, k, N, n, T3));                              // U~ = [U 0]
+        KL(launch_gemm_f64(s, k, N, k, -1.0, T4, k, 1, W, N, 1, 1.0, T3, N));  // Y = U~ - (U U^T) W
+        KL(launch_gemm_f64(s, k, N, k, 1.0, T2, k, 1, T3, N, 1, 0.0, T1, N));  // H Y
+        KL(launch_axpby_f64(s, static_cast<int64_t>(k) * N, 1.0, T1, -1.0, W, T1));  // H Y - W
+        KL(launch_set_identity(s, G, n, N, N, 1.0));                         // E_n
+        KL(launch_gemm_f64(s, n, N, k, 1.0, W, 1, N, T1, N, 1, 1.0, G, N));  // + U^T (H Y - W)
+        return ICA_OK;
+    }
+    KL(launch_set_identity(s, T3, n, N, N, 1.0));
+    KL(launch_gemm_f64(s, n, N, k, -1.0, W, 1, N, W, N, 1, 1.0, T3, N));  // F~ = E_n - U^T W
+    KL(launch_gemm_f64(s, n, n, N, 1.0, T3, N, 1, T3, 1, N, 0.0, A, n));  // S = F~ F~^T (Gram form)
+    KL(launch_jacobi(s, A, V, lam, n, status, 60));
+    KL(launch_scale_cols_fn(s, V, lam, n, 0, T1, status, 1e-10));
+    KL(launch_gemm_f64(s, n, n, n, 1.0, T1, n, 1, V, 1, n, 0.0, T2, n));  // S^(-1/2)
+    KL(launch_gemm_f64(s, n, N, n, 1.0, T2, n, 1, T3, N, 1, 0.0, G, N));  // G = S^(-1/2) F~
+    return ICA_OK;
+}
+
+// Event pool for per-launch timing (profile option). Events are host-side driver objects.
+int ev_take(ica_ctx* c, size_t* cursor) {
+    if (*cursor >= c->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c->ev.push_back(e);
+    }
+    return static_cast<int>((*cursor)++);
+}
+
+// Accumulate the elapsed times of the recorded launches (after a stream synchronisation).
+void harvest(ica_ctx* c) {
+    for (const auto& r : c->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[r.e0], c->ev[r.e1]) == cudaSuccess) {
+            c->kind_ms[r.kind] += ms;
+            c->kind_flops[r.kind] += r.flops;
+            c->kind_n[r.kind] += 1;
+        }
+    }
+    c->recs.clear();
+}
+
+void json_kv(std::string& s, const char* k, double v, bool comma = true) {
+    char buf[96];
+    snprintf(buf, sizeof(buf), "\"%s\": %.10g%s", k, v, comma ? ", " : "");
+    s += buf;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+void ica_default_opts(ica_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = ICA_BF16;
+    o->gauss_test = 0;
+    o->refine_topk = 4;
+    o->refine_iters = 100;
+    o->stage_tol = 1e-4;
+    o->refine_tol = 1e-6;
+    o->fp32_tol_floor = 1e-6;
+    o->B0 = nullptr;
+    o->max_splits = 0;
+}
+
+const char* ica_status_string(int st) {
+    switch (st) {
+        case ICA_OK: return "ok";
+        case ICA_ERR_ARG: return "invalid argument";
+        case ICA_ERR_CUDA: return "CUDA error";
+        case ICA_ERR_NONFINITE: return "non-finite or vanishing restart update";
+        case ICA_ERR_ILLCOND: return "ill-conditioned matrix (singular covariance or F~F~^T)";
+        case ICA_ERR_TIMEOUT: return "bounded device wait timed out";
+        case ICA_ERR_WORKSPACE: return "workspace missing or too small";
+        case ICA_ERR_UNSUPPORTED: return "unsupported precision or feature";
+        default: return "unknown status";
+    }
+}
+
+int ica_create(ica_ctx** out, int device) {
+    if (!out) return ICA_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ICA_ERR_CUDA;
+    ica_ctx* c = new ica_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return ICA_ERR_CUDA;
+    }
+    if (cudaMallocHost(&c->host_i, 128 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->host_d, 1024 * sizeof(double)) != cudaSuccess) {
+        delete c;
+        return ICA_ERR_CUDA;
+    }
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        c->encode = reinterpret_cast<PFN_encodeTiled_t>(fn);
+    *out = c;
+    return ICA_OK;
+}
+
+int ica_destroy(ica_ctx* c) {
+    if (!c) return ICA_OK;
+    if (c->cublas && c->cublas_destroy) c->cublas_destroy(c->cublas);
+    if (c->cublas_lib) dlclose(c->cublas_lib);
+    if (c->host_i) cudaFreeHost(c->host_i);
+    if (c->host_d) cudaFreeHost(c->host_d);
+    delete c;
+    return ICA_OK;
+}
+
+int ica_set_stream(ica_ctx* c, void* stream) {
+    if (!c) return ICA_ERR_ARG;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return ICA_OK;
+}
+
+size_t ica_workspace_bytes(int N, int64_t T, int M, const ica_opts* opts) {
+    if (N < 1 || N > kMaxN || T < 1 || M < 1 || M > 65536) return 0;
+    ica_opts d;
+    ica_default_opts(&d);
+    const ica_opts* o = opts ? opts : &d;
+    return make_layout(N, T, M, o->precision).total;
+}
+
+int ica_set_workspace(ica_ctx* c, void* p, size_t bytes) {
+    if (!c) return ICA_ERR_ARG;
+    if (p && (reinterpret_cast<uintptr_t>(p) % kAlign) != 0) return ICA_ERR_ARG;
+    c->ws = static_cast<uint8_t*>(p);
+    c->ws_bytes = p ? bytes : 0;
+    return ICA_OK;
+}
+
+int ica_whiten(ica_ctx* c, const float* X, int N, int64_t T, float* Xw, double* V, double* mean) {
+    if (!c || !X || !Xw || !V || !mean || N < 1 || N > kMaxN || T < 2 * static_cast<int64_t>(N)) return ICA_ERR_ARG;
+    if (reinterpret_cast<const void*>(X) == reinterpret_cast<const void*>(Xw)) return ICA_ERR_ARG;
+    const Layout L = make_layout(N, T, 1, ICA_FP32);
+    int rc = check_ws(c, L);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    int* status = at<int>(c, L.status);
+    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    double *A = at<double>(c, L.jA), *E = at<double>(c, L.jV), *lam = at<double>(c, L.lam);
+    double *T1 = at<double>(c, L.t1), *bias = at<double>(c, L.t2);
+    const int splits = covariance_splits(N, T);
+    KL(launch_row_mean(s, X, N, T, T, mean));
+    KL(launch_covariance(s, X, mean, N, T, T, at<double>(c, L.cov_part), splits, A));
+    ++c->launches;  // partial + reduce
+    ++c->launches_total;
+    KL(launch_jacobi(s, A, E, lam, N, status, 60));
+    KL(launch_scale_cols_fn(s, E, lam, N, 0, T1, status, 1e-12));
+    KL(launch_gemm_f64(s, N, N, N, 1.0, T1, N, 1, E, 1, N, 0.0, V, N));     // V = E diag(l^-1/2) E^T
+    KL(launch_gemm_f64(s, N, 1, N, 1.0, V, N, 1, mean, 1, 1, 0.0, bias, 1));  // V mean
+    KL(launch_rows_gemm(s, V, N, N, N, X, T, T, bias, Xw, T, nullptr, 0));
+    return read_status(c, L);
+}
+
+int ica_init_restarts(ica_ctx* c, uint64_t seed, int component, int M, int n, float* B, int ldb) {
+    if (!c || !B || M < 1 || n < 1 || n > kMaxN || ldb < n || component < 0) return ICA_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    KL(launch_init_restarts(c->stream, seed, component, M, n, ldb, nullptr, 0, B));
+    return ICA_OK;
+}
+
+int ica_deflation_basis(ica_ctx* c, const double* W, int k, int N, double* G) {
+    if (!c || !G || N < 1 || N > kMaxN || k < 0 || k >= N || (k > 0 && !W)) return ICA_ERR_ARG;
+    const Layout L = make_layout(N, 8, 1, ICA_FP32);
+    int rc = check_ws(c, L);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(at<int>(c, L.status), 0, sizeof(int), c->stream));
+    rc = deflation_basis_impl(c, L, W, k, N, G);
+    if (rc) return rc;
+    return read_status(c, L);
+}
+
+int ica_reduce(ica_ctx* c, const double* G, int n, int N, const float* Xw, int64_t T, float* Xt32, int64_t ldx32,
+               uint16_t* Xt16, int64_t ldx16) {
+    if (!c || !G || !Xw || n < 1 || n > N || N > kMaxN || T < 1) return ICA_ERR_ARG;
+    if ((Xt32 && (ldx32 < T || ldx32 % 8)) || (Xt16 && (ldx16 < T || ldx16 % 8))) return ICA_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    KL(launch_rows_gemm(c->stream, G, n, round_up(n, 16), N, Xw, T, T, nullptr, Xt32, ldx32, Xt16, ldx16));
+    return ICA_OK;
+}
+
+int ica_fp_step(ica_ctx* c, int precision, const float* B, int M, int n, const void* Xt, int64_t T, int64_t ldx,
+                float* Bnew, float* moments) {
+    if (!c || !B || !Xt || !Bnew || M < 1 || M > 65536 || n < 1 || n > kMaxN || T < 1 || ldx < T || ldx % 8)
+        return ICA_ERR_ARG;
+    if (precision != ICA_FP32 && precision != ICA_BF16) return ICA_ERR_UNSUPPORTED;
+    const Layout L = make_layout(n, T, M, ICA_FP32);
+    int rc = check_ws(c, L);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    const int n_pad = round_up(n, 16);
+    CK(cudaMemsetAsync(at<int>(c, L.status), 0, sizeof(int), c->stream));
+    StepShape sh;
+    rc = run_fused(c, L, precision, false, B, n_pad, nullptr, M, n_pad, T, static_cast<const float*>(Xt),
+                   static_cast<const uint16_t*>(Xt), ldx, 0, &sh);
+    if (rc) return rc;
+    KL(launch_combine(c->stream, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows, n_pad,
+                      M, B, 1.0 / static_cast<double>(T), Bnew, moments));
+    return read_status(c, L);
+}
+
+int ica_kurtosis(ica_ctx* c, int precision, const float* B, int M, int n, const void* Xt, int64_t T, int64_t ldx,
+                 double* alpha, double* ups) {
+    if (!c || !B || !Xt || !alpha || !ups || M < 1 || M > 65536 || n < 1 || n > kMaxN || T < 1 || ldx < T ||
+        ldx % 8)
+        return ICA_ERR_ARG;
+    if (precision != ICA_FP32 && precision != ICA_BF16) return ICA_ERR_UNSUPPORTED;
+    const Layout L = make_layout(n, T, M, ICA_FP32);
+    int rc = check_ws(c, L);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    const int n_pad = round_up(n, 16);
+    CK(cudaMemsetAsync(at<int>(c, L.status), 0, sizeof(int), c->stream));
+    StepShape sh;
+    rc = run_fused(c, L, precision, true, B, n_pad, nullptr, M, n_pad, T, static_cast<const float*>(Xt),
+                   static_cast<const uint16_t*>(Xt), ldx, 0, &sh);
+    if (rc) return rc;
+    KL(launch_kurt_finalize(c->stream, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, M,
+                            1.0 / static_cast<double>(T), alpha, ups));
+    return read_status(c, L);
+}
+
+int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_components, int iters, double tol,
+                  uint64_t seed, const ica_opts* opts, double* W_out, double* kurt_out, int* n_found) {
+    if (!c || !Xw || !W_out || !kurt_out || !n_found) return ICA_ERR_ARG;
+    *n_found = 0;
+    if (N < 1 || N > kMaxN || T < 2 * static_cast<int64_t>(N) || M < 1 || M > 65536 || n_components < 1 ||
+        n_components > N || iters < 1 || !(tol > 0.0))
+        return ICA_ERR_ARG;
+    ica_opts d;
+    ica_default_opts(&d);
+    const ica_opts o = opts ? *opts : d;
+    if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_PLAIN_FP32) return ICA_ERR_UNSUPPORTED;
+    if (o.precision == ICA_BF16 && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
+    const Layout L = make_layout(N, T, M, o.precision);
+    int rc = check_ws(c, L);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    const bool bf16 = o.precision == ICA_BF16;
+    const int prec_iter = o.precision;
+    const double inv_T = 1.0 / static_cast<double>(T);
+    int* status = at<int>(c, L.status);
+    int* counts = at<int>(c, L.counts);
+    float* B32 = at<float>(c, L.B32);
+    float* Xt32 = at<float>(c, L.Xt32);
+    uint16_t* Xt16 = at<uint16_t>(c, L.Xt16);
+    int* act[2] = {at<int>(c, L.act0), at<int>(c, L.act1)};
+    int* flags = at<int>(c, L.flags);
+    int* itc = at<int>(c, L.iters);
+    float* traj = at<float>(c, L.traj);
+    double* alpha = at<double>(c, L.alpha);
+    double* ups = at<double>(c, L.ups);
+    int* excl = at<int>(c, L.excl);
+    int* cand = at<int>(c, L.cand);
+    int* slots = at<int>(c, L.slots);
+    double* G = at<double>(c, L.G);
+    double* cstats = at<double>(c, L.comp_stats);
+    const int64_t ldx = L.ldx;
+    const double tol_fp32 = tol > o.fp32_tol_floor ? tol : o.fp32_tol_floor;
+    const double tol_iter = bf16 ? (o.stage_tol > tol ? o.stage_tol : tol) : tol_fp32;
+    const double tol_ref = o.refine_tol > o.fp32_tol_floor ? o.refine_tol : o.fp32_tol_floor;
+
+    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    c->launches = 0;
+    for (int k = 0; k < 4; ++k) {
+        c->kind_ms[k] = 0.0;
+        c->kind_flops[k] = 0.0;
+        c->kind_n[k] = 0;
+    }
+    c->recs.clear();
+    size_t ev_cursor = 0;
+    // run one fused launch, bracketed by CUDA events on the context stream when profiling
+    auto timed = [&](int kind, double flops, auto&& fn) -> int {
+        if (!o.profile) return fn();
+        const int e0 = ev_take(c, &ev_cursor), e1 = ev_take(c, &ev_cursor);
+        if (e0 < 0 || e1 < 0) return ICA_ERR_CUDA;
+        CK(cudaEventRecord(c->ev[e0], s));
+        const int r = fn();
+        CK(cudaEventRecord(c->ev[e1], s));
+        c->recs.push_back({kind, flops, e0, e1});
+        return r;
+    };
+    cudaEvent_t fit_begin = nullptr, fit_end = nullptr;
+    CK(cudaEventCreate(&fit_begin));
+    CK(cudaEventCreate(&fit_end));
+    CK(cudaEventRecord(fit_begin, s));
+    const double dT = static_cast<double>(T);
+    std::string js = "{\"components\": [";
+    int found = 0;
+    for (int i = 0; i < n_components; ++i) {
+        const int n = N - i;
+        const int n_pad = round_up(n, 16);
+        // reduction basis and X~ = G Xw (Section 3.3)
+        rc = deflation_basis_impl(c, L, W_out, i, N, G);
+        if (rc) return rc;
+        KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx));
+        // initial restarts
+        KL(launch_init_restarts(s, seed, i, M, n, n_pad, o.B0 ? o.B0 + static_cast<int64_t>(i) * M * N : nullptr, N,
+                                B32));
+        CK(cudaMemsetAsync(itc, 0, sizeof(int) * M, s));
+        CK(cudaMemsetAsync(traj, 0, sizeof(float) * M * kTrajLen * 2, s));
+        KL(launch_iota(s, act[0], M));
+        int cur = 0, M_act = M, t = 0;
+        std::vector<int> active_hist;
+        // fixed-point iterations with removal of converged rows (Algorithm 2, Section 3.2)
+        while (t < iters && M_act > 0) {
+            StepShape sh;
+            rc = timed(K_ITER, 4.0 * n * M_act * dT, [&] {
+                return run_fused(c, L, prec_iter, false, B32, n_pad, act[cur], M_act, n_pad, T, Xt32, Xt16, ldx,
+                                 o.max_splits, &sh);
+            });
+            if (rc) return rc;
+            KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows, n_pad,
+                               n, act[cur], M_act, B32, n_pad, inv_T, tol_iter, flags, itc,
+                               o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status));
+            KL(launch_compact(s, flags, act[cur], M_act, act[cur ^ 1], counts, nullptr));
+            cur ^= 1;
+            CK(cudaMemcpyAsync(c->host_i, counts, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            rc = map_device_status(c->host_i[1]);
+            if (rc) return rc;
+            M_act = c->host_i[0];
+            active_hist.push_back(M_act);
+            ++t;
+        }
+        // kurtosis of every candidate: converged rows plus rows still running after `iters`
+        {
+            StepShape sh;
+            rc = timed(K_KURT, 2.0 * n * M * dT, [&] {
+                return run_fused(c, L, prec_iter, true, B32, n_pad, nullptr, M, n_pad, T, Xt32, Xt16, ldx,
+                                 o.max_splits, &sh);
+            });
+            if (rc) return rc;
+            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, M, inv_T, alpha,
+                                    ups));
+        }
+        int refine_iters_used = 0, n_cand = 1;
+        if (!bf16) {
+            KL(launch_argmax(s, ups, nullptr, nullptr, M, slots));
+        } else {
+            // distinct top-k candidates, FP32 refinement, FP32 kurtosis, argmax among them
+            const int k = o.refine_topk;
+            KL(launch_select_clear(s, excl, M, cand, k));
+            for (int j = 0; j < k; ++j) {
+                KL(launch_argmax(s, ups, excl, nullptr, M, cand + j));
+                KL(launch_exclude(s, B32, n_pad, n, M, cand + j, excl, 1.0 - 1e-3));
+            }
+            CK(cudaMemcpyAsync(c->host_i + 2, cand, sizeof(int) * k, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            std::vector<int> cl;
+            for (int j = 0; j < k; ++j)
+                if (c->host_i[2 + j] >= 0) cl.push_back(c->host_i[2 + j]);
+            if (cl.empty()) return ICA_ERR_NONFINITE;
+            n_cand = static_cast<int>(cl.size());
+            memcpy(c->host_i + 2, cl.data(), sizeof(int) * cl.size());
+            CK(cudaMemcpyAsync(act[0], c->host_i + 2, sizeof(int) * n_cand, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(cand, c->host_i + 2, sizeof(int) * n_cand, cudaMemcpyHostToDevice, s));
+            int R = n_cand, rcur = 0, rt = 0;
+            while (rt < o.refine_iters && R > 0) {
+                StepShape sh;
+                rc = timed(K_REFINE, 4.0 * n * R * dT, [&] {
+                    return run_fused(c, L, ICA_FP32, false, B32, n_pad, act[rcur], R, n_pad, T, Xt32, Xt16, ldx,
+                                     o.max_splits, &sh);
+                });
+                if (rc) return rc;
+                KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
+                                   n_pad, n, act[rcur], R, B32, n_pad, inv_T, tol_ref, flags, itc, nullptr, kTrajLen,
+                                   status));
+                KL(launch_compact(s, flags, act[rcur], R, act[rcur ^ 1], counts, nullptr));
+                rcur ^= 1;
+                CK(cudaMemcpyAsync(c->host_i, counts, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                rc = map_device_status(c->host_i[1]);
+                if (rc) return rc;
+                R = c->host_i[0];
+                ++rt;
+            }
+            refine_iters_used = rt;
+            StepShape sh;
+            rc = timed(K_REFKURT, 2.0 * n * n_cand * dT, [&] {
+                return run_fused(c, L, ICA_FP32, true, B32, n_pad, cand, n_cand, n_pad, T, Xt32, Xt16, ldx,
+                                 o.max_splits, &sh);
+            });
+            if (rc) return rc;
+            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, cand, n_cand, inv_T, alpha,
+                                    ups));
+            KL(launch_argmax(s, ups, nullptr, cand, n_cand, slots));
+        }
+        // w_i = b_p G appended to W (Algorithm 2)
+        KL(launch_append(s, G, n, N, B32, n_pad, slots, alpha, ups, W_out, i, kurt_out + i, cstats + 4 * i));
+        CK(cudaMemcpyAsync(c->host_d, cstats + 4 * i, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rc = map_device_status(c->host_i[1]);
+        if (rc) return rc;
+        harvest(c);
+        ev_cursor = 0;
+        const double p = c->host_d[0], a_p = c->host_d[1], u_p = c->host_d[2];
+        if (p < 0) return ICA_ERR_NONFINITE;
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s{\"i\": %d, \"iterations\": %d, \"winner\": %d, \"alpha\": %.12g, \"upsilon\": %.12g, "
+                 "\"refine_iterations\": %d, \"candidates\": %d, \"active\": [",
+                 i ? ", " : "", i + 1, t, static_cast<int>(p), a_p, u_p, refine_iters_used, n_cand);
+        js += buf;
+        for (size_t h = 0; h < active_hist.size(); ++h) {
+            snprintf(buf, sizeof(buf), "%s%d", h ? ", " : "", active_hist[h]);
+            js += buf;
+        }
+        js += "]}";
+        // Gaussianity test (Eq. 3): the remaining components are Gaussian
+        if (o.gauss_test && u_p < 2.0 * (N - (i + 1) + 2) * (N - (i + 1) + 1) / static_cast<double>(T)) break;
+        found = i + 1;
+    }
+    CK(cudaEventRecord(fit_end, s));
+    CK(cudaEventSynchronize(fit_end));
+    float fit_ms = 0.f;
+    CK(cudaEventElapsedTime(&fit_ms, fit_begin, fit_end));
+    cudaEventDestroy(fit_begin);
+    cudaEventDestroy(fit_end);
+    js += "], ";
+    json_kv(js, "fit_ms", fit_ms);
+    json_kv(js, "launches", static_cast<double>(c->launches));
+    json_kv(js, "launches_total", static_cast<double>(c->launches_total));
+    js += "\"fused\": {";
+    for (int k = 0; k < 4; ++k) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}", k ? ", " : "",
+                 kKindName[k], c->kind_n[k], c->kind_ms[k], c->kind_flops[k]);
+        js += buf;
+    }
+    js += "}, ";
+    json_kv(js, "n_found", found, false);
+    js += "}";
+    c->stats = js;
+    *n_found = found;
+    return ICA_OK;
+}
+
+int ica_last_stats(ica_ctx* c, char* buf, size_t cap) {
+    if (!c || !buf || cap == 0) return ICA_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    const size_t n = c->stats.size() < cap - 1 ? c->stats.size() : cap - 1;
+    memcpy(buf, c->stats.data(), n);
+    buf[n] = 0;
+    return ICA_OK;
+}
+
+}  // extern "C"

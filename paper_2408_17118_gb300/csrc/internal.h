@@ -1,0 +1,88 @@
+// Internal launch interface between the translation units of the ordering-ICA library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ica {
+
+constexpr int kMaxN = 256;            // channels (and reduced dimension) supported
+constexpr int kMaxCTAs = 4 * 152;     // cap on (split x restart-tile) CTAs of one fused launch
+constexpr int kTrajLen = 5;           // iterations of per-restart features kept (pruner input)
+constexpr int kFp32Rows = 64;         // restart rows per CTA, FP32 fused kernel
+constexpr int kTcRows = 128;          // restart rows per CTA, tcgen05 fused kernel
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// ---- k_small.cu ----
+cudaError_t launch_init_restarts(cudaStream_t s, uint64_t seed, int comp, int M, int n, int ldb,
+                                 const float* B0, int B0_ld, float* B);
+cudaError_t launch_iota(cudaStream_t s, int* idx, int count);
+cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
+                            int part_rows, int n_pad, int n, const int* act_idx, int M_act, float* B32, int ldb,
+                            double inv_T, double tol, int* flags, int* iters, float* traj, int t_iter,
+                            int* status);
+cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
+                           int part_rows, int n_pad, int M, const float* B, double inv_T, float* Bnew,
+                           float* moments);
+cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, int count, int* act_out,
+                           int* count_out_dev, int* count_out_host);
+cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int splits, int part_rows,
+                                 const int* act_idx, int count, double inv_T, double* alpha, double* ups);
+cudaError_t launch_select_clear(cudaStream_t s, int* excluded, int M, int* cand, int kmax);
+cudaError_t launch_argmax(cudaStream_t s, const double* ups, const int* excluded, const int* subset,
+                          int count, int* out_slot);
+cudaError_t launch_exclude(cudaStream_t s, const float* B32, int ldb, int n, int M, const int* sel_slot,
+                           int* excluded, double cos_thresh);
+cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
+                          const int* p_slot, const double* alpha, const double* ups, double* W, int i,
+                          double* kurt_out, double* comp_stats);
+
+// ---- k_linalg.cu ----
+cudaError_t launch_row_mean(cudaStream_t s, const float* X, int N, int64_t T, int64_t ld, double* mean);
+cudaError_t launch_covariance(cudaStream_t s, const float* X, const double* mean, int N, int64_t T,
+                              int64_t ld, double* part, int splits, double* C);
+int covariance_splits(int N, int64_t T);
+cudaError_t launch_jacobi(cudaStream_t s, double* A, double* V, double* lam, int m, int* status,
+                          int max_sweeps);
+cudaError_t launch_gemm_f64(cudaStream_t s, int rows, int cols, int inner, double alpha, const double* A,
+                            int64_t sar, int64_t sac, const double* B, int64_t sbr, int64_t sbc, double beta,
+                            double* C, int64_t ldc);
+cudaError_t launch_set_identity(cudaStream_t s, double* A, int rows, int cols, int64_t ld, double diag);
+cudaError_t launch_scale_cols_fn(cudaStream_t s, const double* Q, const double* lam, int m, int fn,
+                                 double* out, int* status, double ill_thresh);
+cudaError_t launch_axpby_f64(cudaStream_t s, int64_t n, double a, const double* x, double b,
+                             const double* y, double* out);
+cudaError_t launch_pad_cols(cudaStream_t s, const double* W, int k, int N, int ncols, double* out);
+
+// ---- k_reduce.cu ----
+cudaError_t launch_rows_gemm(cudaStream_t s, const double* G, int n, int n_pad, int N, const float* X,
+                             int64_t T, int64_t ldxin, const double* bias, float* out32, int64_t ld32,
+                             uint16_t* out16, int64_t ld16);
+
+// ---- k_fp32.cu ----
+size_t fp32_smem_bytes(int n_pad);
+cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B32, int ldb,
+                              const int* act_idx, int M_act, const float* Xt, int64_t ldx, int n_pad,
+                              int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
+                              int part_rows);
+
+// ---- k_tc.cu ----
+int tc_chunk(int n_pad);
+size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out);
+cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, const CUtensorMap& xmap, const float* B32,
+                            int ldb, const int* act_idx, int M_act, int n_pad, int64_t T, int splits,
+                            int chunks_per_split, int total_chunks, float* part_acc, float* part_mom,
+                            int part_rows, int* status);
+
+// ---- k_plain.cu ----
+cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx, int M_act,
+                               int n_pad, float* out);
+cudaError_t launch_cube_inplace(cudaStream_t s, float* Z, int rows, int64_t T, int64_t ldz);
+cudaError_t launch_row_moments(cudaStream_t s, const float* Z, int rows, int64_t T, int64_t ldz,
+                               float* part_mom);
+
+}  // namespace ica

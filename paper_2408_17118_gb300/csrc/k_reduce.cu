@@ -1,0 +1,112 @@
+// Reduction of signals (Section 3.3, Eq. 8): X~ = G X, and the whitening apply
+// Xw = V X - V mean. FP64 coefficients are rounded to FP32 on load; products accumulate in
+// FP32. Writes FP32 rows and/or their BF16 rounding (the tensor-core operand). Rows n..n_pad-1
+// of the outputs are written as zeros, so the padded reduced dimension contributes nothing to
+// the products of the fused iteration.
+#include "common.cuh"
+#include "internal.h"
+
+namespace ica {
+
+constexpr int RG_BM = 64, RG_BT = 128, RG_BK = 16;
+
+__global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict__ G, int n, int N,
+                                                        const float* __restrict__ X, int64_t T, int64_t ldxin,
+                                                        const double* __restrict__ bias, float* __restrict__ out32,
+                                                        int64_t ld32, uint16_t* __restrict__ out16, int64_t ld16,
+                                                        int n_pad) {
+    __shared__ __align__(16) float Gs[RG_BK][RG_BM];
+    __shared__ __align__(16) float Xs[RG_BK][RG_BT];
+    const int rb = blockIdx.x, tb = blockIdx.y;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t t0 = static_cast<int64_t>(tb) * RG_BT;
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const bool vec_ok = (ldxin % 4 == 0);
+    for (int k0 = 0; k0 < N; k0 += RG_BK) {
+        for (int e = threadIdx.x; e < RG_BK * RG_BM; e += 256) {
+            const int kk = e / RG_BM, rr = e % RG_BM;
+            const int r = rb * RG_BM + rr, k = k0 + kk;
+            Gs[kk][rr] = (r < n && k < N) ? static_cast<float>(G[static_cast<int64_t>(r) * N + k]) : 0.f;
+        }
+        for (int e = threadIdx.x; e < RG_BK * (RG_BT / 4); e += 256) {
+            const int kk = e / (RG_BT / 4), c4 = (e % (RG_BT / 4)) * 4;
+            const int k = k0 + kk;
+            const int64_t t = t0 + c4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < N) {
+                const float* src = X + static_cast<int64_t>(k) * ldxin + t;
+                if (vec_ok && t + 3 < T) {
+                    v = *reinterpret_cast<const float4*>(src);
+                } else {
+                    if (t < T) v.x = src[0];
+                    if (t + 1 < T) v.y = src[1];
+                    if (t + 2 < T) v.z = src[2];
+                    if (t + 3 < T) v.w = src[3];
+                }
+            }
+            *reinterpret_cast<float4*>(&Xs[kk][c4]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < RG_BK; ++kk) {
+            const float4 g = *reinterpret_cast<const float4*>(&Gs[kk][ty * 4]);
+            const float4 xa = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8]);
+            const float4 xb = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8 + 4]);
+            const float gv[4] = {g.x, g.y, g.z, g.w};
+            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(gv[i], xv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = rb * RG_BM + ty * 4 + i;
+        if (r >= n_pad) continue;
+        const float b = (bias && r < n) ? static_cast<float>(bias[r]) : 0.f;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = r < n ? acc[i][j] - b : 0.f;
+        const int64_t t = t0 + tx * 8;
+        if (out32) {
+            float* dst = out32 + static_cast<int64_t>(r) * ld32 + t;
+            if (t + 7 < T && (ld32 % 4 == 0)) {
+                *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<float4*>(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
+                for (int j = 0; j < 8; ++j)
+                    if (t + j < T) dst[j] = v[j];
+            }
+        }
+        if (out16) {
+            uint16_t* dst = out16 + static_cast<int64_t>(r) * ld16 + t;
+            if (t + 7 < T && (ld16 % 8 == 0)) {
+                uint4 pk;
+                pk.x = pack_bf16x2(v[0], v[1]);
+                pk.y = pack_bf16x2(v[2], v[3]);
+                pk.z = pack_bf16x2(v[4], v[5]);
+                pk.w = pack_bf16x2(v[6], v[7]);
+                *reinterpret_cast<uint4*>(dst) = pk;
+            } else {
+                for (int j = 0; j < 8; ++j)
+                    if (t + j < T) dst[j] = static_cast<uint16_t>(pack_bf16x2(v[j], 0.f) & 0xffffu);
+            }
+        }
+    }
+}
+
+cudaError_t launch_rows_gemm(cudaStream_t s, const double* G, int n, int n_pad, int N, const float* X, int64_t T,
+                             int64_t ldxin, const double* bias, float* out32, int64_t ld32, uint16_t* out16,
+                             int64_t ld16) {
+    dim3 grid((n_pad + RG_BM - 1) / RG_BM, static_cast<unsigned>((T + RG_BT - 1) / RG_BT));
+    rows_gemm_kernel<<<grid, 256, 0, s>>>(G, n, N, X, T, ldxin, bias, out32, ld32, out16, ld16, n_pad);
+    return cudaGetLastError();
+}
+
+}  // namespace ica

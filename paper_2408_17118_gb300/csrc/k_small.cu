@@ -1,0 +1,500 @@
+// Per-restart kernels of the fast ordering ICA (Algorithm 2): initial restarts, the
+// normalise / converge / remove step (Section 3.2), stream compaction of the active rows,
+// kurtosis and Upsilon of candidates (Eq. 1-2), candidate selection, and the append
+// w_i = b_p G of the winner.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ica {
+
+// ------------------------------------------------------------------------------------------
+// Initial restarts (Algorithm 2: "Initialize B as an L x (N-i+1) random matrix", then every
+// row normalised). One warp per restart row; lane j handles column pairs (2j, 2j+1) for
+// j = lane + 32q. Values come from Philox4x32-10 + Box-Muller in FP64, or from a caller B0.
+// ------------------------------------------------------------------------------------------
+__global__ void init_restarts_kernel(uint64_t seed, int comp, int M, int n, int ldb, const float* __restrict__ B0,
+                                     int B0_ld, float* __restrict__ B) {
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (l >= M) return;
+    double v[8];
+    double ss = 0.0;
+    const uint2 key = make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = lane + 32 * q;
+        double z0 = 0.0, z1 = 0.0;
+        if (2 * j < n) {
+            if (B0) {
+                z0 = B0[static_cast<int64_t>(l) * B0_ld + 2 * j];
+                if (2 * j + 1 < n) z1 = B0[static_cast<int64_t>(l) * B0_ld + 2 * j + 1];
+            } else {
+                const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(j), static_cast<uint32_t>(l),
+                                                         static_cast<uint32_t>(comp), 0u),
+                                              key);
+                const double u1 = uniform52(r.x, r.y);
+                const double u2 = uniform52(r.z, r.w);
+                const double rad = sqrt(-2.0 * log(u1));
+                const double th = 6.283185307179586 * u2;
+                z0 = rad * cos(th);
+                if (2 * j + 1 < n) z1 = rad * sin(th);
+            }
+        }
+        v[2 * q] = z0;
+        v[2 * q + 1] = z1;
+        ss += z0 * z0 + z1 * z1;
+    }
+    ss = warp_sum(ss);
+    const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = 2 * (lane + 32 * q);
+        if (c < ldb) B[static_cast<int64_t>(l) * ldb + c] = static_cast<float>(v[2 * q] * inv);
+        if (c + 1 < ldb) B[static_cast<int64_t>(l) * ldb + c + 1] = static_cast<float>(v[2 * q + 1] * inv);
+    }
+}
+
+cudaError_t launch_init_restarts(cudaStream_t s, uint64_t seed, int comp, int M, int n, int ldb, const float* B0,
+                                 int B0_ld, float* B) {
+    const int threads = 256;
+    const int blocks = (M * 32 + threads - 1) / threads;
+    init_restarts_kernel<<<blocks, threads, 0, s>>>(seed, comp, M, n, ldb, B0, B0_ld, B);
+    return cudaGetLastError();
+}
+
+__global__ void iota_kernel(int* idx, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) idx[i] = i;
+}
+cudaError_t launch_iota(cudaStream_t s, int* idx, int count) {
+    iota_kernel<<<(count + 255) / 256, 256, 0, s>>>(idx, count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Normalise / converge / remove (Algorithm 2 inner loop; Section 3.2). One warp per active
+// row j (restart r = act_idx[j]): the split-T partial sums of (Z o Z o Z) X~^T are added in a
+// fixed order (deterministic), b' = acc / T - 3 b, b' <- b' / ||b'||,
+// d = min(||b' - b||, ||b' + b||); the row stays active iff d > tol. Rows whose update is
+// zero or non-finite are retired and flagged in the status word. The kurtosis of the
+// pre-update row and d are kept for the first kTrajLen iterations (restart features).
+// ------------------------------------------------------------------------------------------
+__global__ void finalize_kernel(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
+                                int splits, int part_rows, int n_pad, int n, const int* __restrict__ act_idx,
+                                int M_act, float* __restrict__ B32, int ldb, double inv_T, double tol,
+                                int* __restrict__ flags, int* __restrict__ iters, float* __restrict__ traj,
+                                int t_iter, int* status) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= M_act) return;
+    const int r = act_idx ? act_idx[j] : j;
+    double u[8], b[8];
+    double ss = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        u[q] = 0.0;
+        b[q] = 0.0;
+        if (k < n) {
+            double acc = 0.0;
+            for (int sp = 0; sp < splits; ++sp)
+                acc += static_cast<double>(part_acc[(static_cast<int64_t>(sp) * part_rows + j) * n_pad + k]);
+            b[q] = static_cast<double>(B32[static_cast<int64_t>(r) * ldb + k]);
+            u[q] = acc * inv_T - 3.0 * b[q];
+            ss += u[q] * u[q];
+        }
+    }
+    ss = warp_sum(ss);
+    const bool bad = !(ss > 0.0) || !isfinite(ss);
+    double dm = 0.0, dp = 0.0;
+    const double inv = bad ? 0.0 : 1.0 / sqrt(ss);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        u[q] *= inv;
+        dm += (u[q] - b[q]) * (u[q] - b[q]);
+        dp += (u[q] + b[q]) * (u[q] + b[q]);
+    }
+    dm = warp_sum(dm);
+    dp = warp_sum(dp);
+    const double d = sqrt(fmin(dm, dp));
+    if (!bad) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (k < n) B32[static_cast<int64_t>(r) * ldb + k] = static_cast<float>(u[q]);
+        }
+    }
+    if (lane == 0) {
+        flags[j] = (!bad && d > tol) ? 1 : 0;
+        iters[r] += 1;
+        if (bad) atomicOr(status, DEV_NONFINITE);
+        if (traj && t_iter < kTrajLen) {
+            double m2 = 0.0, m4 = 0.0;
+            for (int sp = 0; sp < splits; ++sp) {
+                m2 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 0];
+                m4 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 1];
+            }
+            m2 *= inv_T;
+            m4 *= inv_T;
+            const double alpha = m2 > 0.0 ? m4 / (m2 * m2) - 3.0 : 0.0;
+            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 0] = static_cast<float>(alpha);
+            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 1] = static_cast<float>(d);
+        }
+    }
+}
+
+cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
+                            int part_rows, int n_pad, int n, const int* act_idx, int M_act, float* B32, int ldb,
+                            double inv_T, double tol, int* flags, int* iters, float* traj, int t_iter,
+                            int* status) {
+    const int threads = 256;
+    const int blocks = (M_act * 32 + threads - 1) / threads;
+    finalize_kernel<<<blocks, threads, 0, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, M_act,
+                                                B32, ldb, inv_T, tol, flags, iters, traj, t_iter, status);
+    return cudaGetLastError();
+}
+
+// Un-normalised update (step entry point): Bnew = acc / T - 3 B and moments / T.
+__global__ void combine_kernel(const float* __restrict__ part_acc, const float* __restrict__ part_mom, int splits,
+                               int part_rows, int n_pad, int M, const float* __restrict__ B, double inv_T,
+                               float* __restrict__ Bnew, float* __restrict__ moments) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < static_cast<int64_t>(M) * n_pad) {
+        const int row = static_cast<int>(i / n_pad), k = static_cast<int>(i % n_pad);
+        double acc = 0.0;
+        for (int sp = 0; sp < splits; ++sp)
+            acc += static_cast<double>(part_acc[(static_cast<int64_t>(sp) * part_rows + row) * n_pad + k]);
+        Bnew[i] = static_cast<float>(acc * inv_T - 3.0 * static_cast<double>(B[i]));
+    }
+    if (moments && i < static_cast<int64_t>(M) * 4) {
+        const int row = static_cast<int>(i / 4), c = static_cast<int>(i % 4);
+        double acc = 0.0;
+        if (c < 3)
+            for (int sp = 0; sp < splits; ++sp)
+                acc += static_cast<double>(part_mom[(static_cast<int64_t>(sp) * part_rows + row) * 4 + c]);
+        moments[i] = static_cast<float>(acc * inv_T);
+    }
+}
+
+cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits, int part_rows,
+                           int n_pad, int M, const float* B, double inv_T, float* Bnew, float* moments) {
+    const int64_t total = static_cast<int64_t>(M) * (n_pad > 4 ? n_pad : 4);
+    combine_kernel<<<static_cast<int>((total + 255) / 256), 256, 0, s>>>(part_acc, part_mom, splits, part_rows,
+                                                                          n_pad, M, B, inv_T, Bnew, moments);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Stable stream compaction of the active restart list (Section 3.2: converged rows leave B).
+// One CTA of 1024 threads; thread t owns a contiguous slice of the list.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) compact_kernel(const int* __restrict__ flags, const int* __restrict__ act_in,
+                                                       int count, int* __restrict__ act_out, int* count_out_dev,
+                                                       int* count_out_host) {
+    __shared__ int warp_tot[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (count + 1023) / 1024;
+    const int b = t * per, e = min(count, b + per);
+    int local = 0;
+    for (int i = b; i < e; ++i) local += flags[i] != 0;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = warp_tot[lane];
+        int iv = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += y;
+        }
+        warp_tot[lane] = iv - v;  // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    int pos = warp_tot[w] + incl - local;
+    for (int i = b; i < e; ++i)
+        if (flags[i]) act_out[pos++] = act_in ? act_in[i] : i;
+    if (t == 1023) {
+        const int total = warp_tot[31] + incl;
+        *count_out_dev = total;
+        if (count_out_host) *reinterpret_cast<volatile int*>(count_out_host) = total;
+    }
+}
+
+cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, int count, int* act_out,
+                           int* count_out_dev, int* count_out_host) {
+    compact_kernel<<<1, 1024, 0, s>>>(flags, act_in, count, act_out, count_out_dev, count_out_host);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Kurtosis and objective of candidate rows from split-T moment partials (Eq. 2, Eq. 1).
+// m2 = mean z^2, m4 = mean z^4, q = mean (z^2 - 1)^2. alpha + 2 = m4/m2^2 - 1 is formed as
+// (q - (m2 - 1)^2) / m2^2, which has no cancellation when z^2 ~ 1 (binary-like components
+// whose alpha sits just above -2, where Upsilon is steep).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void alpha_upsilon(double m2, double m4, double q, double& alpha, double& ups) {
+    const double a2 = (q - (m2 - 1.0) * (m2 - 1.0)) / (m2 * m2);
+    alpha = a2 - 2.0;
+    if (!(m2 > 0.0) || !isfinite(a2)) {
+        alpha = 0.0;
+        ups = -INFINITY;  // never selected
+        return;
+    }
+    ups = a2 > 0.0 ? alpha - 2.0 * log(0.5 * a2) : INFINITY;
+    (void)m4;
+}
+
+__global__ void kurt_finalize_kernel(const float* __restrict__ part_mom, int splits, int part_rows,
+                                     const int* __restrict__ act_idx, int count, double inv_T,
+                                     double* __restrict__ alpha, double* __restrict__ ups) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    double m2 = 0.0, m4 = 0.0, q = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+        const float* p = part_mom + (static_cast<int64_t>(sp) * part_rows + j) * 4;
+        m2 += p[0];
+        m4 += p[1];
+        q += p[2];
+    }
+    double a, u;
+    alpha_upsilon(m2 * inv_T, m4 * inv_T, q * inv_T, a, u);
+    const int r = act_idx ? act_idx[j] : j;
+    alpha[r] = a;
+    ups[r] = u;
+}
+
+cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int splits, int part_rows,
+                                 const int* act_idx, int count, double inv_T, double* alpha, double* ups) {
+    kurt_finalize_kernel<<<(count + 255) / 256, 256, 0, s>>>(part_mom, splits, part_rows, act_idx, count, inv_T,
+                                                              alpha, ups);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Candidate selection: p = argmax Upsilon (Algorithm 2), ties to the lowest restart index.
+// Distinct top-k: repeat {argmax over non-excluded rows; exclude every row whose direction
+// matches the pick up to sign (|cos| >= threshold)}.
+// ------------------------------------------------------------------------------------------
+__global__ void select_clear_kernel(int* excluded, int M, int* cand, int kmax) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) excluded[i] = 0;
+    if (i < kmax) cand[i] = -1;
+}
+cudaError_t launch_select_clear(cudaStream_t s, int* excluded, int M, int* cand, int kmax) {
+    const int n = M > kmax ? M : kmax;
+    select_clear_kernel<<<(n + 255) / 256, 256, 0, s>>>(excluded, M, cand, kmax);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ bool better(double u, int i, double bu, int bi) {
+    if (bi < 0) return true;
+    if (u > bu) return true;
+    return u == bu && i < bi;
+}
+
+// subset == nullptr: candidates are rows 0..count-1; else rows subset[0..count) (entries < 0
+// are skipped). Writes the winning row (or -1) to *out_slot.
+__global__ void __launch_bounds__(1024) argmax_kernel(const double* __restrict__ ups, const int* __restrict__ excluded,
+                                                      const int* __restrict__ subset, int count, int* out_slot) {
+    __shared__ double su[32];
+    __shared__ int si[32];
+    double bu = -INFINITY;
+    int bi = -1;
+    for (int j = threadIdx.x; j < count; j += blockDim.x) {
+        const int r = subset ? subset[j] : j;
+        if (r < 0) continue;
+        if (excluded && excluded[r]) continue;
+        const double u = ups[r];
+        if (u != u || u == -INFINITY) continue;
+        if (better(u, r, bu, bi)) {
+            bu = u;
+            bi = r;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ou = __shfl_xor_sync(0xffffffffu, bu, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && better(ou, oi, bu, bi)) {
+            bu = ou;
+            bi = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        su[w] = bu;
+        si[w] = bi;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        bu = lane < nw ? su[lane] : -INFINITY;
+        bi = lane < nw ? si[lane] : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ou = __shfl_xor_sync(0xffffffffu, bu, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi >= 0 && better(ou, oi, bu, bi)) {
+                bu = ou;
+                bi = oi;
+            }
+        }
+        if (lane == 0) *out_slot = bi;
+    }
+}
+
+cudaError_t launch_argmax(cudaStream_t s, const double* ups, const int* excluded, const int* subset, int count,
+                          int* out_slot) {
+    argmax_kernel<<<1, 1024, 0, s>>>(ups, excluded, subset, count, out_slot);
+    return cudaGetLastError();
+}
+
+// One warp per restart row: exclude it when |b . b_sel| >= cos_thresh (same optimum up to sign).
+__global__ void exclude_kernel(const float* __restrict__ B32, int ldb, int n, int M, const int* sel_slot,
+                               int* excluded, double cos_thresh) {
+    const int sel = *sel_slot;
+    if (sel < 0) return;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= M) return;
+    double dot = 0.0, na = 0.0, nb = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double a = B32[static_cast<int64_t>(r) * ldb + k];
+        const double b = B32[static_cast<int64_t>(sel) * ldb + k];
+        dot += a * b;
+        na += a * a;
+        nb += b * b;
+    }
+    dot = warp_sum(dot);
+    na = warp_sum(na);
+    nb = warp_sum(nb);
+    if (lane == 0 && (r == sel || fabs(dot) >= cos_thresh * sqrt(na * nb))) excluded[r] = 1;
+}
+
+cudaError_t launch_exclude(cudaStream_t s, const float* B32, int ldb, int n, int M, const int* sel_slot,
+                           int* excluded, double cos_thresh) {
+    exclude_kernel<<<(M * 32 + 255) / 256, 256, 0, s>>>(B32, ldb, n, M, sel_slot, excluded, cos_thresh);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Append (Algorithm 2, last step): w_i = b_p G (n-dim winner mapped back to N channels; Section
+// 3.3), computed in FP64 after renormalising b_p. The rows of G are orthogonal to the earlier
+// rows of W in exact arithmetic; in FP64 they are so only up to cond(F~F~^T) * eps, so w_i is
+// re-orthogonalised against W[0..i) (classical Gram-Schmidt, applied twice) and renormalised,
+// which keeps W W^T = I at rounding level. The sign is made canonical (largest-magnitude entry
+// positive, first on ties). comp_stats receives (p, alpha_p, Upsilon_p).
+// ------------------------------------------------------------------------------------------
+__device__ double block_sum256(double v, double* red) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[k];
+    return s;
+}
+
+__global__ void __launch_bounds__(256) append_kernel(const double* __restrict__ G, int n, int N,
+                                                     const float* __restrict__ B32, int ldb, const int* p_slot,
+                                                     const double* __restrict__ alpha, const double* __restrict__ ups,
+                                                     double* __restrict__ W, int i, double* kurt_out,
+                                                     double* comp_stats) {
+    __shared__ double b[kMaxN];
+    __shared__ double w[kMaxN];
+    __shared__ double coef[kMaxN];
+    __shared__ double red[8];
+    __shared__ int redi[8];
+    const int p = *p_slot;
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    double* W_row = W + static_cast<int64_t>(i) * N;
+    if (p < 0) {
+        if (t < N) W_row[t] = 0.0;
+        if (t == 0) {
+            *kurt_out = 0.0;
+            comp_stats[0] = -1.0;
+        }
+        return;
+    }
+    const double v = t < n ? static_cast<double>(B32[static_cast<int64_t>(p) * ldb + t]) : 0.0;
+    const double ss = block_sum256(v * v, red);
+    if (t < n) b[t] = v / sqrt(ss);
+    __syncthreads();
+    double acc = 0.0;
+    if (t < N)
+        for (int r = 0; r < n; ++r) acc += b[r] * G[static_cast<int64_t>(r) * N + t];
+    if (t < N) w[t] = acc;
+    __syncthreads();
+    for (int pass = 0; pass < 2 && i > 0; ++pass) {
+        // coef[j] = W_j . w (one thread per earlier row), then w -= sum_j coef[j] W_j
+        for (int j = t; j < i; j += 256) {
+            double d = 0.0;
+            for (int c = 0; c < N; ++c) d += W[static_cast<int64_t>(j) * N + c] * w[c];
+            coef[j] = d;
+        }
+        __syncthreads();
+        if (t < N) {
+            double x = w[t];
+            for (int j = 0; j < i; ++j) x -= coef[j] * W[static_cast<int64_t>(j) * N + t];
+            acc = x;
+        }
+        __syncthreads();
+        if (t < N) w[t] = acc;
+        __syncthreads();
+    }
+    const double nn = block_sum256(t < N ? acc * acc : 0.0, red);
+    acc = t < N ? acc / sqrt(nn) : 0.0;
+    // canonical sign: argmax |w| (lowest index on ties)
+    double best = t < N ? fabs(acc) : -1.0;
+    int bi = t < N ? t : 1 << 30;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[wp] = best;
+        redi[wp] = bi;
+    }
+    __syncthreads();
+    best = red[0];
+    bi = redi[0];
+    for (int k = 1; k < 8; ++k)
+        if (red[k] > best || (red[k] == best && redi[k] < bi)) {
+            best = red[k];
+            bi = redi[k];
+        }
+    __syncthreads();
+    if (t == bi) red[0] = acc;
+    __syncthreads();
+    const double sgn = red[0] < 0.0 ? -1.0 : 1.0;
+    if (t < N) W_row[t] = sgn * acc;
+    if (t == 0) {
+        *kurt_out = alpha[p];
+        comp_stats[0] = static_cast<double>(p);
+        comp_stats[1] = alpha[p];
+        comp_stats[2] = ups[p];
+    }
+}
+
+cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb, const int* p_slot,
+                          const double* alpha, const double* ups, double* W, int i, double* kurt_out,
+                          double* comp_stats) {
+    append_kernel<<<1, 256, 0, s>>>(G, n, N, B32, ldb, p_slot, alpha, ups, W, i, kurt_out, comp_stats);
+    return cudaGetLastError();
+}
+
+}  // namespace ica

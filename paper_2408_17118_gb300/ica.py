@@ -1,0 +1,197 @@
+"""Python binding of the ordering-ICA C ABI: the same entry points as include/ica.h.
+
+Argument marshalling only. Device buffers are torch CUDA tensors (torch provides device memory
+and the stream); every computation runs in libica.so's kernels. Each function raises
+``IcaError`` when the library returns a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import ICA_BF16, ICA_FP32, ICA_PLAIN_FP32, ica_opts  # noqa: F401
+
+
+class IcaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _lib.load()
+        msg = lib.ica_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise IcaError(status, where)
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, name: str = "tensor") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+class Context:
+    """An ica_ctx bound to one device, torch's current stream and a torch-allocated workspace."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _lib.load()
+        self.device = device
+        h = C.c_void_p()
+        _check(self.lib.ica_create(C.byref(h), device), "ica_create")
+        self.handle = h
+        self.workspace = None
+        self.set_stream(torch.cuda.current_stream(device))
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        _check(self.lib.ica_set_stream(self.handle, C.c_void_p(stream.cuda_stream)), "ica_set_stream")
+
+    def ensure_workspace(self, N: int, T: int, M: int, opts: ica_opts | None = None):
+        need = self.lib.ica_workspace_bytes(N, T, M, C.byref(opts) if opts is not None else None)
+        if need == 0:
+            raise ValueError(f"invalid sizes N={N} T={T} M={M}")
+        if self.workspace is None or self.workspace.numel() < need:
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        _check(self.lib.ica_set_workspace(self.handle, C.c_void_p(self.workspace.data_ptr()), self.workspace.numel()),
+               "ica_set_workspace")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.lib.ica_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ica_default_opts(**overrides) -> ica_opts:
+    o = ica_opts()
+    _lib.load().ica_default_opts(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def ica_status_string(status: int) -> str:
+    return _lib.load().ica_status_string(status).decode()
+
+
+def ica_workspace_bytes(N: int, T: int, M: int, opts: ica_opts | None = None) -> int:
+    return int(_lib.load().ica_workspace_bytes(N, T, M, C.byref(opts) if opts is not None else None))
+
+
+def ica_whiten(ctx: Context, X: torch.Tensor, Xw: torch.Tensor | None = None):
+    """X: N x T float32 (CUDA). Returns (Xw float32 N x T, V float64 N x N, mean float64 N)."""
+    N, T = X.shape
+    Xw = torch.empty_like(X) if Xw is None else Xw
+    V = torch.empty((N, N), dtype=torch.float64, device=X.device)
+    mean = torch.empty(N, dtype=torch.float64, device=X.device)
+    ctx.ensure_workspace(N, T, 1, ica_default_opts(precision=ICA_FP32))
+    _check(ctx.lib.ica_whiten(ctx.handle, _ptr(X, torch.float32, "X"), N, T, _ptr(Xw, torch.float32, "Xw"),
+                              _ptr(V), _ptr(mean)), "ica_whiten")
+    return Xw, V, mean
+
+
+def ica_order_fit(ctx: Context, Xw: torch.Tensor, M: int, n_components: int, iters: int, tol: float, seed: int,
+                  opts: ica_opts | None = None, B0: torch.Tensor | None = None):
+    """Fast ordering ICA on whitened Xw (N x T float32). Returns (W float64 n_found x N,
+    kurtosis float64 n_found)."""
+    N, T = Xw.shape
+    opts = ica_default_opts() if opts is None else opts
+    if B0 is not None:
+        if B0.shape != (n_components, M, N):
+            raise ValueError("B0 must be n_components x M x N")
+        opts.B0 = _ptr(B0, torch.float32, "B0")
+    ctx.ensure_workspace(N, T, M, opts)
+    W = torch.zeros((n_components, N), dtype=torch.float64, device=Xw.device)
+    kurt = torch.zeros(n_components, dtype=torch.float64, device=Xw.device)
+    nf = C.c_int(0)
+    _check(ctx.lib.ica_order_fit(ctx.handle, _ptr(Xw, torch.float32, "Xw"), N, T, M, n_components, iters, float(tol),
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(opts), _ptr(W), _ptr(kurt), C.byref(nf)),
+           "ica_order_fit")
+    return W[: nf.value], kurt[: nf.value]
+
+
+def ica_last_stats(ctx: Context) -> str:
+    buf = C.create_string_buffer(1 << 20)
+    _check(ctx.lib.ica_last_stats(ctx.handle, buf, len(buf)), "ica_last_stats")
+    return buf.value.decode()
+
+
+def ica_init_restarts(ctx: Context, seed: int, component: int, M: int, n: int, ldb: int | None = None,
+                      device: int = 0) -> torch.Tensor:
+    ldb = n if ldb is None else ldb
+    B = torch.empty((M, ldb), dtype=torch.float32, device=f"cuda:{device}")
+    _check(ctx.lib.ica_init_restarts(ctx.handle, int(seed) & 0xFFFFFFFFFFFFFFFF, component, M, n, _ptr(B), ldb),
+           "ica_init_restarts")
+    return B
+
+
+def ica_deflation_basis(ctx: Context, W: torch.Tensor, N: int) -> torch.Tensor:
+    k = W.shape[0]
+    G = torch.empty((N - k, N), dtype=torch.float64, device=W.device)
+    ctx.ensure_workspace(N, 8, 1, ica_default_opts(precision=ICA_FP32))
+    _check(ctx.lib.ica_deflation_basis(ctx.handle, _ptr(W, torch.float64, "W") if k else None, k, N, _ptr(G)),
+           "ica_deflation_basis")
+    return G
+
+
+def _ld(T: int) -> int:
+    return (T + 7) // 8 * 8
+
+
+def ica_reduce(ctx: Context, G: torch.Tensor, Xw: torch.Tensor, want32: bool = True, want16: bool = True):
+    """X~ = G Xw. Returns (Xt32 n_pad x ld float32 or None, Xt16 n_pad x ld bfloat16 or None)."""
+    n, N = G.shape
+    T = Xw.shape[1]
+    n_pad = (n + 15) // 16 * 16
+    ld = _ld(T)
+    Xt32 = torch.empty((n_pad, ld), dtype=torch.float32, device=Xw.device) if want32 else None
+    Xt16 = torch.empty((n_pad, ld), dtype=torch.bfloat16, device=Xw.device) if want16 else None
+    _check(ctx.lib.ica_reduce(ctx.handle, _ptr(G, torch.float64, "G"), n, N, _ptr(Xw, torch.float32, "Xw"), T,
+                              _ptr(Xt32), ld, _ptr(Xt16), ld), "ica_reduce")
+    return Xt32, Xt16
+
+
+def _xt_args(Xt: torch.Tensor, precision: int):
+    want = torch.float32 if precision == ICA_FP32 else torch.bfloat16
+    if Xt.dtype != want:
+        raise ValueError(f"Xt must be {want} for precision {precision}")
+    return _ptr(Xt, want, "Xt"), Xt.shape[1]
+
+
+def ica_fp_step(ctx: Context, precision: int, B: torch.Tensor, n: int, Xt: torch.Tensor, T: int):
+    """One un-normalised matrix-form update of the M rows of B (M x n_pad float32).
+    Returns (Bnew M x n_pad float32, moments M x 4 float32)."""
+    M, n_pad = B.shape
+    xp, ldx = _xt_args(Xt, precision)
+    ctx.ensure_workspace(n, T, M, ica_default_opts(precision=ICA_FP32))
+    Bnew = torch.empty_like(B)
+    mom = torch.empty((M, 4), dtype=torch.float32, device=B.device)
+    _check(ctx.lib.ica_fp_step(ctx.handle, precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(Bnew),
+                               _ptr(mom)), "ica_fp_step")
+    return Bnew, mom
+
+
+def ica_kurtosis(ctx: Context, precision: int, B: torch.Tensor, n: int, Xt: torch.Tensor, T: int):
+    """alpha and Upsilon (float64, M each) of the rows of B on reduced data Xt."""
+    M, n_pad = B.shape
+    xp, ldx = _xt_args(Xt, precision)
+    ctx.ensure_workspace(n, T, M, ica_default_opts(precision=ICA_FP32))
+    a = torch.empty(M, dtype=torch.float64, device=B.device)
+    u = torch.empty(M, dtype=torch.float64, device=B.device)
+    _check(ctx.lib.ica_kurtosis(ctx.handle, precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(a),
+                                _ptr(u)), "ica_kurtosis")
+    return a, u

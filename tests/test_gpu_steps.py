@@ -1,0 +1,235 @@
+"""Per-step parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Sizes span several tiles and ragged tails (restart tiles of 64/128 rows, sample chunks of 64/128,
+reduced dimension padded to 16). Tolerances are derived from the arithmetic of each step:
+
+* FP32 products: |error| <= 1e-4 * S + 1e-6, with S = sum_t |z_t^3 x_kt| / T the magnitude
+  scale of the element (FP32 accumulation, random-walk growth with wide margin).
+* BF16 tensor-core update: the operands are rounded to BF16 on both sides (the oracle takes the
+  same rounded inputs); the GPU additionally rounds z^3 to BF16 (relative error <= 2^-9) and
+  accumulates in FP32, so |error| <= 2^-8 * S + 1e-6 (a factor 2 of slack on the rounding
+  bound).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2408_17118_gb300 import ica
+
+    c = ica.Context(0)
+    yield c
+    c.close()
+
+
+def rup(v, m):
+    return (v + m - 1) // m * m
+
+
+def bf16(a: np.ndarray) -> np.ndarray:
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def padded_xt(X: np.ndarray, n_pad: int, dtype) -> torch.Tensor:
+    n, T = X.shape
+    ld = rup(T, 8)
+    out = torch.zeros((n_pad, ld), dtype=dtype)
+    out[:n, :T] = torch.from_numpy(X.astype(np.float32)).to(dtype)
+    return out.cuda()
+
+
+def random_rows(M, n, n_pad, seed):
+    B = oracle.normalise_rows(np.random.default_rng(seed).standard_normal((M, n))).astype(np.float32)
+    Bp = np.zeros((M, n_pad), dtype=np.float32)
+    Bp[:, :n] = B
+    return Bp
+
+
+# ------------------------------------------------------------------------------ initial restarts
+@pytest.mark.parametrize("seed,comp,M,n", [(0, 0, 64, 8), (12345678901, 3, 130, 37), (2 ** 63 + 5, 7, 7, 256),
+                                           (1, 0, 1, 1), (99, 200, 300, 255)])
+def test_init_restarts(ctx, seed, comp, M, n):
+    from paper_2408_17118_gb300 import ica
+
+    ldb = rup(n, 16)
+    B = ica.ica_init_restarts(ctx, seed, comp, M, n, ldb).cpu().numpy()
+    ref = oracle.normalise_rows(oracle.restart_normals(seed, comp, M, n))
+    assert np.abs(B[:, :n] - ref).max() < 2e-7
+    assert np.all(B[:, n:] == 0)
+
+
+# ------------------------------------------------------------------------------ deflation basis
+@pytest.mark.parametrize("N,k", [(8, 1), (8, 4), (8, 7), (33, 10), (33, 20), (64, 32), (64, 63), (130, 65),
+                                 (256, 1), (256, 128), (256, 200)])
+def test_deflation_basis(ctx, N, k):
+    from paper_2408_17118_gb300 import ica
+
+    Q, _ = np.linalg.qr(np.random.default_rng(N * 7 + k).standard_normal((N, N)))
+    W = np.ascontiguousarray(Q[:k])
+    G = ica.ica_deflation_basis(ctx, torch.from_numpy(W).cuda(), N).cpu().numpy()
+    ref = oracle.deflation_basis(W, N)
+    assert G.shape == ref.shape
+    # both sides evaluate (F~F~^T)^(-1/2) F~ in FP64; their rounding errors are amplified by
+    # 1 / lambda_min(F~F~^T), which reaches ~1e5 for N = 256
+    Ft = (np.eye(N) - W.T @ W)[: N - k]
+    lam_min = np.linalg.eigvalsh(Ft @ Ft.T).min()
+    tol = max(1e-12, 100 * np.finfo(np.float64).eps / lam_min)
+    assert np.abs(G - ref).max() < tol, (np.abs(G - ref).max(), tol)
+    assert np.abs(G @ G.T - np.eye(N - k)).max() < tol
+    assert np.abs(W @ G.T).max() < tol
+
+
+def test_deflation_basis_identity(ctx):
+    from paper_2408_17118_gb300 import ica
+
+    G = ica.ica_deflation_basis(ctx, torch.zeros((0, 12), dtype=torch.float64).cuda(), 12).cpu().numpy()
+    assert np.array_equal(G, np.eye(12))
+
+
+# ------------------------------------------------------------------------------ whitening
+@pytest.mark.parametrize("kind", ["c1", "eeg64", "n256"])
+def test_whiten(ctx, kind):
+    from paper_2408_17118_gb300 import ica
+
+    if kind == "c1":
+        X = synth.c1(0).X
+    elif kind == "eeg64":
+        X = synth.eeg_like(64, 20_000, 8, seed=1).X
+    else:
+        X = synth.eeg_like(256, 6000, 8, seed=2).X
+    Xw, V, mean = ica.ica_whiten(ctx, torch.from_numpy(X).cuda())
+    Xw_o, V_o, mean_o = oracle.whiten(X)
+    assert np.abs(mean.cpu().numpy() - mean_o).max() < 1e-12 * (1 + np.abs(mean_o).max())
+    assert np.abs(V.cpu().numpy() - V_o).max() < 1e-8 * np.abs(V_o).max()
+    # FP32 apply: N-term FP32 dot products of O(1) values
+    assert np.abs(Xw.cpu().numpy() - Xw_o).max() < 5e-5 * max(1.0, np.abs(Xw_o).max())
+
+
+# ------------------------------------------------------------------------------ reduction
+@pytest.mark.parametrize("N,k,T", [(8, 0, 1000), (20, 7, 4099), (64, 30, 20_000), (130, 3, 3000)])
+def test_reduce(ctx, N, k, T):
+    from paper_2408_17118_gb300 import ica
+
+    Xw = synth.small_random(N, T, seed=N + k).astype(np.float32)
+    if k:
+        Q, _ = np.linalg.qr(np.random.default_rng(k).standard_normal((N, N)))
+        G = oracle.deflation_basis(Q[:k], N)
+    else:
+        G = np.eye(N)
+    n = N - k
+    Xt32, Xt16 = ica.ica_reduce(ctx, torch.from_numpy(np.ascontiguousarray(G)).cuda(), torch.from_numpy(Xw).cuda())
+    Xt32 = Xt32.cpu()
+    Xt16 = Xt16.cpu()
+    ref = G @ Xw.astype(np.float64)
+    got = Xt32.numpy()[:n, :T]
+    assert np.abs(got - ref).max() < 2e-6 * N * max(1.0, np.abs(Xw).max())
+    assert torch.equal(Xt16[:, :T], Xt32[:, :T].to(torch.bfloat16))  # BF16 copy = rounding of the FP32 result
+    assert torch.all(Xt32[n:, :T] == 0) and torch.all(Xt16[n:, :T].float() == 0)
+
+
+# ------------------------------------------------------------------------------ fused update
+STEP_SHAPES = [(1, 1, 64), (63, 5, 1000), (64, 16, 4097), (65, 17, 12345), (129, 37, 2000), (200, 64, 40_000),
+               (300, 100, 5000), (128, 128, 8192), (130, 129, 3000), (257, 200, 6000), (100, 256, 10_000)]
+
+
+def oracle_update(B, Xt, T, bf16_inputs):
+    Bq = bf16(B) if bf16_inputs else B.astype(np.float64)
+    Xq = bf16(Xt) if bf16_inputs else Xt.astype(np.float64)
+    Bq = Bq.astype(np.float64)
+    Xq = Xq.astype(np.float64)
+    Z = Bq @ Xq
+    U = (Z ** 3) @ Xq.T / T - 3.0 * B.astype(np.float64)
+    S = (np.abs(Z) ** 3) @ np.abs(Xq).T / T
+    return U, S, Z
+
+
+@pytest.mark.parametrize("M,n,T", STEP_SHAPES)
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fp_step(ctx, prec, M, n, T):
+    from paper_2408_17118_gb300 import ica
+
+    n_pad = rup(n, 16)
+    Xt = synth.small_random(n, T, seed=M + n + T)
+    B = random_rows(M, n, n_pad, seed=M * 31 + n)
+    p = ica.ICA_FP32 if prec == "fp32" else ica.ICA_BF16
+    xt = padded_xt(Xt, n_pad, torch.float32 if prec == "fp32" else torch.bfloat16)
+    Bnew, mom = ica.ica_fp_step(ctx, p, torch.from_numpy(B).cuda(), n, xt, T)
+    Bnew = Bnew.cpu().numpy()
+    mom = mom.cpu().numpy()
+    U, S, Z = oracle_update(B[:, :n], Xt, T, prec == "bf16")
+    tol = (1e-4 if prec == "fp32" else 2.0 ** -8) * S + 1e-6
+    err = np.abs(Bnew[:, :n] - U)
+    assert np.all(err <= tol), (err.max(), (err / tol).max())
+    assert np.all(Bnew[:, n:] == 0)
+    m2 = np.mean(Z ** 2, axis=1)
+    m4 = np.mean(Z ** 4, axis=1)
+    assert np.allclose(mom[:, 0], m2, rtol=2e-5, atol=1e-7)
+    assert np.allclose(mom[:, 1], m4, rtol=2e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("M,n,T", [(64, 8, 10_000), (300, 37, 4097), (129, 128, 20_000), (100, 200, 5000)])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_kurtosis(ctx, prec, M, n, T):
+    from paper_2408_17118_gb300 import ica
+
+    n_pad = rup(n, 16)
+    Xt = synth.small_random(n, T, seed=n + T)  # includes binary rows (alpha close to -2)
+    B = random_rows(M, n, n_pad, seed=n)
+    # make some rows point exactly / almost exactly at single sources (binary, uniform, ...)
+    for r in range(min(M, 2 * n)):
+        j = r % n
+        v = np.zeros(n_pad, dtype=np.float32)
+        v[j] = 1.0
+        if r >= n:
+            v[(j + 1) % n] = 1e-3
+            v /= np.linalg.norm(v)
+        B[r] = v
+    p = ica.ICA_FP32 if prec == "fp32" else ica.ICA_BF16
+    xt = padded_xt(Xt, n_pad, torch.float32 if prec == "fp32" else torch.bfloat16)
+    a, u = ica.ica_kurtosis(ctx, p, torch.from_numpy(B).cuda(), n, xt, T)
+    a = a.cpu().numpy()
+    u = u.cpu().numpy()
+    Bq = bf16(B[:, :n]).astype(np.float64) if prec == "bf16" else B[:, :n].astype(np.float64)
+    Xq = bf16(Xt).astype(np.float64) if prec == "bf16" else Xt.astype(np.float64)
+    Z = Bq @ Xq
+    m2 = np.mean(Z ** 2, axis=1)
+    ref_a2 = np.mean(Z ** 4, axis=1) / m2 ** 2 - 1.0  # alpha + 2 of the normalised row
+    # alpha + 2 from FP32 sums of (z^2 - 1)^2: relative error ~1e-5 plus an absolute floor
+    got_a2 = a + 2.0
+    assert np.all(np.abs(got_a2 - ref_a2) <= 3e-5 * ref_a2 + 1e-8), np.abs(got_a2 - ref_a2).max()
+    fin = ref_a2 > 1e-9
+    ref_u = ref_a2[fin] - 2.0 - 2.0 * np.log(ref_a2[fin] / 2.0)
+    assert np.allclose(u[fin], ref_u, rtol=1e-4, atol=1e-5)
+
+
+def test_fp_step_full_size_sampled(ctx):
+    """The launch configuration of the N=64, T=200,000, M=1024 fit (first iteration), BF16:
+    sampled rows against the oracle on the same BF16 inputs."""
+    from paper_2408_17118_gb300 import ica
+
+    M, n, T = 1024, 64, 200_000
+    w = synth.c2(0)
+    Xw, V, mean = ica.ica_whiten(ctx, torch.from_numpy(w.X).cuda())
+    Xt32, Xt16 = ica.ica_reduce(ctx, torch.eye(n, dtype=torch.float64).cuda(), Xw)
+    B = ica.ica_init_restarts(ctx, 5, 0, M, n, n)
+    Bnew, mom = ica.ica_fp_step(ctx, ica.ICA_BF16, B, n, Xt16, T)
+    rows = np.random.default_rng(0).choice(M, 16, replace=False)
+    Xq = Xt16[:n, :T].float().cpu().numpy().astype(np.float64)
+    Bs = B.cpu().numpy()[rows]
+    Zs = bf16(Bs).astype(np.float64) @ Xq
+    U = (Zs ** 3) @ Xq.T / T - 3.0 * Bs
+    S = (np.abs(Zs) ** 3) @ np.abs(Xq).T / T
+    err = np.abs(Bnew.cpu().numpy()[rows] - U)
+    assert np.all(err <= 2.0 ** -8 * S + 1e-6), (err / (2.0 ** -8 * S + 1e-6)).max()
