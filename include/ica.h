@@ -163,6 +163,34 @@ int ica_fp_step(ica_ctx* ctx, int precision, const float* B, int M, int n, const
 int ica_kurtosis(ica_ctx* ctx, int precision, const float* B, int M, int n, const void* Xt,
                  int64_t T, int64_t ldx, double* alpha, double* ups);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free entry point. (The paper has no counterpart: this is a deployment aid.)
+ * --------------------------------------------------------------------------------------- */
+
+/* Same computation and layouts as ica_fp_step, for callers that cannot call cudaMalloc at all:
+   code inside an application whose allocator has already reserved the whole device (a
+   framework caching allocator, an inference server's memory pool), plug-ins that may not
+   allocate after start-up, or latency-critical loops that cannot afford cudaFree's implicit
+   device synchronisation. It needs no context and no workspace: the split-T partial sums live
+   in a 16 MiB array inside this library (one per GPU that loads the library, held until the
+   process exits). It calls no cudaMalloc, cudaFree or other allocating routine.
+   - The first call made with a given device current looks up that array's device address
+     (cudaGetSymbolAddress) and the tensor-map encoder; make that first call before any stream
+     capture that might include this entry point.
+   - Limit: M rows rounded up to the kernel's restart tile (128 for ICA_BF16, 64 for ICA_FP32)
+     times (round_up(n, 16) + 4) * 4 bytes must fit in 16 MiB less 256 bytes, i.e. about
+     16,000 rows at n = 256; beyond it the call returns ICA_ERR_WORKSPACE without launching
+     anything. Arguments outside ica_fp_step's range (M > 65536, ...) return ICA_ERR_ARG. Within the limit the sample range is split
+     into fewer pieces than ica_fp_step may use, so results can differ from it by FP32
+     summation order.
+   - Every call on a device shares the same array and the array keeps the last call's contents
+     (the call clears the status word it needs zeroed). Calls whose kernels overlap on the GPU
+     (different streams, or different host threads) race on it: serialise them.
+   - stream: the cudaStream_t to enqueue on (NULL = legacy default stream); the call
+     synchronises it once at the end to read the status word. */
+int ica_fp_step_noalloc(int precision, const float* B, int M, int n, const void* Xt, int64_t T,
+                        int64_t ldx, float* Bnew, float* moments, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ica_reduce": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, vp, i64]),
     "ica_fp_step": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_kurtosis": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
+    "ica_fp_step_noalloc": (i32, [i32, vp, i32, i32, vp, i64, i64, vp, vp, vp]),
 }
 
 _lib = None

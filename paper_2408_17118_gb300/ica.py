@@ -195,3 +195,19 @@ def ica_kurtosis(ctx: Context, precision: int, B: torch.Tensor, n: int, Xt: torc
     _check(ctx.lib.ica_kurtosis(ctx.handle, precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(a),
                                 _ptr(u)), "ica_kurtosis")
     return a, u
+
+
+def ica_fp_step_noalloc(precision: int, B: torch.Tensor, n: int, Xt: torch.Tensor, T: int,
+                        stream: torch.cuda.Stream | None = None):
+    """ica_fp_step without a context or workspace: for callers that cannot allocate device
+    memory (the library keeps its scratch in a fixed 16 MiB array per GPU). Returns
+    (Bnew, moments); the output tensors here are allocated by torch only for this binding's
+    convenience - a C caller passes its own."""
+    M, n_pad = B.shape
+    xp, ldx = _xt_args(Xt, precision)
+    stream = torch.cuda.current_stream(B.device) if stream is None else stream
+    Bnew = torch.empty_like(B)
+    mom = torch.empty((M, 4), dtype=torch.float32, device=B.device)
+    _check(_lib.load().ica_fp_step_noalloc(precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(Bnew),
+                                           _ptr(mom), C.c_void_p(stream.cuda_stream)), "ica_fp_step_noalloc")
+    return Bnew, mom
