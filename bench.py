@@ -257,6 +257,11 @@ def run_ours(args):
             a = kinds.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0})
             for f in a:
                 a[f] += v[f]
+    # device time per step of every phase of the fit (CUDA events around each launch)
+    phases = {k: v["ms"] / args.steps for k, v in kinds.items()}
+    for s in stats:
+        for k, v in s.get("phases", {}).items():
+            phases[k] = phases.get(k, 0.0) + v["ms"] / args.steps
 
     # whole-job aggregate over ranks: FLOPs summed, time = slowest rank
     if world > 1:
@@ -345,7 +350,7 @@ def run_ours(args):
             "e2e": {"value": e2e_tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": int(X_host.numel() * 4),
                     "d2h_bytes_per_step": int(K * N * 8 + K * 8), "time_s": statistics.median(e2e_ms) / 1e3},
             "clocks": clocks, "gpu_launches": int(launches),
-            "fused_kinds": kinds, "orthonormality": orth,
+            "fused_kinds": kinds, "phase_ms_per_step": phases, "orthonormality": orth,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

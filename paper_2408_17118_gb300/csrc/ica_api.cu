@@ -52,13 +52,16 @@ struct ica_ctx {
         int e0, e1;
     };
     std::vector<Rec> recs;
-    double kind_ms[4] = {0, 0, 0, 0}, kind_flops[4] = {0, 0, 0, 0};
-    long long kind_n[4] = {0, 0, 0, 0};
+    double kind_ms[10] = {}, kind_flops[10] = {};
+    long long kind_n[10] = {};
 };
 
 // kinds of timed fused launches
-enum { K_ITER = 0, K_KURT = 1, K_REFINE = 2, K_REFKURT = 3 };
-static const char* kKindName[4] = {"iteration", "kurtosis", "refine", "refine_kurtosis"};
+// kinds of timed launches: the four fused kernels, then the remaining phases of a component
+enum { K_ITER = 0, K_KURT = 1, K_REFINE = 2, K_REFKURT = 3, K_FINALIZE = 4, K_COMPACT = 5, K_BASIS = 6,
+       K_REDUCE = 7, K_SELECT = 8, K_APPEND = 9, K_NKINDS = 10 };
+static const char* kKindName[K_NKINDS] = {"iteration", "kurtosis", "refine", "refine_kurtosis", "finalize",
+                                          "compact", "basis", "reduce", "select", "append"};
 
 #define CK(call)                                      \
     do {                                              \
@@ -81,8 +84,9 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     int n_pad_max = 0, M_pad = 0, part_rows_max = 0;
     int64_t ldx = 0;
-    size_t status, counts, Xt32, Xt16, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots,
-        part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, total;
+    int tcols = 0;  // row length (elements) of the transposed BF16 copy
+    size_t status, counts, Xt32, Xt16, Xt16t, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots,
+        part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, comp_rows, total;
 };
 
 Layout make_layout(int N, int64_t T, int M, int precision) {
@@ -103,6 +107,8 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.counts = take(16 * sizeof(int));
     L.Xt32 = take(sizeof(float) * L.n_pad_max * static_cast<size_t>(L.ldx));
     L.Xt16 = take(precision == ICA_BF16 ? sizeof(uint16_t) * L.n_pad_max * static_cast<size_t>(L.ldx) : 0);
+    L.tcols = round_up64cols(L.n_pad_max < 128 ? L.n_pad_max : 128);
+    L.Xt16t = take(precision == ICA_BF16 ? sizeof(uint16_t) * static_cast<size_t>(L.ldx) * L.tcols : 0);
     L.Z = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(M) * L.ldx : 0);
     L.B32 = take(sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max);
     L.Bact = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max : 0);
@@ -128,6 +134,7 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.t4 = take(sizeof(double) * nN);
     L.cov_part = take(sizeof(double) * nN * covariance_splits(N, T));
     L.comp_stats = take(sizeof(double) * 4 * (N + 1));
+    L.comp_rows = take(sizeof(long long) * 2 * (N + 1));  // per component: rows updated (stage, refine)
     L.total = off;
     return L;
 }
@@ -156,6 +163,19 @@ void choose_splits(int64_t total_chunks, int tiles, int waves_ctas, int max_spli
     const int64_t c = (total_chunks + s - 1) / s;
     *cps = static_cast<int>(c);
     *splits = static_cast<int>((total_chunks + c - 1) / c);
+}
+
+// X~^T (T rows x tcols elements, reduced index contiguous): box {64 reduced entries, TC samples}.
+int encode_xmap_t(ica_ctx* c, CUtensorMap* map, const uint16_t* Xt16t, int tcols, int64_t T, int TC) {
+    if (!c->encode) return ICA_ERR_UNSUPPORTED;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(tcols), static_cast<cuuint64_t>(T)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(tcols) * 2};
+    cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(TC)};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = c->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(Xt16t), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ICA_OK : ICA_ERR_CUDA;
 }
 
 int encode_xmap(ica_ctx* c, CUtensorMap* map, const uint16_t* Xt16, int n_pad, int64_t T, int64_t ld) {
@@ -189,64 +209,100 @@ int ensure_cublas(ica_ctx* c) {
     return ICA_OK;
 }
 
-// One fused update of the active rows -> split partials. Returns the split count used.
+// One fused launch over the active rows -> split-T partial sums in the workspace.
 struct StepShape {
     int splits = 1, cps = 1, part_rows = 0;
 };
 
-int run_fused(ica_ctx* c, const Layout& L, int precision, bool moments_only, const float* B32, int ldb,
-              const int* act, int M_act, int n_pad, int64_t T, const float* Xt32, const uint16_t* Xt16, int64_t ldx,
-              int max_splits, StepShape* shape) {
+struct FusedArgs {
+    int precision = ICA_BF16;
+    bool moments_only = false;  // kurtosis pass: moments only, no update
+    bool moments = true;        // update pass: also accumulate sum z^2, sum z^4
+    const float* B32 = nullptr;
+    int ldb = 0;
+    const int* act = nullptr;        // active restart ids (NULL: rows 0..M_act-1)
+    const int* count_dev = nullptr;  // device count of active rows (NULL: M_act is exact)
+    int M_act = 0;                   // host upper bound of the active count (sizes the grid)
+    int n_pad = 0;
+    int64_t T = 0;
+    const float* Xt32 = nullptr;
+    const uint16_t* Xt16 = nullptr;
+    const uint16_t* Xt16t = nullptr;  // transposed BF16 copy (T x tcols) or NULL
+    int tcols = 0;
+    int64_t ldx = 0;
+    int max_splits = 0;
+};
+
+int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape) {
     cudaStream_t s = c->stream;
     float* pacc = at<float>(c, L.part_acc);
     float* pmom = at<float>(c, L.part_mom);
     int* status = at<int>(c, L.status);
-    if (precision == ICA_BF16) {
-        const int TC = tc_chunk(n_pad);
-        const int64_t total = (T + TC - 1) / TC;
-        const int tiles = (M_act + kTcRows - 1) / kTcRows;
-        choose_splits(total, tiles, 2 * 152, max_splits, &shape->splits, &shape->cps);
+    if (a.precision == ICA_BF16) {
+        const int TC = tc_chunk(a.n_pad);
+        const int64_t total = (a.T + TC - 1) / TC;
+        const int tiles = (a.M_act + kTcRows - 1) / kTcRows;
+        choose_splits(total, tiles, 152, a.max_splits, &shape->splits, &shape->cps);  // one CTA per SM, one wave
         shape->part_rows = tiles * kTcRows;
-        CUtensorMap map;
-        int rc = encode_xmap(c, &map, Xt16, n_pad, T, ldx);
+        CUtensorMap map, map_t;
+        int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
         if (rc) return rc;
-        KL(launch_fused_tc(s, moments_only, map, B32, ldb, act, M_act, n_pad, T, shape->splits, shape->cps,
-                           static_cast<int>(total), pacc, pmom, shape->part_rows, status));
+        const bool use_t = a.Xt16t && tc_transposed(a.n_pad);
+        if (use_t) {
+            rc = encode_xmap_t(c, &map_t, a.Xt16t, a.tcols, a.T, TC);
+            if (rc) return rc;
+        }
+        KL(launch_fused_tc(s, a.moments_only, a.moments, map, use_t ? &map_t : nullptr, a.B32, a.ldb, a.act,
+                           a.count_dev, a.M_act, a.n_pad, a.T, shape->splits, shape->cps, static_cast<int>(total), pacc,
+                           pmom, shape->part_rows, status));
         return ICA_OK;
     }
-    if (precision == ICA_FP32) {
-        const int64_t total = (T + 63) / 64;
-        const int tiles = (M_act + kFp32Rows - 1) / kFp32Rows;
-        choose_splits(total, tiles, 4 * 152, max_splits, &shape->splits, &shape->cps);
+    if (a.precision == ICA_FP32) {
+        const int64_t total = (a.T + 63) / 64;
+        if (a.M_act <= kFp32SmallRows) {  // a few candidates: row tile of 16, bound by reading X~
+            choose_splits(total, 1, 2 * 152, a.max_splits, &shape->splits, &shape->cps);
+            shape->part_rows = kFp32SmallRows;
+            KL(launch_fused_fp32_small(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx,
+                                       a.n_pad, a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
+            return ICA_OK;
+        }
+        const int tiles = (a.M_act + kFp32Rows - 1) / kFp32Rows;
+        choose_splits(total, tiles, 4 * 152, a.max_splits, &shape->splits, &shape->cps);
         shape->part_rows = tiles * kFp32Rows;
-        KL(launch_fused_fp32(s, moments_only, B32, ldb, act, M_act, Xt32, ldx, n_pad, T, shape->splits, shape->cps,
-                             pacc, pmom, shape->part_rows));
+        KL(launch_fused_fp32(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx, a.n_pad,
+                             a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
         return ICA_OK;
     }
-    // plain FP32 matrix form: Z = B X~ in device memory, cube, second product
+    // plain FP32 matrix form: Z = B X~ in device memory, cube, second product (cuBLAS)
     int rc = ensure_cublas(c);
     if (rc) return rc;
     float* Bact = at<float>(c, L.Bact);
     float* Z = at<float>(c, L.Z);
-    KL(launch_gather_rows(s, B32, ldb, act, M_act, n_pad, Bact));
+    const int rows = a.M_act;
+    KL(launch_gather_rows(s, a.B32, a.ldb, a.act, a.count_dev, rows, a.n_pad, Bact));
     if (c->cublas_set_stream(c->cublas, s) != 0) return ICA_ERR_CUDA;
     const float one = 1.f, zero = 0.f;
-    if (c->sgemm(c->cublas, 0, 0, static_cast<int>(T), M_act, n_pad, &one, Xt32, static_cast<int>(ldx), Bact, n_pad,
-                 &zero, Z, static_cast<int>(ldx)) != 0)
+    if (c->sgemm(c->cublas, 0, 0, static_cast<int>(a.T), rows, a.n_pad, &one, a.Xt32, static_cast<int>(a.ldx), Bact,
+                 a.n_pad, &zero, Z, static_cast<int>(a.ldx)) != 0)
         return ICA_ERR_CUDA;
     shape->splits = 1;
     shape->cps = 1;
-    shape->part_rows = M_act;
-    if (moments_only) {
-        KL(launch_row_moments(s, Z, M_act, T, ldx, pmom));
+    shape->part_rows = rows;
+    if (a.moments_only) {
+        KL(launch_row_moments(s, Z, rows, a.T, a.ldx, pmom));
         return ICA_OK;
     }
-    KL(launch_cube_inplace(s, Z, M_act, T, ldx));
-    if (c->sgemm(c->cublas, 1, 0, n_pad, M_act, static_cast<int>(T), &one, Xt32, static_cast<int>(ldx), Z,
-                 static_cast<int>(ldx), &zero, pacc, n_pad) != 0)
+    KL(launch_cube_inplace(s, Z, rows, a.T, a.ldx));
+    if (c->sgemm(c->cublas, 1, 0, a.n_pad, rows, static_cast<int>(a.T), &one, a.Xt32, static_cast<int>(a.ldx), Z,
+                 static_cast<int>(a.ldx), &zero, pacc, a.n_pad) != 0)
         return ICA_ERR_CUDA;
     return ICA_OK;
 }
+
+// Host reads of the device active count after iteration t (1-based): every iteration at
+// first, when most restarts leave, then every second, then every fourth. Between reads the
+// launches are sized for the last count read, an upper bound (counts only fall).
+bool sync_due(int t) { return t <= 4 || (t <= 12 && t % 2 == 0) || t % 4 == 0; }
 
 int check_ws(ica_ctx* c, const Layout& L) {
     if (!c->ws || c->ws_bytes < L.total) return ICA_ERR_WORKSPACE;
@@ -481,15 +537,30 @@ int ica_fp_step(ica_ctx* c, int precision, const float* B, int M, int n, const v
     if (!c || !B || !Xt || !Bnew || M < 1 || M > 65536 || n < 1 || n > kMaxN || T < 1 || ldx < T || ldx % 8)
         return ICA_ERR_ARG;
     if (precision != ICA_FP32 && precision != ICA_BF16) return ICA_ERR_UNSUPPORTED;
-    const Layout L = make_layout(n, T, M, ICA_FP32);
+    const Layout L = make_layout(n, T, M, precision);
     int rc = check_ws(c, L);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
     const int n_pad = round_up(n, 16);
     CK(cudaMemsetAsync(at<int>(c, L.status), 0, sizeof(int), c->stream));
     StepShape sh;
-    rc = run_fused(c, L, precision, false, B, n_pad, nullptr, M, n_pad, T, static_cast<const float*>(Xt),
-                   static_cast<const uint16_t*>(Xt), ldx, 0, &sh);
+    FusedArgs fa;
+    fa.precision = precision;
+    fa.B32 = B;
+    fa.ldb = n_pad;
+    fa.M_act = M;
+    fa.n_pad = n_pad;
+    fa.T = T;
+    fa.Xt32 = static_cast<const float*>(Xt);
+    fa.Xt16 = static_cast<const uint16_t*>(Xt);
+    fa.ldx = ldx;
+    if (precision == ICA_BF16 && tc_transposed(n_pad)) {
+        uint16_t* xt = at<uint16_t>(c, L.Xt16t);
+        KL(launch_transpose_bf16(c->stream, static_cast<const uint16_t*>(Xt), n_pad, T, ldx, xt, L.tcols));
+        fa.Xt16t = xt;
+        fa.tcols = L.tcols;
+    }
+    rc = run_fused(c, L, fa, &sh);
     if (rc) return rc;
     KL(launch_combine(c->stream, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows, n_pad,
                       M, B, 1.0 / static_cast<double>(T), Bnew, moments));
@@ -502,17 +573,33 @@ int ica_kurtosis(ica_ctx* c, int precision, const float* B, int M, int n, const 
         ldx % 8)
         return ICA_ERR_ARG;
     if (precision != ICA_FP32 && precision != ICA_BF16) return ICA_ERR_UNSUPPORTED;
-    const Layout L = make_layout(n, T, M, ICA_FP32);
+    const Layout L = make_layout(n, T, M, precision);
     int rc = check_ws(c, L);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
     const int n_pad = round_up(n, 16);
     CK(cudaMemsetAsync(at<int>(c, L.status), 0, sizeof(int), c->stream));
     StepShape sh;
-    rc = run_fused(c, L, precision, true, B, n_pad, nullptr, M, n_pad, T, static_cast<const float*>(Xt),
-                   static_cast<const uint16_t*>(Xt), ldx, 0, &sh);
+    FusedArgs fa;
+    fa.precision = precision;
+    fa.moments_only = true;
+    fa.B32 = B;
+    fa.ldb = n_pad;
+    fa.M_act = M;
+    fa.n_pad = n_pad;
+    fa.T = T;
+    fa.Xt32 = static_cast<const float*>(Xt);
+    fa.Xt16 = static_cast<const uint16_t*>(Xt);
+    fa.ldx = ldx;
+    if (precision == ICA_BF16 && tc_transposed(n_pad)) {
+        uint16_t* xt = at<uint16_t>(c, L.Xt16t);
+        KL(launch_transpose_bf16(c->stream, static_cast<const uint16_t*>(Xt), n_pad, T, ldx, xt, L.tcols));
+        fa.Xt16t = xt;
+        fa.tcols = L.tcols;
+    }
+    rc = run_fused(c, L, fa, &sh);
     if (rc) return rc;
-    KL(launch_kurt_finalize(c->stream, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, M,
+    KL(launch_kurt_finalize(c->stream, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, nullptr, M,
                             1.0 / static_cast<double>(T), alpha, ups));
     return read_status(c, L);
 }
@@ -535,10 +622,9 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     CK(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
     const bool bf16 = o.precision == ICA_BF16;
-    const int prec_iter = o.precision;
     const double inv_T = 1.0 / static_cast<double>(T);
     int* status = at<int>(c, L.status);
-    int* counts = at<int>(c, L.counts);
+    int* counts = at<int>(c, L.counts);  // [0], [1]: active counts (double-buffered); [2]: candidates
     float* B32 = at<float>(c, L.B32);
     float* Xt32 = at<float>(c, L.Xt32);
     uint16_t* Xt16 = at<uint16_t>(c, L.Xt16);
@@ -550,24 +636,29 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     double* ups = at<double>(c, L.ups);
     int* excl = at<int>(c, L.excl);
     int* cand = at<int>(c, L.cand);
+    int* cand_list = at<int>(c, L.slots) + 32;
     int* slots = at<int>(c, L.slots);
     double* G = at<double>(c, L.G);
     double* cstats = at<double>(c, L.comp_stats);
+    long long* crows = at<long long>(c, L.comp_rows);
     const int64_t ldx = L.ldx;
     const double tol_fp32 = tol > o.fp32_tol_floor ? tol : o.fp32_tol_floor;
     const double tol_iter = bf16 ? (o.stage_tol > tol ? o.stage_tol : tol) : tol_fp32;
     const double tol_ref = o.refine_tol > o.fp32_tol_floor ? o.refine_tol : o.fp32_tol_floor;
+    const int refine_iters = o.refine_iters < iters ? o.refine_iters : iters;
 
     CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(crows, 0, sizeof(long long) * 2 * (N + 1), s));
     c->launches = 0;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < K_NKINDS; ++k) {
         c->kind_ms[k] = 0.0;
         c->kind_flops[k] = 0.0;
         c->kind_n[k] = 0;
     }
     c->recs.clear();
     size_t ev_cursor = 0;
-    // run one fused launch, bracketed by CUDA events on the context stream when profiling
+    // one fused launch, bracketed by CUDA events on the context stream when profiling; the
+    // FLOP count uses the host's active count of the last read (an upper bound between reads)
     auto timed = [&](int kind, double flops, auto&& fn) -> int {
         if (!o.profile) return fn();
         const int e0 = ev_take(c, &ev_cursor), e1 = ev_take(c, &ev_cursor);
@@ -578,145 +669,230 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         c->recs.push_back({kind, flops, e0, e1});
         return r;
     };
+    // read the device count of the active rows (and the status word) back to the host
+    auto read_count = [&](const int* count_dev, int* out) -> int {
+        CK(cudaMemcpyAsync(c->host_i, count_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int r = map_device_status(c->host_i[1]);
+        if (r) return r;
+        *out = c->host_i[0];
+        return ICA_OK;
+    };
     cudaEvent_t fit_begin = nullptr, fit_end = nullptr;
     CK(cudaEventCreate(&fit_begin));
     CK(cudaEventCreate(&fit_end));
     CK(cudaEventRecord(fit_begin, s));
     const double dT = static_cast<double>(T);
-    std::string js = "{\"components\": [";
+    std::vector<int> comp_iters, comp_refine;
+    std::vector<std::vector<int>> comp_hist;
     int found = 0;
     for (int i = 0; i < n_components; ++i) {
         const int n = N - i;
         const int n_pad = round_up(n, 16);
         // reduction basis and X~ = G Xw (Section 3.3)
-        rc = deflation_basis_impl(c, L, W_out, i, N, G);
+        rc = timed(K_BASIS, 0.0, [&] { return deflation_basis_impl(c, L, W_out, i, N, G); });
         if (rc) return rc;
-        KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx));
+        const bool want_t = bf16 && tc_transposed(n_pad);
+        rc = timed(K_REDUCE, 0.0, [&] {
+            KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx,
+                                want_t ? at<uint16_t>(c, L.Xt16t) : nullptr, L.tcols));
+            return ICA_OK;
+        });
+        if (rc) return rc;
         // initial restarts
         KL(launch_init_restarts(s, seed, i, M, n, n_pad, o.B0 ? o.B0 + static_cast<int64_t>(i) * M * N : nullptr, N,
                                 B32));
         CK(cudaMemsetAsync(itc, 0, sizeof(int) * M, s));
         CK(cudaMemsetAsync(traj, 0, sizeof(float) * M * kTrajLen * 2, s));
-        KL(launch_iota(s, act[0], M));
-        int cur = 0, M_act = M, t = 0;
-        std::vector<int> active_hist;
+        KL(launch_iota(s, act[0], M, counts + 0));
+        FusedArgs fa;
+        fa.precision = o.precision;
+        fa.B32 = B32;
+        fa.ldb = n_pad;
+        fa.n_pad = n_pad;
+        fa.T = T;
+        fa.Xt32 = Xt32;
+        fa.Xt16 = Xt16;
+        fa.Xt16t = want_t ? at<uint16_t>(c, L.Xt16t) : nullptr;
+        fa.tcols = L.tcols;
+        fa.ldx = ldx;
+        fa.max_splits = o.max_splits;
         // fixed-point iterations with removal of converged rows (Algorithm 2, Section 3.2)
-        while (t < iters && M_act > 0) {
+        int cur = 0, M_host = M, t = 0;
+        std::vector<int> hist;
+        while (t < iters && M_host > 0) {
             StepShape sh;
-            rc = timed(K_ITER, 4.0 * n * M_act * dT, [&] {
-                return run_fused(c, L, prec_iter, false, B32, n_pad, act[cur], M_act, n_pad, T, Xt32, Xt16, ldx,
-                                 o.max_splits, &sh);
+            fa.act = act[cur];
+            fa.count_dev = counts + cur;
+            fa.M_act = M_host;
+            fa.moments_only = false;
+            fa.moments = t < kTrajLen;
+            rc = timed(K_ITER, 4.0 * n * M_host * dT, [&] { return run_fused(c, L, fa, &sh); });
+            if (rc) return rc;
+            rc = timed(K_FINALIZE, 0.0, [&] {
+                KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
+                                   n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
+                                   o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status));
+                return ICA_OK;
             });
             if (rc) return rc;
-            KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows, n_pad,
-                               n, act[cur], M_act, B32, n_pad, inv_T, tol_iter, flags, itc,
-                               o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status));
-            KL(launch_compact(s, flags, act[cur], M_act, act[cur ^ 1], counts, nullptr));
-            cur ^= 1;
-            CK(cudaMemcpyAsync(c->host_i, counts, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            rc = map_device_status(c->host_i[1]);
+            rc = timed(K_COMPACT, 0.0, [&] {
+                KL(launch_compact(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1),
+                                  crows + 2 * i));
+                return ICA_OK;
+            });
             if (rc) return rc;
-            M_act = c->host_i[0];
-            active_hist.push_back(M_act);
+            cur ^= 1;
             ++t;
+            if (sync_due(t)) {
+                rc = read_count(counts + cur, &M_host);
+                if (rc) return rc;
+                hist.push_back(M_host);
+            }
         }
         // kurtosis of every candidate: converged rows plus rows still running after `iters`
         {
             StepShape sh;
-            rc = timed(K_KURT, 2.0 * n * M * dT, [&] {
-                return run_fused(c, L, prec_iter, true, B32, n_pad, nullptr, M, n_pad, T, Xt32, Xt16, ldx,
-                                 o.max_splits, &sh);
-            });
+            fa.act = nullptr;
+            fa.count_dev = nullptr;
+            fa.M_act = M;
+            fa.moments_only = true;
+            rc = timed(K_KURT, 2.0 * n * M * dT, [&] { return run_fused(c, L, fa, &sh); });
             if (rc) return rc;
-            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, M, inv_T, alpha,
-                                    ups));
+            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, nullptr, M, inv_T,
+                                    alpha, ups));
         }
-        int refine_iters_used = 0, n_cand = 1;
+        int rt = 0;
         if (!bf16) {
-            KL(launch_argmax(s, ups, nullptr, nullptr, M, slots));
+            KL(launch_argmax(s, ups, nullptr, nullptr, nullptr, M, slots));
         } else {
             // distinct top-k candidates, FP32 refinement, FP32 kurtosis, argmax among them
             const int k = o.refine_topk;
-            KL(launch_select_clear(s, excl, M, cand, k));
-            for (int j = 0; j < k; ++j) {
-                KL(launch_argmax(s, ups, excl, nullptr, M, cand + j));
-                KL(launch_exclude(s, B32, n_pad, n, M, cand + j, excl, 1.0 - 1e-3));
-            }
-            CK(cudaMemcpyAsync(c->host_i + 2, cand, sizeof(int) * k, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            std::vector<int> cl;
-            for (int j = 0; j < k; ++j)
-                if (c->host_i[2 + j] >= 0) cl.push_back(c->host_i[2 + j]);
-            if (cl.empty()) return ICA_ERR_NONFINITE;
-            n_cand = static_cast<int>(cl.size());
-            memcpy(c->host_i + 2, cl.data(), sizeof(int) * cl.size());
-            CK(cudaMemcpyAsync(act[0], c->host_i + 2, sizeof(int) * n_cand, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(cand, c->host_i + 2, sizeof(int) * n_cand, cudaMemcpyHostToDevice, s));
-            int R = n_cand, rcur = 0, rt = 0;
-            while (rt < o.refine_iters && R > 0) {
-                StepShape sh;
-                rc = timed(K_REFINE, 4.0 * n * R * dT, [&] {
-                    return run_fused(c, L, ICA_FP32, false, B32, n_pad, act[rcur], R, n_pad, T, Xt32, Xt16, ldx,
-                                     o.max_splits, &sh);
-                });
-                if (rc) return rc;
-                KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
-                                   n_pad, n, act[rcur], R, B32, n_pad, inv_T, tol_ref, flags, itc, nullptr, kTrajLen,
-                                   status));
-                KL(launch_compact(s, flags, act[rcur], R, act[rcur ^ 1], counts, nullptr));
-                rcur ^= 1;
-                CK(cudaMemcpyAsync(c->host_i, counts, sizeof(int), cudaMemcpyDeviceToHost, s));
-                CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                rc = map_device_status(c->host_i[1]);
-                if (rc) return rc;
-                R = c->host_i[0];
-                ++rt;
-            }
-            refine_iters_used = rt;
-            StepShape sh;
-            rc = timed(K_REFKURT, 2.0 * n * n_cand * dT, [&] {
-                return run_fused(c, L, ICA_FP32, true, B32, n_pad, cand, n_cand, n_pad, T, Xt32, Xt16, ldx,
-                                 o.max_splits, &sh);
+            rc = timed(K_SELECT, 0.0, [&] {
+                KL(launch_select_clear(s, excl, M, cand, k));
+                for (int j = 0; j < k; ++j) {
+                    KL(launch_argmax(s, ups, excl, nullptr, nullptr, M, cand + j));
+                    KL(launch_exclude(s, B32, n_pad, n, M, cand + j, excl, 1.0 - 1e-3));
+                }
+                KL(launch_compact_cand(s, cand, k, act[0], cand_list, counts + 2));
+                return ICA_OK;
             });
             if (rc) return rc;
-            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, cand, n_cand, inv_T, alpha,
-                                    ups));
-            KL(launch_argmax(s, ups, nullptr, cand, n_cand, slots));
+            CK(cudaMemcpyAsync(counts + 0, counts + 2, sizeof(int), cudaMemcpyDeviceToDevice, s));
+            int rcur = 0, R_host = k;
+            fa.precision = ICA_FP32;
+            while (rt < refine_iters && R_host > 0) {
+                StepShape sh;
+                fa.act = act[rcur];
+                fa.count_dev = counts + rcur;
+                fa.M_act = R_host;
+                fa.moments_only = false;
+                fa.moments = false;
+                rc = timed(K_REFINE, 4.0 * n * R_host * dT, [&] { return run_fused(c, L, fa, &sh); });
+                if (rc) return rc;
+                rc = timed(K_FINALIZE, 0.0, [&] {
+                    KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
+                                       n_pad, n, act[rcur], counts + rcur, R_host, B32, n_pad, inv_T, tol_ref, flags,
+                                       itc, nullptr, kTrajLen, status));
+                    return ICA_OK;
+                });
+                if (rc) return rc;
+                rc = timed(K_COMPACT, 0.0, [&] {
+                    KL(launch_compact(s, flags, act[rcur], counts + rcur, R_host, act[rcur ^ 1], counts + (rcur ^ 1),
+                                      crows + 2 * i + 1));
+                    return ICA_OK;
+                });
+                if (rc) return rc;
+                rcur ^= 1;
+                ++rt;
+                if (sync_due(rt)) {
+                    rc = read_count(counts + rcur, &R_host);
+                    if (rc) return rc;
+                }
+            }
+            StepShape sh;
+            fa.act = cand_list;
+            fa.count_dev = counts + 2;
+            fa.M_act = k;
+            fa.moments_only = true;
+            rc = timed(K_REFKURT, 2.0 * n * k * dT, [&] { return run_fused(c, L, fa, &sh); });
+            if (rc) return rc;
+            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, cand_list, counts + 2, k,
+                                    inv_T, alpha, ups));
+            KL(launch_argmax(s, ups, nullptr, cand_list, counts + 2, k, slots));
         }
         // w_i = b_p G appended to W (Algorithm 2)
-        KL(launch_append(s, G, n, N, B32, n_pad, slots, alpha, ups, W_out, i, kurt_out + i, cstats + 4 * i));
-        CK(cudaMemcpyAsync(c->host_d, cstats + 4 * i, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        rc = map_device_status(c->host_i[1]);
+        rc = timed(K_APPEND, 0.0, [&] {
+            KL(launch_append(s, G, n, N, B32, n_pad, slots, alpha, ups, W_out, i, kurt_out + i, cstats + 4 * i));
+            return ICA_OK;
+        });
         if (rc) return rc;
-        harvest(c);
-        ev_cursor = 0;
-        const double p = c->host_d[0], a_p = c->host_d[1], u_p = c->host_d[2];
-        if (p < 0) return ICA_ERR_NONFINITE;
-        char buf[256];
-        snprintf(buf, sizeof(buf), "%s{\"i\": %d, \"iterations\": %d, \"winner\": %d, \"alpha\": %.12g, \"upsilon\": %.12g, "
-                 "\"refine_iterations\": %d, \"candidates\": %d, \"active\": [",
-                 i ? ", " : "", i + 1, t, static_cast<int>(p), a_p, u_p, refine_iters_used, n_cand);
-        js += buf;
-        for (size_t h = 0; h < active_hist.size(); ++h) {
-            snprintf(buf, sizeof(buf), "%s%d", h ? ", " : "", active_hist[h]);
-            js += buf;
+        comp_iters.push_back(t);
+        comp_refine.push_back(rt);
+        comp_hist.push_back(hist);
+        if (o.profile) {
+            CK(cudaStreamSynchronize(s));
+            harvest(c);
+            ev_cursor = 0;
         }
-        js += "]}";
-        // Gaussianity test (Eq. 3): the remaining components are Gaussian
-        if (o.gauss_test && u_p < 2.0 * (N - (i + 1) + 2) * (N - (i + 1) + 1) / static_cast<double>(T)) break;
         found = i + 1;
+        if (o.gauss_test) {
+            // Gaussianity test (Eq. 3): the remaining components are Gaussian
+            CK(cudaMemcpyAsync(c->host_d, cstats + 4 * i, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            rc = map_device_status(c->host_i[1]);
+            if (rc) return rc;
+            const double u_p = c->host_d[2];
+            if (u_p < 2.0 * (N - (i + 1) + 2) * (N - (i + 1) + 1) / static_cast<double>(T)) {
+                found = i;
+                break;
+            }
+        }
     }
     CK(cudaEventRecord(fit_end, s));
+    const int nst = found > 0 ? found : 1;
+    CK(cudaMemcpyAsync(c->host_d, cstats, sizeof(double) * 4 * nst, cudaMemcpyDeviceToHost, s));
+    std::vector<long long> rows_h(2 * (N + 1));
+    CK(cudaMemcpyAsync(rows_h.data(), crows, sizeof(long long) * 2 * (N + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaEventSynchronize(fit_end));
+    CK(cudaStreamSynchronize(s));
+    rc = map_device_status(c->host_i[1]);
+    if (rc) return rc;
     float fit_ms = 0.f;
     CK(cudaEventElapsedTime(&fit_ms, fit_begin, fit_end));
     cudaEventDestroy(fit_begin);
     cudaEventDestroy(fit_end);
+    // algorithmic FLOPs from the exact per-component counts of updated rows (4 n rows T)
+    double it_flops = 0.0, ref_flops = 0.0;
+    for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i) {
+        it_flops += 4.0 * (N - i) * static_cast<double>(rows_h[2 * i]) * dT;
+        ref_flops += 4.0 * (N - i) * static_cast<double>(rows_h[2 * i + 1]) * dT;
+    }
+    c->kind_flops[K_ITER] = it_flops;
+    c->kind_flops[K_REFINE] = ref_flops;
+    double kurt_flops = 0.0;
+    for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i) kurt_flops += 2.0 * (N - i) * static_cast<double>(M) * dT;
+    c->kind_flops[K_KURT] = kurt_flops;
+    std::string js = "{\"components\": [";
+    for (int i = 0; i < found; ++i) {
+        const double p = c->host_d[4 * i], a_p = c->host_d[4 * i + 1], u_p = c->host_d[4 * i + 2];
+        if (p < 0) return ICA_ERR_NONFINITE;
+        char buf[256];
+        snprintf(buf, sizeof(buf),
+                 "%s{\"i\": %d, \"iterations\": %d, \"winner\": %d, \"alpha\": %.12g, \"upsilon\": %.12g, "
+                 "\"refine_iterations\": %d, \"rows_updated\": %lld, \"refine_rows\": %lld, \"active\": [",
+                 i ? ", " : "", i + 1, comp_iters[i], static_cast<int>(p), a_p, u_p, comp_refine[i], rows_h[2 * i],
+                 rows_h[2 * i + 1]);
+        js += buf;
+        for (size_t h = 0; h < comp_hist[i].size(); ++h) {
+            snprintf(buf, sizeof(buf), "%s%d", h ? ", " : "", comp_hist[i][h]);
+            js += buf;
+        }
+        js += "]}";
+    }
     js += "], ";
     json_kv(js, "fit_ms", fit_ms);
     json_kv(js, "launches", static_cast<double>(c->launches));
@@ -726,6 +902,13 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         char buf[200];
         snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}", k ? ", " : "",
                  kKindName[k], c->kind_n[k], c->kind_ms[k], c->kind_flops[k]);
+        js += buf;
+    }
+    js += "}, \"phases\": {";
+    for (int k = 4; k < K_NKINDS; ++k) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}", k > 4 ? ", " : "", kKindName[k],
+                 c->kind_n[k], c->kind_ms[k]);
         js += buf;
     }
     js += "}, ";

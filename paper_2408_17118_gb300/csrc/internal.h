@@ -20,21 +20,23 @@ inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 // ---- k_small.cu ----
 cudaError_t launch_init_restarts(cudaStream_t s, uint64_t seed, int comp, int M, int n, int ldb,
                                  const float* B0, int B0_ld, float* B);
-cudaError_t launch_iota(cudaStream_t s, int* idx, int count);
+cudaError_t launch_iota(cudaStream_t s, int* idx, int count, int* count_dev);
 cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
-                            int part_rows, int n_pad, int n, const int* act_idx, int M_act, float* B32, int ldb,
-                            double inv_T, double tol, int* flags, int* iters, float* traj, int t_iter,
-                            int* status);
+                            int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
+                            float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
+                            int t_iter, int* status);
 cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                            int part_rows, int n_pad, int M, const float* B, double inv_T, float* Bnew,
                            float* moments);
-cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, int count, int* act_out,
-                           int* count_out_dev, int* count_out_host);
+cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, const int* count_in_dev,
+                           int count_host, int* act_out, int* count_out_dev, long long* rows_accum);
+cudaError_t launch_compact_cand(cudaStream_t s, const int* cand, int k, int* list_a, int* list_b, int* count_dev);
 cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int splits, int part_rows,
-                                 const int* act_idx, int count, double inv_T, double* alpha, double* ups);
+                                 const int* act_idx, const int* count_dev, int count, double inv_T, double* alpha,
+                                 double* ups);
 cudaError_t launch_select_clear(cudaStream_t s, int* excluded, int M, int* cand, int kmax);
 cudaError_t launch_argmax(cudaStream_t s, const double* ups, const int* excluded, const int* subset,
-                          int count, int* out_slot);
+                          const int* count_dev, int count, int* out_slot);
 cudaError_t launch_exclude(cudaStream_t s, const float* B32, int ldb, int n, int M, const int* sel_slot,
                            int* excluded, double cos_thresh);
 cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
@@ -61,26 +63,39 @@ cudaError_t launch_pad_cols(cudaStream_t s, const double* W, int k, int N, int n
 // ---- k_reduce.cu ----
 cudaError_t launch_rows_gemm(cudaStream_t s, const double* G, int n, int n_pad, int N, const float* X,
                              int64_t T, int64_t ldxin, const double* bias, float* out32, int64_t ld32,
-                             uint16_t* out16, int64_t ld16);
+                             uint16_t* out16, int64_t ld16, uint16_t* out16t = nullptr, int64_t ld16t = 0);
+cudaError_t launch_transpose_bf16(cudaStream_t s, const uint16_t* Xn, int n_pad, int64_t T, int64_t ldx,
+                                  uint16_t* Xt, int64_t ldt);
+inline int round_up64cols(int n_pad) { return (n_pad + 63) / 64 * 64; }
 
 // ---- k_fp32.cu ----
 size_t fp32_smem_bytes(int n_pad);
 cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B32, int ldb,
-                              const int* act_idx, int M_act, const float* Xt, int64_t ldx, int n_pad,
-                              int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
-                              int part_rows);
+                              const int* act_idx, const int* count_dev, int M_act, const float* Xt, int64_t ldx,
+                              int n_pad, int64_t T, int splits, int chunks_per_split, float* part_acc,
+                              float* part_mom, int part_rows);
+constexpr int kFp32SmallRows = 16;  // rows of the small-batch FP32 kernel (one CTA row tile)
+size_t fp32_small_smem_bytes(int n_pad);
+cudaError_t launch_fused_fp32_small(cudaStream_t s, bool moments_only, const float* B32, int ldb,
+                                    const int* act_idx, const int* count_dev, int M_act_host, const float* Xt,
+                                    int64_t ldx, int n_pad, int64_t T, int splits, int chunks_per_split,
+                                    float* part_acc, float* part_mom, int part_rows);
 
 // ---- k_tc.cu ----
 int tc_chunk(int n_pad);
+bool tc_transposed(int n_pad);
 size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out);
-cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, const CUtensorMap& xmap, const float* B32,
-                            int ldb, const int* act_idx, int M_act, int n_pad, int64_t T, int splits,
-                            int chunks_per_split, int total_chunks, float* part_acc, float* part_mom,
-                            int part_rows, int* status);
+// xmap: X~ (n_pad x T, samples contiguous), box {64, n_pad}. xmap_t (optional, n_pad <= 128):
+// X~^T (T x round_up64cols(n_pad), reduced index contiguous), box {64, tc_chunk(n_pad)}; when
+// given, the first product reads it as a K-major operand.
+cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
+                            const CUtensorMap* xmap_t, const float* B32, int ldb, const int* act_idx,
+                            const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
+                            int total_chunks, float* part_acc, float* part_mom, int part_rows, int* status);
 
 // ---- k_plain.cu ----
-cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx, int M_act,
-                               int n_pad, float* out);
+cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx,
+                               const int* count_dev, int M_act, int n_pad, float* out);
 cudaError_t launch_cube_inplace(cudaStream_t s, float* Z, int rows, int64_t T, int64_t ldz);
 cudaError_t launch_row_moments(cudaStream_t s, const float* Z, int rows, int64_t T, int64_t ldz,
                                float* part_mom);

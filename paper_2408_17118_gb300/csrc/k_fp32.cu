@@ -20,7 +20,8 @@ size_t fp32_smem_bytes(int n_pad) {
 
 template <bool MOMENTS_ONLY>
 __global__ void __launch_bounds__(256) fused_fp32_kernel(const float* __restrict__ B32, int ldb,
-                                                         const int* __restrict__ act_idx, int M_act,
+                                                         const int* __restrict__ act_idx,
+                                                         const int* __restrict__ count_dev, int M_act_host,
                                                          const float* __restrict__ Xt, int64_t ldx, int n_pad,
                                                          int64_t T, int chunks_per_split, float* __restrict__ part_acc,
                                                          float* __restrict__ part_mom, int part_rows) {
@@ -31,6 +32,8 @@ __global__ void __launch_bounds__(256) fused_fp32_kernel(const float* __restrict
                                        // restarts XOR-swizzled by sample/4 against bank conflicts)
     const int split = blockIdx.x, tile = blockIdx.y;
     const int m0 = tile * F_MT;
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    if (m0 >= M_act) return;  // grid sized for an upper bound of the active count
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int kj = n_pad / 16;
 
@@ -118,11 +121,10 @@ __global__ void __launch_bounds__(256) fused_fp32_kernel(const float* __restrict
                 const float zv[4] = {zc.x, zc.y, zc.z, zc.w};
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    if (j < kj) {
-                        const float x = Xs[(tx + 16 * j) * F_XS + t];
+                    if (j >= kj) break;  // uniform exit: no predicated-off work for small n
+                    const float x = Xs[(tx + 16 * j) * F_XS + t];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(zv[i], x, acc[i][j]);
-                    }
+                    for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(zv[i], x, acc[i][j]);
                 }
             }
         }
@@ -150,15 +152,161 @@ __global__ void __launch_bounds__(256) fused_fp32_kernel(const float* __restrict
         }
         if (!MOMENTS_ONLY) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (j < kj) part_acc[prow * n_pad + tx + 16 * j] = acc[i][j];
+            for (int j = 0; j < 16; ++j) {
+                if (j >= kj) break;
+                part_acc[prow * n_pad + tx + 16 * j] = acc[i][j];
+            }
         }
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Small-batch variant for at most 16 restart rows (the FP32 refinement of a few distinct
+// candidates): one row per thread row, 16 rows x 64 samples per chunk, so no tensor work is
+// spent on empty rows and the launch is bound by reading X~ once.
+// ------------------------------------------------------------------------------------------
+constexpr int S_MT = 16;
+constexpr int S_ZS = S_MT + 1;  // padded z^3 row stride (bank conflicts)
+
+size_t fp32_small_smem_bytes(int n_pad) {
+    return sizeof(float) * (static_cast<size_t>(S_MT) * n_pad + static_cast<size_t>(n_pad) * F_XS +
+                            static_cast<size_t>(F_TC) * S_ZS);
+}
+
+template <bool MOMENTS_ONLY>
+__global__ void __launch_bounds__(256) fused_fp32_small_kernel(const float* __restrict__ B32, int ldb,
+                                                               const int* __restrict__ act_idx,
+                                                               const int* __restrict__ count_dev, int M_act_host,
+                                                               const float* __restrict__ Xt, int64_t ldx, int n_pad,
+                                                               int64_t T, int chunks_per_split,
+                                                               float* __restrict__ part_acc,
+                                                               float* __restrict__ part_mom, int part_rows) {
+    extern __shared__ __align__(16) float ssm[];
+    float* Bs = ssm;                  // [S_MT][n_pad]
+    float* Xs = Bs + S_MT * n_pad;    // [n_pad][F_XS]
+    float* Zs = Xs + n_pad * F_XS;    // [F_TC][S_ZS]
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    const int split = blockIdx.x;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty = restart row, tx = sample group
+    const int kj = n_pad / 16;
+    for (int e = tid; e < S_MT * n_pad; e += 256) {
+        const int m = e / n_pad, k = e % n_pad;
+        float v = 0.f;
+        if (m < M_act) {
+            const int r = act_idx ? act_idx[m] : m;
+            v = B32[static_cast<int64_t>(r) * ldb + k];
+        }
+        Bs[e] = v;
+    }
+    const int64_t c_begin = static_cast<int64_t>(split) * chunks_per_split;
+    const int64_t total_chunks = (T + F_TC - 1) / F_TC;
+    const int64_t c_end = c_begin + chunks_per_split < total_chunks ? c_begin + chunks_per_split : total_chunks;
+    float acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+    float m2 = 0.f, m4 = 0.f, mq = 0.f;
+    for (int64_t c = c_begin; c < c_end; ++c) {
+        const int64_t t0 = c * F_TC;
+        __syncthreads();
+        for (int e = tid; e < n_pad * (F_TC / 4); e += 256) {
+            const int k = e / (F_TC / 4), c4 = (e % (F_TC / 4)) * 4;
+            const int64_t t = t0 + c4;
+            const float* src = Xt + static_cast<int64_t>(k) * ldx + t;
+            float4 v;
+            if (t + 3 < T) {
+                v = *reinterpret_cast<const float4*>(src);
+            } else {
+                v.x = t < T ? src[0] : 0.f;
+                v.y = t + 1 < T ? src[1] : 0.f;
+                v.z = t + 2 < T ? src[2] : 0.f;
+                v.w = t + 3 < T ? src[3] : 0.f;
+            }
+            *reinterpret_cast<float4*>(&Xs[k * F_XS + c4]) = v;
+        }
+        __syncthreads();
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < n_pad; ++k) {
+            const float b = Bs[ty * n_pad + k];
+            const float4 x = *reinterpret_cast<const float4*>(&Xs[k * F_XS + tx * 4]);
+            z[0] = fmaf(b, x.x, z[0]);
+            z[1] = fmaf(b, x.y, z[1]);
+            z[2] = fmaf(b, x.z, z[2]);
+            z[3] = fmaf(b, x.w, z[3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float z2 = z[j] * z[j];
+            m2 += z2;
+            m4 = fmaf(z2, z2, m4);
+            if (MOMENTS_ONLY) {
+                const float e = (t0 + tx * 4 + j < T) ? z2 - 1.f : 0.f;
+                mq = fmaf(e, e, mq);
+            } else {
+                Zs[(tx * 4 + j) * S_ZS + ty] = z2 * z[j];
+            }
+        }
+        if (!MOMENTS_ONLY) {
+            __syncthreads();
+            for (int t = 0; t < F_TC; ++t) {
+                const float zc = Zs[t * S_ZS + ty];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (j >= kj) break;  // uniform exit: no predicated-off work for small n
+                    acc[j] = fmaf(zc, Xs[(tx + 16 * j) * F_XS + t], acc[j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        m4 += __shfl_xor_sync(0xffffffffu, m4, o);
+        mq += __shfl_xor_sync(0xffffffffu, mq, o);
+    }
+    if (ty >= M_act) return;
+    const int64_t prow = static_cast<int64_t>(split) * part_rows + ty;
+    if (tx == 0) {
+        part_mom[prow * 4 + 0] = m2;
+        part_mom[prow * 4 + 1] = m4;
+        part_mom[prow * 4 + 2] = mq;
+        part_mom[prow * 4 + 3] = 0.f;
+    }
+    if (!MOMENTS_ONLY) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j >= kj) break;
+            part_acc[prow * n_pad + tx + 16 * j] = acc[j];
+        }
+    }
+}
+
+cudaError_t launch_fused_fp32_small(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
+                                    const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
+                                    int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
+                                    int part_rows) {
+    const size_t smem = fp32_small_smem_bytes(n_pad);
+    cudaError_t e;
+    if (moments_only) {
+        e = cudaFuncSetAttribute(fused_fp32_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        fused_fp32_small_kernel<true><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
+                                                                n_pad, T, chunks_per_split, part_acc, part_mom,
+                                                                part_rows);
+    } else {
+        e = cudaFuncSetAttribute(fused_fp32_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        fused_fp32_small_kernel<false><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
+                                                                 n_pad, T, chunks_per_split, part_acc, part_mom,
+                                                                 part_rows);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
-                              int M_act, const float* Xt, int64_t ldx, int n_pad, int64_t T, int splits,
-                              int chunks_per_split, float* part_acc, float* part_mom, int part_rows) {
+                              const int* count_dev, int M_act, const float* Xt, int64_t ldx, int n_pad, int64_t T,
+                              int splits, int chunks_per_split, float* part_acc, float* part_mom, int part_rows) {
     const size_t smem = fp32_smem_bytes(n_pad);
     const dim3 grid(splits, (M_act + F_MT - 1) / F_MT);
     cudaError_t e;
@@ -166,13 +314,13 @@ cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B3
         e = cudaFuncSetAttribute(fused_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        fused_fp32_kernel<true><<<grid, 256, smem, s>>>(B32, ldb, act_idx, M_act, Xt, ldx, n_pad, T,
+        fused_fp32_kernel<true><<<grid, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act, Xt, ldx, n_pad, T,
                                                         chunks_per_split, part_acc, part_mom, part_rows);
     } else {
         e = cudaFuncSetAttribute(fused_fp32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        fused_fp32_kernel<false><<<grid, 256, smem, s>>>(B32, ldb, act_idx, M_act, Xt, ldx, n_pad, T,
+        fused_fp32_kernel<false><<<grid, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act, Xt, ldx, n_pad, T,
                                                          chunks_per_split, part_acc, part_mom, part_rows);
     }
     return cudaGetLastError();

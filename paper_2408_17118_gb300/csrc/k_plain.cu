@@ -6,19 +6,26 @@
 
 namespace ica {
 
-// out (M_act x n_pad) = rows act_idx[j] of B32.
+// out (M_act x n_pad) = rows act_idx[j] of B32 for j < *count_dev, zero rows beyond (the
+// products then run on an upper bound of the active count).
 __global__ void gather_rows_kernel(const float* __restrict__ B32, int ldb, const int* __restrict__ act_idx,
-                                   int M_act, int n_pad, float* __restrict__ out) {
+                                   const int* __restrict__ count_dev, int M_act, int n_pad, float* __restrict__ out) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= static_cast<int64_t>(M_act) * n_pad) return;
+    const int count = count_dev ? *count_dev : M_act;
     const int j = static_cast<int>(i / n_pad), k = static_cast<int>(i % n_pad);
+    if (j >= count) {
+        out[i] = 0.f;
+        return;
+    }
     const int r = act_idx ? act_idx[j] : j;
     out[i] = B32[static_cast<int64_t>(r) * ldb + k];
 }
-cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx, int M_act, int n_pad,
-                               float* out) {
+cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx, const int* count_dev,
+                               int M_act, int n_pad, float* out) {
     const int64_t n = static_cast<int64_t>(M_act) * n_pad;
-    gather_rows_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(B32, ldb, act_idx, M_act, n_pad, out);
+    gather_rows_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(B32, ldb, act_idx, count_dev, M_act,
+                                                                              n_pad, out);
     return cudaGetLastError();
 }
 

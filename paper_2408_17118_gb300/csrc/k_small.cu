@@ -64,31 +64,71 @@ cudaError_t launch_init_restarts(cudaStream_t s, uint64_t seed, int comp, int M,
     return cudaGetLastError();
 }
 
-__global__ void iota_kernel(int* idx, int count) {
+__global__ void iota_kernel(int* idx, int count, int* count_dev) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) idx[i] = i;
+    if (i == 0 && count_dev) *count_dev = count;
 }
-cudaError_t launch_iota(cudaStream_t s, int* idx, int count) {
-    iota_kernel<<<(count + 255) / 256, 256, 0, s>>>(idx, count);
+cudaError_t launch_iota(cudaStream_t s, int* idx, int count, int* count_dev) {
+    iota_kernel<<<(count + 255) / 256, 256, 0, s>>>(idx, count, count_dev);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------
-// Normalise / converge / remove (Algorithm 2 inner loop; Section 3.2). One warp per active
-// row j (restart r = act_idx[j]): the split-T partial sums of (Z o Z o Z) X~^T are added in a
-// fixed order (deterministic), b' = acc / T - 3 b, b' <- b' / ||b'||,
-// d = min(||b' - b||, ||b' + b||); the row stays active iff d > tol. Rows whose update is
-// zero or non-finite are retired and flagged in the status word. The kurtosis of the
-// pre-update row and d are kept for the first kTrajLen iterations (restart features).
+// Normalise / converge / remove (Algorithm 2 inner loop; Section 3.2). One CTA of NW warps per
+// active row j (restart r = act_idx[j]); rows j >= *count_dev exit (the grid is sized for an
+// upper bound). The split-T partial sums of (Z o Z o Z) X~^T are added deterministically: warp w
+// sums splits w, w + NW, ... in order, then warp 0 adds the NW warp sums in order. Then
+// b' = acc / T - 3 b, b' <- b' / ||b'||, d = min(||b' - b||, ||b' + b||); the row stays active
+// iff d > tol. Rows whose update is zero or non-finite are retired and flagged in the status
+// word. For the first kTrajLen iterations the kurtosis of the pre-update row and d are kept as
+// per-restart features.
 // ------------------------------------------------------------------------------------------
-__global__ void finalize_kernel(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
-                                int splits, int part_rows, int n_pad, int n, const int* __restrict__ act_idx,
-                                int M_act, float* __restrict__ B32, int ldb, double inv_T, double tol,
-                                int* __restrict__ flags, int* __restrict__ iters, float* __restrict__ traj,
-                                int t_iter, int* status) {
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
+                                                           const float* __restrict__ part_mom, int splits,
+                                                           int part_rows, int n_pad, int n,
+                                                           const int* __restrict__ act_idx,
+                                                           const int* __restrict__ count_dev, int M_act_host,
+                                                           float* __restrict__ B32, int ldb, double inv_T, double tol,
+                                                           int* __restrict__ flags, int* __restrict__ iters,
+                                                           float* __restrict__ traj, int t_iter, int* status) {
+    extern __shared__ double fin_red[];  // [NW][n_pad] then [NW][2]
+    double* red = fin_red;
+    double* redm = fin_red + NW * n_pad;
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    const int j = blockIdx.x;
     if (j >= M_act) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool want_traj = traj && t_iter < kTrajLen;
+    {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        double m2 = 0.0, m4 = 0.0;
+#pragma unroll 4
+        for (int sp = w; sp < splits; sp += NW) {
+            const float* p = part_acc + (static_cast<int64_t>(sp) * part_rows + j) * n_pad;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = lane + 32 * q;
+                if (k < n_pad) acc[q] += static_cast<double>(p[k]);
+            }
+            if (want_traj && lane == 0) {
+                m2 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 0];
+                m4 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 1];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (k < n_pad) red[w * n_pad + k] = acc[q];
+        }
+        if (lane == 0) {
+            redm[2 * w] = m2;
+            redm[2 * w + 1] = m4;
+        }
+    }
+    __syncthreads();
+    if (w != 0) return;
     const int r = act_idx ? act_idx[j] : j;
     double u[8], b[8];
     double ss = 0.0;
@@ -99,8 +139,7 @@ __global__ void finalize_kernel(const float* __restrict__ part_acc, const float*
         b[q] = 0.0;
         if (k < n) {
             double acc = 0.0;
-            for (int sp = 0; sp < splits; ++sp)
-                acc += static_cast<double>(part_acc[(static_cast<int64_t>(sp) * part_rows + j) * n_pad + k]);
+            for (int ww = 0; ww < NW; ++ww) acc += red[ww * n_pad + k];
             b[q] = static_cast<double>(B32[static_cast<int64_t>(r) * ldb + k]);
             u[q] = acc * inv_T - 3.0 * b[q];
             ss += u[q] * u[q];
@@ -130,11 +169,11 @@ __global__ void finalize_kernel(const float* __restrict__ part_acc, const float*
         flags[j] = (!bad && d > tol) ? 1 : 0;
         iters[r] += 1;
         if (bad) atomicOr(status, DEV_NONFINITE);
-        if (traj && t_iter < kTrajLen) {
+        if (want_traj) {
             double m2 = 0.0, m4 = 0.0;
-            for (int sp = 0; sp < splits; ++sp) {
-                m2 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 0];
-                m4 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 1];
+            for (int ww = 0; ww < NW; ++ww) {
+                m2 += redm[2 * ww];
+                m4 += redm[2 * ww + 1];
             }
             m2 *= inv_T;
             m4 *= inv_T;
@@ -145,14 +184,25 @@ __global__ void finalize_kernel(const float* __restrict__ part_acc, const float*
     }
 }
 
+// Rows with many splits and few rows (the refinement) get 32 warps each, others 8.
 cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
-                            int part_rows, int n_pad, int n, const int* act_idx, int M_act, float* B32, int ldb,
-                            double inv_T, double tol, int* flags, int* iters, float* traj, int t_iter,
-                            int* status) {
-    const int threads = 256;
-    const int blocks = (M_act * 32 + threads - 1) / threads;
-    finalize_kernel<<<blocks, threads, 0, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, M_act,
-                                                B32, ldb, inv_T, tol, flags, iters, traj, t_iter, status);
+                            int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
+                            float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
+                            int t_iter, int* status) {
+    if (M_act <= 64 && splits > 16) {
+        const size_t smem = sizeof(double) * 32 * (n_pad + 2);
+        cudaError_t e = cudaFuncSetAttribute(finalize_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        finalize_kernel<32><<<M_act, 1024, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
+                                                      count_dev, M_act, B32, ldb, inv_T, tol, flags, iters, traj,
+                                                      t_iter, status);
+    } else {
+        const size_t smem = sizeof(double) * 8 * (n_pad + 2);
+        finalize_kernel<8><<<M_act, 256, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
+                                                    count_dev, M_act, B32, ldb, inv_T, tol, flags, iters, traj,
+                                                    t_iter, status);
+    }
     return cudaGetLastError();
 }
 
@@ -191,9 +241,12 @@ cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* p
 // One CTA of 1024 threads; thread t owns a contiguous slice of the list.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) compact_kernel(const int* __restrict__ flags, const int* __restrict__ act_in,
-                                                       int count, int* __restrict__ act_out, int* count_out_dev,
-                                                       int* count_out_host) {
+                                                       const int* __restrict__ count_in_dev, int count_host,
+                                                       int* __restrict__ act_out, int* count_out_dev,
+                                                       long long* rows_accum) {
     __shared__ int warp_tot[32];
+    const int count = count_in_dev ? *count_in_dev : count_host;
+    if (threadIdx.x == 0 && rows_accum) *rows_accum += count;  // rows this iteration updated
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (count + 1023) / 1024;
     const int b = t * per, e = min(count, b + per);
@@ -221,16 +274,29 @@ __global__ void __launch_bounds__(1024) compact_kernel(const int* __restrict__ f
     int pos = warp_tot[w] + incl - local;
     for (int i = b; i < e; ++i)
         if (flags[i]) act_out[pos++] = act_in ? act_in[i] : i;
-    if (t == 1023) {
-        const int total = warp_tot[31] + incl;
-        *count_out_dev = total;
-        if (count_out_host) *reinterpret_cast<volatile int*>(count_out_host) = total;
-    }
+    if (t == 1023) *count_out_dev = warp_tot[31] + incl;
 }
 
-cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, int count, int* act_out,
-                           int* count_out_dev, int* count_out_host) {
-    compact_kernel<<<1, 1024, 0, s>>>(flags, act_in, count, act_out, count_out_dev, count_out_host);
+cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, const int* count_in_dev,
+                           int count_host, int* act_out, int* count_out_dev, long long* rows_accum) {
+    compact_kernel<<<1, 1024, 0, s>>>(flags, act_in, count_in_dev, count_host, act_out, count_out_dev, rows_accum);
+    return cudaGetLastError();
+}
+
+// Valid entries (>= 0) of the candidate slots, in order, to two lists and a device count.
+__global__ void compact_cand_kernel(const int* cand, int k, int* list_a, int* list_b, int* count_dev) {
+    if (threadIdx.x != 0) return;
+    int c = 0;
+    for (int j = 0; j < k; ++j)
+        if (cand[j] >= 0) {
+            list_a[c] = cand[j];
+            list_b[c] = cand[j];
+            ++c;
+        }
+    *count_dev = c;
+}
+cudaError_t launch_compact_cand(cudaStream_t s, const int* cand, int k, int* list_a, int* list_b, int* count_dev) {
+    compact_cand_kernel<<<1, 32, 0, s>>>(cand, k, list_a, list_b, count_dev);
     return cudaGetLastError();
 }
 
@@ -253,8 +319,9 @@ __device__ __forceinline__ void alpha_upsilon(double m2, double m4, double q, do
 }
 
 __global__ void kurt_finalize_kernel(const float* __restrict__ part_mom, int splits, int part_rows,
-                                     const int* __restrict__ act_idx, int count, double inv_T,
-                                     double* __restrict__ alpha, double* __restrict__ ups) {
+                                     const int* __restrict__ act_idx, const int* __restrict__ count_dev, int count_host,
+                                     double inv_T, double* __restrict__ alpha, double* __restrict__ ups) {
+    const int count = count_dev ? *count_dev : count_host;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
     double m2 = 0.0, m4 = 0.0, q = 0.0;
@@ -272,9 +339,10 @@ __global__ void kurt_finalize_kernel(const float* __restrict__ part_mom, int spl
 }
 
 cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int splits, int part_rows,
-                                 const int* act_idx, int count, double inv_T, double* alpha, double* ups) {
-    kurt_finalize_kernel<<<(count + 255) / 256, 256, 0, s>>>(part_mom, splits, part_rows, act_idx, count, inv_T,
-                                                              alpha, ups);
+                                 const int* act_idx, const int* count_dev, int count, double inv_T, double* alpha,
+                                 double* ups) {
+    kurt_finalize_kernel<<<(count + 255) / 256, 256, 0, s>>>(part_mom, splits, part_rows, act_idx, count_dev, count,
+                                                              inv_T, alpha, ups);
     return cudaGetLastError();
 }
 
@@ -303,9 +371,11 @@ __device__ __forceinline__ bool better(double u, int i, double bu, int bi) {
 // subset == nullptr: candidates are rows 0..count-1; else rows subset[0..count) (entries < 0
 // are skipped). Writes the winning row (or -1) to *out_slot.
 __global__ void __launch_bounds__(1024) argmax_kernel(const double* __restrict__ ups, const int* __restrict__ excluded,
-                                                      const int* __restrict__ subset, int count, int* out_slot) {
+                                                      const int* __restrict__ subset, const int* __restrict__ count_dev,
+                                                      int count_host, int* out_slot) {
     __shared__ double su[32];
     __shared__ int si[32];
+    const int count = count_dev ? *count_dev : count_host;
     double bu = -INFINITY;
     int bi = -1;
     for (int j = threadIdx.x; j < count; j += blockDim.x) {
@@ -351,9 +421,9 @@ __global__ void __launch_bounds__(1024) argmax_kernel(const double* __restrict__
     }
 }
 
-cudaError_t launch_argmax(cudaStream_t s, const double* ups, const int* excluded, const int* subset, int count,
-                          int* out_slot) {
-    argmax_kernel<<<1, 1024, 0, s>>>(ups, excluded, subset, count, out_slot);
+cudaError_t launch_argmax(cudaStream_t s, const double* ups, const int* excluded, const int* subset,
+                          const int* count_dev, int count, int* out_slot) {
+    argmax_kernel<<<1, 1024, 0, s>>>(ups, excluded, subset, count_dev, count, out_slot);
     return cudaGetLastError();
 }
 

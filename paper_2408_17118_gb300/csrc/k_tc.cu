@@ -10,11 +10,13 @@
 // product (contraction over the reduced dimension) and the K-major B operand of the second
 // (contraction over samples). The epilogue also accumulates sum z^2 and sum z^4 per restart
 // (and sum (z^2 - 1)^2 in the moments-only variant, which skips the second product and is
-// used for the kurtosis of candidates, Eq. 2).
+// used for the kurtosis of candidates, Eq. 2); the update variant accumulates the moments
+// only when asked (the first iterations, whose kurtosis trajectory is kept per restart).
 //
-// Warp roles (320 threads): warp 0 issues TMA loads, warp 1 allocates TMEM and issues MMAs
-// (one thread), warps 2..9 convert TMEM rows (warp w reads TMEM lanes 32*(w%4).., half
-// (w-2)/4 of the chunk's columns). Every wait is bounded (ICA_WAIT_NS): on timeout the CTA
+// Warp roles (576 threads): warp 0 issues TMA loads, warp 1 allocates TMEM and issues MMAs
+// (one thread), warps 2..17 convert TMEM rows (warp w reads TMEM lanes 32*(w%4).., quarter
+// (w-2)/4 of the chunk's columns: four warps per scheduler keep the cube conversion, which at
+// small n is the longest stage of a chunk, off the critical path of the tensor pipe). Every wait is bounded (ICA_WAIT_NS): on timeout the CTA
 // raises the device status word, drains its outstanding copies and MMAs, frees TMEM and
 // returns.
 #include "common.cuh"
@@ -22,28 +24,44 @@
 
 namespace ica {
 
-int tc_chunk(int n_pad) { return n_pad <= 128 ? 128 : 64; }
+// Samples per chunk and number of Z / P buffers: with NB buffers the MMA thread issues the
+// first product NB-1 chunks ahead of the second, so the cube conversion of one chunk overlaps
+// the products of the next ones. TMEM holds D2 (n_pad columns) plus NB Z buffers of TC columns;
+// shared memory must keep at least NB + 1 X~ stages in flight (NB stages are pinned by chunks
+// waiting for their second product).
+// Chunks are as wide as TMEM allows (fixed costs per chunk - barrier round trips and commits -
+// dominate at small n): n_pad <= 64 uses 192 samples (accumulator 64 columns + 2 x 192).
+int tc_chunk(int n_pad) { return n_pad <= 64 ? 192 : 64; }
+int tc_buffers(int n_pad) { return 2; }
+// Optional K-major operand for the first product from a transposed copy of X~. Measured on GB300
+// the MN-major read of the X~ tile is as fast, so the copy is not used (saves its traffic).
+bool tc_transposed(int n_pad) { return false; }
 
 namespace {
 constexpr int kBars = 40;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kScratchBytes = 8192u;  // barriers, TMEM slot, moment exchange
 struct TcLayout {
-    uint32_t a_bytes, xsub_bytes, xstage_bytes, p_bytes, stages, off_x, off_p, off_bar, total;
+    uint32_t a_bytes, xsub_bytes, xn_bytes, xstage_bytes, p_bytes, stages, off_x, off_p, off_bar, total;
 };
-TcLayout tc_layout(int n_pad, bool moments_only, int TC) {
+TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, bool KT) {
     TcLayout L{};
     L.a_bytes = static_cast<uint32_t>((n_pad + 63) / 64) * 16384u;
     L.xsub_bytes = static_cast<uint32_t>(n_pad) * 128u;
-    L.xstage_bytes = static_cast<uint32_t>(TC / 64) * L.xsub_bytes;
+    L.xn_bytes = static_cast<uint32_t>(TC / 64) * L.xsub_bytes;  // X~ tile: n_pad rows x TC samples
+    // + X~^T tile: ceil(n_pad / 64) K-blocks of TC rows x 128 bytes
+    L.xstage_bytes = L.xn_bytes + (KT ? static_cast<uint32_t>((n_pad + 63) / 64) * static_cast<uint32_t>(TC) * 128u : 0u);
     L.p_bytes = moments_only ? 0u : static_cast<uint32_t>(TC / 64) * 16384u;
-    const uint32_t fixed = L.a_bytes + 2u * L.p_bytes + 4096u + 1024u;  // + barriers/scratch + alignment
+    const uint32_t fixed = L.a_bytes + NB * L.p_bytes + kScratchBytes + 1024u;  // + scratch + alignment
     const uint32_t budget = 227u * 1024u;
     uint32_t st = (budget - fixed) / L.xstage_bytes;
     if (st > 8) st = 8;
     L.stages = st;
     L.off_x = L.a_bytes;
     L.off_p = L.off_x + st * L.xstage_bytes;
-    L.off_bar = L.off_p + 2u * L.p_bytes;
-    L.total = L.off_bar + 4096u + 1024u;
+    L.off_bar = L.off_p + NB * L.p_bytes;
+    L.total = L.off_bar + kScratchBytes + 1024u;
     // one CTA per SM: the kernel allocates all 512 TMEM columns
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;
     return L;
@@ -51,7 +69,7 @@ TcLayout tc_layout(int n_pad, bool moments_only, int TC) {
 }  // namespace
 
 size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out) {
-    const TcLayout L = tc_layout(n_pad, moments_only, tc_chunk(n_pad));
+    const TcLayout L = tc_layout(n_pad, moments_only, tc_chunk(n_pad), tc_buffers(n_pad), tc_transposed(n_pad));
     if (stages_out) *stages_out = static_cast<int>(L.stages);
     return L.total;
 }
@@ -71,36 +89,40 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <int TC, bool MOMENTS_ONLY>
-__global__ void __launch_bounds__(320, 1)
-    fused_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restrict__ B32, int ldb,
-                    const int* __restrict__ act_idx, int M_act, int n_pad, int64_t T, int chunks_per_split,
-                    int total_chunks, int stages, uint32_t a_bytes, uint32_t xsub_bytes, uint32_t off_x,
+template <int TC, int NB, bool KT, bool MOMENTS_ONLY, bool MOMENTS>
+__global__ void __launch_bounds__(kThreads, 1)
+    fused_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap_t,
+                    const float* __restrict__ B32, int ldb,
+                    const int* __restrict__ act_idx, const int* __restrict__ count_dev, int M_act_host, int n_pad, int64_t T, int chunks_per_split,
+                    int total_chunks, int stages, uint32_t a_bytes, uint32_t xsub_bytes, uint32_t xstage_bytes,
+                    uint32_t off_x,
                     uint32_t off_p, uint32_t off_bar, float* __restrict__ part_acc, float* __restrict__ part_mom,
                     int part_rows, int* status) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_u32 = smem_u32(smem_raw);
     const uint32_t base_u32 = (raw_u32 + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_u32 - raw_u32);
-    const uint32_t xstage_bytes = static_cast<uint32_t>(TC / 64) * xsub_bytes;
+    const uint32_t xn_bytes = static_cast<uint32_t>(TC / 64) * xsub_bytes;  // X~^T tile follows at xn_bytes
     constexpr uint32_t p_bytes = static_cast<uint32_t>(TC / 64) * 16384u;
     const uint32_t sA = base_u32, sX = base_u32 + off_x, sP = base_u32 + off_p;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + off_bar);
     uint64_t* full = bars;          // [8]  X~ stage loaded
     uint64_t* empty = bars + 8;     // [8]  X~ stage released by the MMAs that read it
-    uint64_t* d1_full = bars + 16;  // [2]  Z chunk ready in TMEM
-    uint64_t* d1_empty = bars + 18; // [2]  Z chunk read out by the 8 epilogue warps
-    uint64_t* p_full = bars + 20;   // [2]  P chunk written to SMEM by the 8 epilogue warps
-    uint64_t* p_empty = bars + 22;  // [2]  P chunk consumed by the second product
-    uint64_t* d2_full = bars + 24;  //      accumulator complete
-    uint64_t* mma_done = bars + 25; //      every MMA of this CTA retired (teardown)
+    constexpr int LOOK = NB - 1;    // second product of chunk c is issued after the first of c+LOOK
+    uint64_t* d1_full = bars + 16;  // [NB] Z chunk ready in TMEM
+    uint64_t* d1_empty = bars + 19; // [NB] Z chunk read out by the 16 epilogue warps
+    uint64_t* p_full = bars + 22;   // [NB] P chunk written to SMEM by the 16 epilogue warps
+    uint64_t* d2_full = bars + 28;  //      accumulator complete
+    uint64_t* mma_done = bars + 29; //      every MMA of this CTA retired (teardown)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kBars);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    float* mom_sm = reinterpret_cast<float*>(bars + kBars + 2);  // [128][4]
+    float* mom_sm = reinterpret_cast<float*>(bars + kBars + 2);  // [3][128][4]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.x, tile = blockIdx.y;
     const int m0 = tile * kTcRows;
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    if (m0 >= M_act) return;  // grid sized for an upper bound of the active count
     const int c_begin = split * chunks_per_split;
     const int c_end = min(total_chunks, c_begin + chunks_per_split);
     const int nch = c_end - c_begin;
@@ -110,18 +132,20 @@ __global__ void __launch_bounds__(320, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             mbar_init(&d1_full[b], 1);
-            mbar_init(&d1_empty[b], 8);
-            mbar_init(&p_full[b], 8);
-            mbar_init(&p_empty[b], 1);
+            mbar_init(&d1_empty[b], kEpiWarps);
+            mbar_init(&p_full[b], kEpiWarps);
         }
         mbar_init(d2_full, 1);
         mbar_init(mma_done, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) tma_prefetch_desc(&xmap);
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&xmap);
+        if (KT) tma_prefetch_desc(&xmap_t);
+    }
     if (warp == 1) {
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
@@ -130,7 +154,7 @@ __global__ void __launch_bounds__(320, 1)
         // restart tile -> BF16, K-major, 128-byte swizzle: K-block kb (64 columns) at kb*16 KB
         const int et = threadIdx.x - 64;
         const int cpr = n_pad / 8;
-        for (int idx = et; idx < kTcRows * cpr; idx += 256) {
+        for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
             const int row = idx / cpr, ch = idx % cpr;
             const int gm = m0 + row;
             float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
@@ -152,7 +176,7 @@ __global__ void __launch_bounds__(320, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tD2 = tmem;
-    const uint32_t tD1_0 = tmem + 256u, tD1_1 = tmem + 256u + static_cast<uint32_t>(TC);
+    constexpr uint32_t kD1Col = TC == 192 ? 64u : (TC == 128 ? 128u : 256u);  // Z buffers after D2
 
     if (warp == 0) {
         // ------------------------------------------------------------------ TMA producer
@@ -165,10 +189,14 @@ __global__ void __launch_bounds__(320, 1)
                     break;
                 mbar_arrive_expect_tx(&full[s], xstage_bytes);
                 const int tg = (c_begin + c) * TC;
+                const uint32_t stage = sX + static_cast<uint32_t>(s) * xstage_bytes;
 #pragma unroll
                 for (int sub = 0; sub < TC / 64; ++sub)
-                    tma_load_2d(sX + static_cast<uint32_t>(s) * xstage_bytes + static_cast<uint32_t>(sub) * xsub_bytes,
-                                &xmap, &full[s], tg + sub * 64, 0);
+                    tma_load_2d(stage + static_cast<uint32_t>(sub) * xsub_bytes, &xmap, &full[s], tg + sub * 64, 0);
+                if (KT)
+                    for (int kb = 0; kb < (n_pad + 63) / 64; ++kb)
+                        tma_load_2d(stage + xn_bytes + static_cast<uint32_t>(kb * TC) * 128u, &xmap_t, &full[s], kb * 64,
+                                    tg);
                 ++issued;
             }
             // drain: every issued load must land before the CTA can exit
@@ -180,47 +208,52 @@ __global__ void __launch_bounds__(320, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t id1 = idesc_bf16(128, TC, 1);  // B operand MN-major (samples contiguous)
+            constexpr uint32_t id1 = idesc_bf16(128, TC, KT ? 0u : 1u);  // B: X~^T K-major, or X~ MN-major
             const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(n_pad), 0);
+            // Descriptors are built once; a K step only moves the start-address field (address >> 4,
+            // bits 0-13), which cannot carry into the next field for shared addresses below 256 KB.
+            const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
+            const uint64_t b1_desc = KT ? sw128_desc(sX + xn_bytes, 16u, 1024u) : sw128_desc(sX, xsub_bytes, 1024u);
+            const uint64_t p_desc = sw128_desc(sP, 16u, 1024u);
+            const uint64_t x_desc = sw128_desc(sX, 16u, 1024u);
+            const uint32_t stage16 = xstage_bytes >> 4;
+            const int ksteps1 = n_pad / 16;
             bool ok = true;
-            for (int c = 0; c <= nch && ok; ++c) {
+            for (int c = 0; c < nch + LOOK && ok; ++c) {
                 if (c < nch) {
-                    const int s = c % stages, b = c & 1;
+                    const int s = c % stages, b = c % NB;
                     ok = mbar_wait(&full[s], static_cast<uint32_t>(c / stages) & 1u, abort_flag, status);
-                    if (ok && c >= 2) ok = mbar_wait(&d1_empty[b], static_cast<uint32_t>((c - 2) >> 1) & 1u, abort_flag, status);
+                    if (ok && c >= NB)
+                        ok = mbar_wait(&d1_empty[b], static_cast<uint32_t>((c - NB) / NB) & 1u, abort_flag, status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t xs = sX + static_cast<uint32_t>(s) * xstage_bytes;
-                    const uint32_t d1 = b ? tD1_1 : tD1_0;
-                    for (int ks = 0; ks < n_pad / 16; ++ks) {
-                        const uint64_t ad = sw128_desc(sA + static_cast<uint32_t>(ks >> 2) * 16384u +
-                                                           static_cast<uint32_t>(ks & 3) * 32u,
-                                                       16u, 1024u);
-                        const uint64_t bd = sw128_desc(xs + static_cast<uint32_t>(ks) * 2048u, xsub_bytes, 1024u);
-                        umma_bf16(d1, ad, bd, id1, ks > 0 ? 1u : 0u);
+                    const uint32_t d1 = tmem + kD1Col + static_cast<uint32_t>(b * TC);
+                    const uint64_t b1s = b1_desc + static_cast<uint64_t>(static_cast<uint32_t>(s) * stage16);
+#pragma unroll
+                    for (int ks = 0; ks < 16; ++ks) {
+                        if (ks >= ksteps1) break;
+                        const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                        const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
+                                                  : (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                        umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                     }
                     umma_commit(&d1_full[b]);
                     if (MOMENTS_ONLY) umma_commit(&empty[s]);
                 }
-                if (!MOMENTS_ONLY && c >= 1) {
-                    const int cp = c - 1, sp = cp % stages, bp = cp & 1;
-                    ok = mbar_wait(&p_full[bp], static_cast<uint32_t>(cp >> 1) & 1u, abort_flag, status);
+                if (!MOMENTS_ONLY && c >= LOOK) {
+                    const int cp = c - LOOK, sp = cp % stages, bp = cp % NB;
+                    ok = mbar_wait(&p_full[bp], static_cast<uint32_t>(cp / NB) & 1u, abort_flag, status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t xs = sX + static_cast<uint32_t>(sp) * xstage_bytes;
-                    const uint32_t ps = sP + static_cast<uint32_t>(bp) * p_bytes;
+                    const uint64_t ps = p_desc + static_cast<uint64_t>((static_cast<uint32_t>(bp) * p_bytes) >> 4);
+                    const uint64_t xs = x_desc + static_cast<uint64_t>(static_cast<uint32_t>(sp) * stage16);
 #pragma unroll
                     for (int ks = 0; ks < TC / 16; ++ks) {
-                        const uint64_t ad = sw128_desc(ps + static_cast<uint32_t>(ks >> 2) * 16384u +
-                                                           static_cast<uint32_t>(ks & 3) * 32u,
-                                                       16u, 1024u);
-                        const uint64_t bd = sw128_desc(xs + static_cast<uint32_t>(ks >> 2) * xsub_bytes +
-                                                           static_cast<uint32_t>(ks & 3) * 32u,
-                                                       16u, 1024u);
-                        umma_bf16(tD2, ad, bd, id2, (cp > 0 || ks > 0) ? 1u : 0u);
+                        const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                        const uint32_t b_off = ((ks >> 2) * xsub_bytes + (ks & 3) * 32u) >> 4;
+                        umma_bf16(tD2, ps + a_off, xs + b_off, id2, (cp > 0 || ks > 0) ? 1u : 0u);
                     }
-                    umma_commit(&p_empty[bp]);
-                    umma_commit(&empty[sp]);
+                    umma_commit(&empty[sp]);  // releases the X~ stage and the P buffer
                 }
             }
             if (!MOMENTS_ONLY) umma_commit(d2_full);
@@ -230,22 +263,23 @@ __global__ void __launch_bounds__(320, 1)
     } else {
         // ------------------------------------------------------------------ epilogue warps
         const int q = warp & 3;
-        const int h = (warp - 2) >> 2;
+        const int h = (warp - 2) >> 2;  // column quarter 0..3
         const int row = q * 32 + lane;
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-        constexpr int CW = TC / 2;
+        constexpr int CW = TC / 4;
         float2 s2 = make_float2(0.f, 0.f), s4 = make_float2(0.f, 0.f);
         float sq = 0.f;
         bool ok = true;
         for (int c = 0; c < nch; ++c) {
-            const int b = c & 1;
-            ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], static_cast<uint32_t>(c >> 1) & 1u, abort_flag, status));
+            const int b = c % NB;
+            ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], static_cast<uint32_t>(c / NB) & 1u, abort_flag, status));
             if (!ok) break;
             tc_fence_after();
             float v[CW];
-            const uint32_t d1 = (b ? tD1_1 : tD1_0) + lane_off + static_cast<uint32_t>(h * CW);
-#pragma unroll
-            for (int g = 0; g < CW / 32; ++g) tmem_ld32(d1 + static_cast<uint32_t>(g * 32), *reinterpret_cast<float(*)[32]>(&v[g * 32]));
+            const uint32_t d1 = tmem + kD1Col + static_cast<uint32_t>(b * TC) + lane_off + static_cast<uint32_t>(h * CW);
+            if constexpr (CW >= 32) tmem_ld32(d1, *reinterpret_cast<float(*)[32]>(&v[0]));
+            if constexpr (CW == 64) tmem_ld32(d1 + 32u, *reinterpret_cast<float(*)[32]>(&v[32]));
+            if constexpr (CW % 32 == 16) tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
@@ -256,8 +290,10 @@ __global__ void __launch_bounds__(320, 1)
             for (int i = 0; i < CW; i += 2) {
                 const float2 z = make_float2(v[i], v[i + 1]);
                 const float2 z2 = mul2(z, z);
-                s2 = add2(s2, z2);
-                s4 = fma2(z2, z2, s4);
+                if (MOMENTS || MOMENTS_ONLY) {
+                    s2 = add2(s2, z2);
+                    s4 = fma2(z2, z2, s4);
+                }
                 if (MOMENTS_ONLY) {
                     const float e0 = (tbase + i < T) ? z2.x - 1.f : 0.f;
                     const float e1 = (tbase + i + 1 < T) ? z2.y - 1.f : 0.f;
@@ -268,9 +304,12 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
             if (!MOMENTS_ONLY) {
-                if (c >= 2) {
-                    ok = __all_sync(0xffffffffu,
-                                    mbar_wait(&p_empty[b], static_cast<uint32_t>((c - 2) >> 1) & 1u, abort_flag, status));
+                if (c >= NB) {
+                    // P[b] is free once the second product of chunk c - NB retired; that product's
+                    // commit released the X~ stage of chunk c - NB
+                    const int cr = c - NB;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&empty[cr % stages], static_cast<uint32_t>(cr / stages) & 1u,
+                                                           abort_flag, status));
                     if (!ok) break;
                 }
                 const uint32_t pbase = sP + static_cast<uint32_t>(b) * p_bytes;
@@ -290,7 +329,7 @@ __global__ void __launch_bounds__(320, 1)
         }
         const int grow = m0 + row;
         const int64_t prow = static_cast<int64_t>(split) * part_rows + grow;
-        if (!MOMENTS_ONLY && ok) {
+        if (!MOMENTS_ONLY && ok && h < 2) {  // accumulator read-out: two warps per lane quarter
             ok = __all_sync(0xffffffffu, mbar_wait(d2_full, 0u, abort_flag, status));
             if (ok) {
                 tc_fence_after();
@@ -308,16 +347,25 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
         }
-        if (h == 1) {
-            mom_sm[row * 4 + 0] = s2.x + s2.y;
-            mom_sm[row * 4 + 1] = s4.x + s4.y;
-            mom_sm[row * 4 + 2] = sq;
+        if (h > 0) {
+            float* dst = mom_sm + ((h - 1) * kTcRows + row) * 4;
+            dst[0] = s2.x + s2.y;
+            dst[1] = s4.x + s4.y;
+            dst[2] = sq;
         }
-        named_bar_sync(1, 256);
+        named_bar_sync(1, 32 * kEpiWarps);
         if (h == 0 && grow < M_act) {
-            part_mom[prow * 4 + 0] = s2.x + s2.y + mom_sm[row * 4 + 0];
-            part_mom[prow * 4 + 1] = s4.x + s4.y + mom_sm[row * 4 + 1];
-            part_mom[prow * 4 + 2] = sq + mom_sm[row * 4 + 2];
+            float m2 = s2.x + s2.y, m4 = s4.x + s4.y, mq = sq;
+#pragma unroll
+            for (int hh = 0; hh < 3; ++hh) {  // fixed order: quarters 1, 2, 3
+                const float* src = mom_sm + (hh * kTcRows + row) * 4;
+                m2 += src[0];
+                m4 += src[1];
+                mq += src[2];
+            }
+            part_mom[prow * 4 + 0] = m2;
+            part_mom[prow * 4 + 1] = m4;
+            part_mom[prow * 4 + 2] = mq;
             part_mom[prow * 4 + 3] = 0.f;
         }
     }
@@ -329,41 +377,45 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
-template <int TC, bool MO>
-static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const float* B32, int ldb,
-                                  const int* act_idx, int M_act, int n_pad, int64_t T, int splits,
-                                  int chunks_per_split, int total_chunks, float* part_acc, float* part_mom,
-                                  int part_rows, int* status) {
-    const TcLayout L = tc_layout(n_pad, MO, TC);
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TC, MO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(L.total));
+template <int TC, int NB, bool KT, bool MO, bool MOM>
+static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const CUtensorMap* xmap_t,
+                                  const float* B32, int ldb,
+                                  const int* act_idx, const int* count_dev, int M_act, int n_pad, int64_t T,
+                                  int splits, int chunks_per_split, int total_chunks, float* part_acc,
+                                  float* part_mom, int part_rows, int* status) {
+    const TcLayout L = tc_layout(n_pad, MO, TC, NB, KT);
+    if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
+    if (KT && !xmap_t) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TC, NB, KT, MO, MOM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.total));
     if (e != cudaSuccess) return e;
     const dim3 grid(splits, (M_act + kTcRows - 1) / kTcRows);
-    fused_tc_kernel<TC, MO><<<grid, 320, L.total, s>>>(xmap, B32, ldb, act_idx, M_act, n_pad, T, chunks_per_split,
-                                                       total_chunks, static_cast<int>(L.stages), L.a_bytes,
-                                                       L.xsub_bytes, L.off_x, L.off_p, L.off_bar, part_acc, part_mom,
-                                                       part_rows, status);
+    fused_tc_kernel<TC, NB, KT, MO, MOM><<<grid, kThreads, L.total, s>>>(
+        xmap, KT ? *xmap_t : xmap, B32, ldb, act_idx, count_dev, M_act, n_pad, T, chunks_per_split, total_chunks,
+        static_cast<int>(L.stages), L.a_bytes, L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p, L.off_bar, part_acc,
+        part_mom, part_rows, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, const CUtensorMap& xmap, const float* B32, int ldb,
-                            const int* act_idx, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
+cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
+                            const CUtensorMap* xmap_t, const float* B32, int ldb, const int* act_idx,
+                            const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
                             int total_chunks, float* part_acc, float* part_mom, int part_rows, int* status) {
     const int TC = tc_chunk(n_pad);
-    if (TC == 128) {
-        return moments_only ? launch_tc_impl<128, true>(s, xmap, B32, ldb, act_idx, M_act, n_pad, T, splits,
-                                                        chunks_per_split, total_chunks, part_acc, part_mom,
-                                                        part_rows, status)
-                            : launch_tc_impl<128, false>(s, xmap, B32, ldb, act_idx, M_act, n_pad, T, splits,
-                                                         chunks_per_split, total_chunks, part_acc, part_mom,
-                                                         part_rows, status);
-    }
-    return moments_only ? launch_tc_impl<64, true>(s, xmap, B32, ldb, act_idx, M_act, n_pad, T, splits,
-                                                   chunks_per_split, total_chunks, part_acc, part_mom, part_rows,
-                                                   status)
-                        : launch_tc_impl<64, false>(s, xmap, B32, ldb, act_idx, M_act, n_pad, T, splits,
-                                                    chunks_per_split, total_chunks, part_acc, part_mom, part_rows,
-                                                    status);
+    const bool KT = xmap_t && tc_transposed(n_pad);
+#define ICA_TC_ARGS s, xmap, xmap_t, B32, ldb, act_idx, count_dev, M_act, n_pad, T, splits, chunks_per_split, \
+                    total_chunks, part_acc, part_mom, part_rows, status
+#define ICA_TC_DISPATCH(TCV, NBV, KTV)                                                                \
+    do {                                                                                            \
+        if (moments_only) return launch_tc_impl<TCV, NBV, KTV, true, true>(ICA_TC_ARGS);            \
+        return moments ? launch_tc_impl<TCV, NBV, KTV, false, true>(ICA_TC_ARGS)                    \
+                       : launch_tc_impl<TCV, NBV, KTV, false, false>(ICA_TC_ARGS);                  \
+    } while (0)
+    if (TC == 192) ICA_TC_DISPATCH(192, 2, false);
+    if (KT) ICA_TC_DISPATCH(64, 2, true);
+    ICA_TC_DISPATCH(64, 2, false);
+#undef ICA_TC_DISPATCH
+#undef ICA_TC_ARGS
 }
 
 }  // namespace ica

@@ -177,7 +177,7 @@ def ica_fp_step(ctx: Context, precision: int, B: torch.Tensor, n: int, Xt: torch
     Returns (Bnew M x n_pad float32, moments M x 4 float32)."""
     M, n_pad = B.shape
     xp, ldx = _xt_args(Xt, precision)
-    ctx.ensure_workspace(n, T, M, ica_default_opts(precision=ICA_FP32))
+    ctx.ensure_workspace(n, T, M, ica_default_opts(precision=precision))
     Bnew = torch.empty_like(B)
     mom = torch.empty((M, 4), dtype=torch.float32, device=B.device)
     _check(ctx.lib.ica_fp_step(ctx.handle, precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(Bnew),
@@ -189,7 +189,7 @@ def ica_kurtosis(ctx: Context, precision: int, B: torch.Tensor, n: int, Xt: torc
     """alpha and Upsilon (float64, M each) of the rows of B on reduced data Xt."""
     M, n_pad = B.shape
     xp, ldx = _xt_args(Xt, precision)
-    ctx.ensure_workspace(n, T, M, ica_default_opts(precision=ICA_FP32))
+    ctx.ensure_workspace(n, T, M, ica_default_opts(precision=precision))
     a = torch.empty(M, dtype=torch.float64, device=B.device)
     u = torch.empty(M, dtype=torch.float64, device=B.device)
     _check(ctx.lib.ica_kurtosis(ctx.handle, precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(a),
