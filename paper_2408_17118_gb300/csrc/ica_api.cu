@@ -625,6 +625,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     const double inv_T = 1.0 / static_cast<double>(T);
     int* status = at<int>(c, L.status);
     int* counts = at<int>(c, L.counts);  // [0], [1]: active counts (double-buffered); [2]: candidates
+    unsigned int* done_ctr = reinterpret_cast<unsigned int*>(counts + 8);  // finalize's block counter
     float* B32 = at<float>(c, L.B32);
     float* Xt32 = at<float>(c, L.Xt32);
     uint16_t* Xt16 = at<uint16_t>(c, L.Xt16);
@@ -648,6 +649,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     const int refine_iters = o.refine_iters < iters ? o.refine_iters : iters;
 
     CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(done_ctr, 0, sizeof(unsigned int), s));
     CK(cudaMemsetAsync(crows, 0, sizeof(long long) * 2 * (N + 1), s));
     c->launches = 0;
     for (int k = 0; k < K_NKINDS; ++k) {
@@ -733,13 +735,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             rc = timed(K_FINALIZE, 0.0, [&] {
                 KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
                                    n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
-                                   o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status));
-                return ICA_OK;
-            });
-            if (rc) return rc;
-            rc = timed(K_COMPACT, 0.0, [&] {
-                KL(launch_compact(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1),
-                                  crows + 2 * i));
+                                   o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
+                                   counts + (cur ^ 1), crows + 2 * i, done_ctr));
                 return ICA_OK;
             });
             if (rc) return rc;
@@ -794,13 +791,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                 rc = timed(K_FINALIZE, 0.0, [&] {
                     KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
                                        n_pad, n, act[rcur], counts + rcur, R_host, B32, n_pad, inv_T, tol_ref, flags,
-                                       itc, nullptr, kTrajLen, status));
-                    return ICA_OK;
-                });
-                if (rc) return rc;
-                rc = timed(K_COMPACT, 0.0, [&] {
-                    KL(launch_compact(s, flags, act[rcur], counts + rcur, R_host, act[rcur ^ 1], counts + (rcur ^ 1),
-                                      crows + 2 * i + 1));
+                                       itc, nullptr, kTrajLen, status, act[rcur ^ 1], counts + (rcur ^ 1),
+                                       crows + 2 * i + 1, done_ctr));
                     return ICA_OK;
                 });
                 if (rc) return rc;

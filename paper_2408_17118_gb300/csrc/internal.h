@@ -24,12 +24,11 @@ cudaError_t launch_iota(cudaStream_t s, int* idx, int count, int* count_dev);
 cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
-                            int t_iter, int* status);
+                            int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
+                            unsigned int* done_ctr);
 cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                            int part_rows, int n_pad, int M, const float* B, double inv_T, float* Bnew,
                            float* moments);
-cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, const int* count_in_dev,
-                           int count_host, int* act_out, int* count_out_dev, long long* rows_accum);
 cudaError_t launch_compact_cand(cudaStream_t s, const int* cand, int k, int* list_a, int* list_b, int* count_dev);
 cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int splits, int part_rows,
                                  const int* act_idx, const int* count_dev, int count, double inv_T, double* alpha,

@@ -83,86 +83,105 @@ cudaError_t launch_iota(cudaStream_t s, int* idx, int count, int* count_dev) {
 // iff d > tol. Rows whose update is zero or non-finite are retired and flagged in the status
 // word. For the first kTrajLen iterations the kurtosis of the pre-update row and d are kept as
 // per-restart features.
+// All arithmetic is FP32 (GB300's FP64 rate is 1/64 of FP32 and this kernel runs every
+// iteration); the sums over splits are compensated (Neumaier), so their error stays at one FP32
+// rounding of the result instead of growing with the number of splits.
 // ------------------------------------------------------------------------------------------
+struct CompSum {  // s + c carries the exact running sum to about twice FP32 precision
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
+// One row j of the update: all NW warps sum the split partials, warp 0 finishes the row.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
-                                                           const float* __restrict__ part_mom, int splits,
-                                                           int part_rows, int n_pad, int n,
-                                                           const int* __restrict__ act_idx,
-                                                           const int* __restrict__ count_dev, int M_act_host,
-                                                           float* __restrict__ B32, int ldb, double inv_T, double tol,
-                                                           int* __restrict__ flags, int* __restrict__ iters,
-                                                           float* __restrict__ traj, int t_iter, int* status) {
-    extern __shared__ double fin_red[];  // [NW][n_pad] then [NW][2]
-    double* red = fin_red;
-    double* redm = fin_red + NW * n_pad;
-    const int M_act = count_dev ? *count_dev : M_act_host;
-    const int j = blockIdx.x;
-    if (j >= M_act) return;
+__device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
+                                             int splits, int part_rows, int n_pad, int n,
+                                             const int* __restrict__ act_idx, int j, float* __restrict__ B32,
+                                             int ldb, float inv_T, float tol, int* __restrict__ flags,
+                                             int* __restrict__ iters, float* __restrict__ traj, int t_iter,
+                                             int* status, float* red_s, float* red_c, float* redm) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool want_traj = traj && t_iter < kTrajLen;
+    const int nq = (n_pad + 31) >> 5;  // columns per lane
     {
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        double m2 = 0.0, m4 = 0.0;
+
+        CompSum acc[8];
+        CompSum m2, m4;
 #pragma unroll 4
         for (int sp = w; sp < splits; sp += NW) {
             const float* p = part_acc + (static_cast<int64_t>(sp) * part_rows + j) * n_pad;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
+                if (q >= nq) break;
                 const int k = lane + 32 * q;
-                if (k < n_pad) acc[q] += static_cast<double>(p[k]);
+                if (k < n_pad) acc[q].add(p[k]);
             }
             if (want_traj && lane == 0) {
-                m2 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 0];
-                m4 += part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 1];
+                m2.add(part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 0]);
+                m4.add(part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 1]);
             }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
+            if (q >= nq) break;
             const int k = lane + 32 * q;
-            if (k < n_pad) red[w * n_pad + k] = acc[q];
+            if (k < n_pad) {
+                red_s[w * n_pad + k] = acc[q].s;
+                red_c[w * n_pad + k] = acc[q].c;
+            }
         }
         if (lane == 0) {
-            redm[2 * w] = m2;
-            redm[2 * w + 1] = m4;
+            redm[4 * w + 0] = m2.s;
+            redm[4 * w + 1] = m2.c;
+            redm[4 * w + 2] = m4.s;
+            redm[4 * w + 3] = m4.c;
         }
     }
     __syncthreads();
     if (w != 0) return;
     const int r = act_idx ? act_idx[j] : j;
-    double u[8], b[8];
-    double ss = 0.0;
+    float u[8], b[8];
+    float ss = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int k = lane + 32 * q;
-        u[q] = 0.0;
-        b[q] = 0.0;
-        if (k < n) {
-            double acc = 0.0;
-            for (int ww = 0; ww < NW; ++ww) acc += red[ww * n_pad + k];
-            b[q] = static_cast<double>(B32[static_cast<int64_t>(r) * ldb + k]);
-            u[q] = acc * inv_T - 3.0 * b[q];
-            ss += u[q] * u[q];
+        u[q] = 0.f;
+        b[q] = 0.f;
+        if (q < nq && k < n) {
+            CompSum acc;
+            float cs = 0.f;
+            for (int ww = 0; ww < NW; ++ww) {
+                acc.add(red_s[ww * n_pad + k]);
+                cs += red_c[ww * n_pad + k];
+            }
+            b[q] = B32[static_cast<int64_t>(r) * ldb + k];
+            u[q] = (acc.value() + cs) * inv_T - 3.f * b[q];
+            ss = fmaf(u[q], u[q], ss);
         }
     }
-    ss = warp_sum(ss);
-    const bool bad = !(ss > 0.0) || !isfinite(ss);
-    double dm = 0.0, dp = 0.0;
-    const double inv = bad ? 0.0 : 1.0 / sqrt(ss);
+    ss = warp_sumf(ss);
+    const bool bad = !(ss > 0.f) || !isfinite(ss);
+    float dm = 0.f, dp = 0.f;
+    const float inv = bad ? 0.f : rsqrtf(ss);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         u[q] *= inv;
-        dm += (u[q] - b[q]) * (u[q] - b[q]);
-        dp += (u[q] + b[q]) * (u[q] + b[q]);
+        dm = fmaf(u[q] - b[q], u[q] - b[q], dm);
+        dp = fmaf(u[q] + b[q], u[q] + b[q], dp);
     }
-    dm = warp_sum(dm);
-    dp = warp_sum(dp);
-    const double d = sqrt(fmin(dm, dp));
+    dm = warp_sumf(dm);
+    dp = warp_sumf(dp);
+    const float d = sqrtf(fminf(dm, dp));
     if (!bad) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int k = lane + 32 * q;
-            if (k < n) B32[static_cast<int64_t>(r) * ldb + k] = static_cast<float>(u[q]);
+            if (q < nq && k < n) B32[static_cast<int64_t>(r) * ldb + k] = u[q];
         }
     }
     if (lane == 0) {
@@ -170,17 +189,80 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
         iters[r] += 1;
         if (bad) atomicOr(status, DEV_NONFINITE);
         if (want_traj) {
-            double m2 = 0.0, m4 = 0.0;
+            CompSum m2, m4;
             for (int ww = 0; ww < NW; ++ww) {
-                m2 += redm[2 * ww];
-                m4 += redm[2 * ww + 1];
+                m2.add(redm[4 * ww + 0]);
+                m2.add(redm[4 * ww + 1]);
+                m4.add(redm[4 * ww + 2]);
+                m4.add(redm[4 * ww + 3]);
             }
-            m2 *= inv_T;
-            m4 *= inv_T;
-            const double alpha = m2 > 0.0 ? m4 / (m2 * m2) - 3.0 : 0.0;
-            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 0] = static_cast<float>(alpha);
-            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 1] = static_cast<float>(d);
+            const float e2 = m2.value() * inv_T, e4 = m4.value() * inv_T;
+            const float alpha = e2 > 0.f ? e4 / (e2 * e2) - 3.f : 0.f;
+            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 0] = alpha;
+            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 1] = d;
         }
+    }
+}
+
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
+                                                           const float* __restrict__ part_mom, int splits,
+                                                           int part_rows, int n_pad, int n,
+                                                           const int* __restrict__ act_idx,
+                                                           const int* __restrict__ count_dev, int M_act_host,
+                                                           float* __restrict__ B32, int ldb, float inv_T, float tol,
+                                                           int* __restrict__ flags, int* __restrict__ iters,
+                                                           float* __restrict__ traj, int t_iter, int* status,
+                                                           int* __restrict__ act_out, int* count_out,
+                                                           long long* rows_accum, unsigned int* done_ctr) {
+    extern __shared__ float fin_red[];  // [NW][n_pad] sums, [NW][n_pad] compensations, [NW][4] moments
+    __shared__ int is_last;
+    __shared__ int warp_tot[NW];
+    float* red_s = fin_red;
+    float* red_c = fin_red + NW * n_pad;
+    float* redm = fin_red + 2 * NW * n_pad;
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    const int j = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j < M_act) {
+        finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
+                         traj, t_iter, status, red_s, red_c, redm);
+    }
+    // Compaction of the active list (Section 3.2: converged rows leave B) into act_out/count_out,
+    // by the last block to finish: every block counts itself in after its flag is visible
+    // device-wide. act_out and count_out must not alias act_idx and count_dev; *done_ctr is zero
+    // on entry and is left zero.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        is_last = atomicAdd(done_ctr, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const int nthr = NW * 32;
+    const int per = (M_act + nthr - 1) / nthr;
+    const int b0 = threadIdx.x * per, e0 = min(M_act, b0 + per);
+    int local = 0;
+    for (int i = b0; i < e0; ++i) local += __ldcg(flags + i) != 0;  // L2: written by other blocks
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int ww = 0; ww < w; ++ww) before += warp_tot[ww];
+    int pos = before + incl - local;
+    for (int i = b0; i < e0; ++i)
+        if (__ldcg(flags + i)) act_out[pos++] = act_idx ? act_idx[i] : i;
+    if (threadIdx.x == nthr - 1) {
+        *count_out = before + incl;
+        if (rows_accum) *rows_accum += M_act;  // rows this iteration updated
+        *done_ctr = 0u;                        // ready for the next launch
     }
 }
 
@@ -188,20 +270,22 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
 cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
-                            int t_iter, int* status) {
+                            int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
+                            unsigned int* done_ctr) {
+    const float fT = static_cast<float>(inv_T), ftol = static_cast<float>(tol);
     if (M_act <= 64 && splits > 16) {
-        const size_t smem = sizeof(double) * 32 * (n_pad + 2);
+        const size_t smem = sizeof(float) * 32 * (2 * n_pad + 4);
         cudaError_t e = cudaFuncSetAttribute(finalize_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         finalize_kernel<32><<<M_act, 1024, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
-                                                      count_dev, M_act, B32, ldb, inv_T, tol, flags, iters, traj,
-                                                      t_iter, status);
+                                                      count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
+                                                      t_iter, status, act_out, count_out, rows_accum, done_ctr);
     } else {
-        const size_t smem = sizeof(double) * 8 * (n_pad + 2);
+        const size_t smem = sizeof(float) * 8 * (2 * n_pad + 4);
         finalize_kernel<8><<<M_act, 256, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
-                                                    count_dev, M_act, B32, ldb, inv_T, tol, flags, iters, traj,
-                                                    t_iter, status);
+                                                    count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
+                                                    t_iter, status, act_out, count_out, rows_accum, done_ctr);
     }
     return cudaGetLastError();
 }
@@ -233,53 +317,6 @@ cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* p
     const int64_t total = static_cast<int64_t>(M) * (n_pad > 4 ? n_pad : 4);
     combine_kernel<<<static_cast<int>((total + 255) / 256), 256, 0, s>>>(part_acc, part_mom, splits, part_rows,
                                                                           n_pad, M, B, inv_T, Bnew, moments);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------------------------------
-// Stable stream compaction of the active restart list (Section 3.2: converged rows leave B).
-// One CTA of 1024 threads; thread t owns a contiguous slice of the list.
-// ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) compact_kernel(const int* __restrict__ flags, const int* __restrict__ act_in,
-                                                       const int* __restrict__ count_in_dev, int count_host,
-                                                       int* __restrict__ act_out, int* count_out_dev,
-                                                       long long* rows_accum) {
-    __shared__ int warp_tot[32];
-    const int count = count_in_dev ? *count_in_dev : count_host;
-    if (threadIdx.x == 0 && rows_accum) *rows_accum += count;  // rows this iteration updated
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int per = (count + 1023) / 1024;
-    const int b = t * per, e = min(count, b + per);
-    int local = 0;
-    for (int i = b; i < e; ++i) local += flags[i] != 0;
-    int incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        int v = warp_tot[lane];
-        int iv = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, iv, o);
-            if (lane >= o) iv += y;
-        }
-        warp_tot[lane] = iv - v;  // exclusive prefix of warp totals
-    }
-    __syncthreads();
-    int pos = warp_tot[w] + incl - local;
-    for (int i = b; i < e; ++i)
-        if (flags[i]) act_out[pos++] = act_in ? act_in[i] : i;
-    if (t == 1023) *count_out_dev = warp_tot[31] + incl;
-}
-
-cudaError_t launch_compact(cudaStream_t s, const int* flags, const int* act_in, const int* count_in_dev,
-                           int count_host, int* act_out, int* count_out_dev, long long* rows_accum) {
-    compact_kernel<<<1, 1024, 0, s>>>(flags, act_in, count_in_dev, count_host, act_out, count_out_dev, rows_accum);
     return cudaGetLastError();
 }
 
