@@ -259,11 +259,12 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
     }
     if (a.precision == ICA_FP32) {
         const int64_t total = (a.T + 63) / 64;
-        if (a.M_act <= kFp32SmallRows) {  // a few candidates: row tile of 16, bound by reading X~
-            choose_splits(total, 1, 2 * 152, a.max_splits, &shape->splits, &shape->cps);
-            shape->part_rows = kFp32SmallRows;
-            KL(launch_fused_fp32_small(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx,
-                                       a.n_pad, a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
+        if (a.M_act <= kFp32SmallRows) {  // a few candidates: bound by streaming X~
+            const int64_t total_rows_chunks = (a.T + fp32_rows_chunk(a.n_pad) - 1) / fp32_rows_chunk(a.n_pad);
+            choose_splits(total_rows_chunks, 1, 2 * 152, a.max_splits, &shape->splits, &shape->cps);
+            shape->part_rows = fp32_rows_tile(a.M_act);
+            KL(launch_fused_fp32_rows(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx,
+                                      a.n_pad, a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
             return ICA_OK;
         }
         const int tiles = (a.M_act + kFp32Rows - 1) / kFp32Rows;
@@ -681,9 +682,16 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         *out = c->host_i[0];
         return ICA_OK;
     };
-    cudaEvent_t fit_begin = nullptr, fit_end = nullptr;
-    CK(cudaEventCreate(&fit_begin));
-    CK(cudaEventCreate(&fit_end));
+    struct EventGuard {  // destroys the fit's two events on every return path
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~EventGuard() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } fit_ev;
+    CK(cudaEventCreate(&fit_ev.e[0]));
+    CK(cudaEventCreate(&fit_ev.e[1]));
+    cudaEvent_t fit_begin = fit_ev.e[0], fit_end = fit_ev.e[1];
     CK(cudaEventRecord(fit_begin, s));
     const double dT = static_cast<double>(T);
     std::vector<int> comp_iters, comp_refine;
@@ -851,12 +859,10 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaEventSynchronize(fit_end));
     CK(cudaStreamSynchronize(s));
+    float fit_ms = 0.f;
     rc = map_device_status(c->host_i[1]);
     if (rc) return rc;
-    float fit_ms = 0.f;
     CK(cudaEventElapsedTime(&fit_ms, fit_begin, fit_end));
-    cudaEventDestroy(fit_begin);
-    cudaEventDestroy(fit_end);
     // algorithmic FLOPs from the exact per-component counts of updated rows (4 n rows T)
     double it_flops = 0.0, ref_flops = 0.0;
     for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i) {

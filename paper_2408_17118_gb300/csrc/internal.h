@@ -73,12 +73,14 @@ cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B3
                               const int* act_idx, const int* count_dev, int M_act, const float* Xt, int64_t ldx,
                               int n_pad, int64_t T, int splits, int chunks_per_split, float* part_acc,
                               float* part_mom, int part_rows);
-constexpr int kFp32SmallRows = 16;  // rows of the small-batch FP32 kernel (one CTA row tile)
-size_t fp32_small_smem_bytes(int n_pad);
-cudaError_t launch_fused_fp32_small(cudaStream_t s, bool moments_only, const float* B32, int ldb,
-                                    const int* act_idx, const int* count_dev, int M_act_host, const float* Xt,
-                                    int64_t ldx, int n_pad, int64_t T, int splits, int chunks_per_split,
-                                    float* part_acc, float* part_mom, int part_rows);
+constexpr int kFp32SmallRows = 16;  // at most this many rows go to the few-row FP32 kernel
+int fp32_rows_tile(int M_act);       // its row tile (4 or 16) for M_act <= kFp32SmallRows rows
+int fp32_rows_chunk(int n_pad);      // samples per chunk of the few-row kernel
+size_t fp32_rows_smem_bytes(int n_pad, int R);
+cudaError_t launch_fused_fp32_rows(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
+                                   const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
+                                   int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
+                                   int part_rows);
 
 // ---- k_tc.cu ----
 int tc_chunk(int n_pad);

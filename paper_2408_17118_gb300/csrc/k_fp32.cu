@@ -161,147 +161,249 @@ __global__ void __launch_bounds__(256) fused_fp32_kernel(const float* __restrict
 }
 
 // ------------------------------------------------------------------------------------------
-// Small-batch variant for at most 16 restart rows (the FP32 refinement of a few distinct
-// candidates): one row per thread row, 16 rows x 64 samples per chunk, so no tensor work is
-// spent on empty rows and the launch is bound by reading X~ once.
+// Few-row variant for at most R = 4 or 16 restart rows (the FP32 refinement of the distinct
+// best candidates of a component, Algorithm 2's pick made on FP32 data). The work per sample is
+// 4 R n FLOPs against n FP32 loads, so the kernel is bound by streaming X~ (from L2: the
+// refinement iterations of a component re-read the same X~). Per chunk of CS samples:
+//   staging: X~ chunk -> shared memory, transposed to sample-major (row stride n_pad + 4, which
+//            keeps both the transposing stores and the 16-byte reads free of bank conflicts);
+//            the next chunk's loads are issued into registers before this chunk is computed;
+//   pass 1:  thread (sample s, k-part h) forms the partial z_r(s) over its quarter of k for
+//            all R rows (b broadcast from shared memory), the parts are summed, and z^3 kept;
+//   pass 2:  thread (k-quad q, sample group g) accumulates acc[r][4q..4q+3] += z^3_r(t) x~_t
+//            over the samples t = g, g + G, ... of the chunk, in registers across all chunks.
+// At the end the per-thread accumulators are summed over g in a fixed order (deterministic).
 // ------------------------------------------------------------------------------------------
-constexpr int S_MT = 16;
-constexpr int S_ZS = S_MT + 1;  // padded z^3 row stride (bank conflicts)
+namespace {
+__host__ __device__ constexpr int rows_cs(int n_pad) { return n_pad <= 64 ? 128 : (n_pad <= 128 ? 64 : 32); }
+}  // namespace
 
-size_t fp32_small_smem_bytes(int n_pad) {
-    return sizeof(float) * (static_cast<size_t>(S_MT) * n_pad + static_cast<size_t>(n_pad) * F_XS +
-                            static_cast<size_t>(F_TC) * S_ZS);
+int fp32_rows_tile(int M_act) { return M_act <= 4 ? 4 : 16; }
+
+size_t fp32_rows_smem_bytes(int n_pad, int R) {
+    const int CS = rows_cs(n_pad), SX = n_pad + 4;
+    const size_t work = static_cast<size_t>(CS) * SX + 256u * R + static_cast<size_t>(CS) * R;
+    const size_t red = 1024u * R;
+    return sizeof(float) * (static_cast<size_t>(n_pad) * R + (work > red ? work : red) + 24 * R);
 }
 
-template <bool MOMENTS_ONLY>
-__global__ void __launch_bounds__(256) fused_fp32_small_kernel(const float* __restrict__ B32, int ldb,
-                                                               const int* __restrict__ act_idx,
-                                                               const int* __restrict__ count_dev, int M_act_host,
-                                                               const float* __restrict__ Xt, int64_t ldx, int n_pad,
-                                                               int64_t T, int chunks_per_split,
-                                                               float* __restrict__ part_acc,
-                                                               float* __restrict__ part_mom, int part_rows) {
-    extern __shared__ __align__(16) float ssm[];
-    float* Bs = ssm;                  // [S_MT][n_pad]
-    float* Xs = Bs + S_MT * n_pad;    // [n_pad][F_XS]
-    float* Zs = Xs + n_pad * F_XS;    // [F_TC][S_ZS]
+template <int R, bool MOMENTS_ONLY>
+__global__ void __launch_bounds__(256) fused_fp32_rows_kernel(const float* __restrict__ B32, int ldb,
+                                                              const int* __restrict__ act_idx,
+                                                              const int* __restrict__ count_dev, int M_act_host,
+                                                              const float* __restrict__ Xt, int64_t ldx, int n_pad,
+                                                              int64_t T, int chunks_per_split,
+                                                              float* __restrict__ part_acc,
+                                                              float* __restrict__ part_mom, int part_rows) {
+    extern __shared__ __align__(16) float rsm[];
+    const int CS = rows_cs(n_pad), SX = n_pad + 4, H = 256 / CS, KQ = n_pad / 4, G = 256 / KQ;
+    float* Bs = rsm;                    // [n_pad][R]
+    float* Xs = Bs + n_pad * R;         // [CS][SX]   sample-major X~ chunk
+    float* zp = Xs + CS * SX;           // [H][CS][R] partial z
+    float* z3 = zp + 256 * R;           // [CS][R]    z^3
+    float* red = Xs;                    // [G][R][n_pad] end-of-kernel reduction (aliases the above)
+    const size_t work = static_cast<size_t>(CS) * SX + 256u * R + static_cast<size_t>(CS) * R;
+    float* redm = Xs + (work > 1024u * R ? work : 1024u * R);  // [8][R][3]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M_act = count_dev ? *count_dev : M_act_host;
     const int split = blockIdx.x;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty = restart row, tx = sample group
-    const int kj = n_pad / 16;
-    for (int e = tid; e < S_MT * n_pad; e += 256) {
-        const int m = e / n_pad, k = e % n_pad;
+
+    for (int e = tid; e < n_pad * R; e += 256) {
+        const int k = e / R, r = e % R;
         float v = 0.f;
-        if (m < M_act) {
-            const int r = act_idx ? act_idx[m] : m;
-            v = B32[static_cast<int64_t>(r) * ldb + k];
-        }
+        if (r < M_act) v = B32[static_cast<int64_t>(act_idx ? act_idx[r] : r) * ldb + k];
         Bs[e] = v;
     }
+    const int64_t total_chunks = (T + CS - 1) / CS;
     const int64_t c_begin = static_cast<int64_t>(split) * chunks_per_split;
-    const int64_t total_chunks = (T + F_TC - 1) / F_TC;
     const int64_t c_end = c_begin + chunks_per_split < total_chunks ? c_begin + chunks_per_split : total_chunks;
-    float acc[16];
+
+    // staging map: a warp instruction covers 4 consecutive k x 8 consecutive samples
+    const int n_el = CS * n_pad;  // <= 8192: at most 32 per thread
+    float pre[32];
+    auto load_chunk = [&](int64_t c) {
+        const int64_t t0 = c * CS;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-    float m2 = 0.f, m4 = 0.f, mq = 0.f;
+        for (int j = 0; j < 32; ++j) {
+            const int e = tid + 256 * j;
+            if (e >= n_el) break;
+            const int wi = e >> 5, l = e & 31;
+            const int k = 4 * (wi % KQ) + (l & 3), t = 8 * (wi / KQ) + (l >> 2);
+            pre[j] = (t0 + t < T) ? __ldg(Xt + static_cast<int64_t>(k) * ldx + t0 + t) : 0.f;
+        }
+    };
+    auto store_chunk = [&]() {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int e = tid + 256 * j;
+            if (e >= n_el) break;
+            const int wi = e >> 5, l = e & 31;
+            const int k = 4 * (wi % KQ) + (l & 3), t = 8 * (wi / KQ) + (l >> 2);
+            Xs[t * SX + k] = pre[j];
+        }
+    };
+
+    float acc[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[r][j] = 0.f;
+    float m2 = 0.f, m4 = 0.f, mq = 0.f;  // moments of row tid % R
+    const int s1 = tid % CS, h1 = tid / CS;
+    const int q_lo = h1 * KQ / H, q_hi = (h1 + 1) * KQ / H;
+    const int q2 = tid % KQ, g2 = tid / KQ;
+
+    if (c_begin < c_end) load_chunk(c_begin);
     for (int64_t c = c_begin; c < c_end; ++c) {
-        const int64_t t0 = c * F_TC;
+        const int64_t t0 = c * CS;
+        __syncthreads();  // the previous chunk's readers are done with Xs / z3
+        store_chunk();
         __syncthreads();
-        for (int e = tid; e < n_pad * (F_TC / 4); e += 256) {
-            const int k = e / (F_TC / 4), c4 = (e % (F_TC / 4)) * 4;
-            const int64_t t = t0 + c4;
-            const float* src = Xt + static_cast<int64_t>(k) * ldx + t;
-            float4 v;
-            if (t + 3 < T) {
-                v = *reinterpret_cast<const float4*>(src);
-            } else {
-                v.x = t < T ? src[0] : 0.f;
-                v.y = t + 1 < T ? src[1] : 0.f;
-                v.z = t + 2 < T ? src[2] : 0.f;
-                v.w = t + 3 < T ? src[3] : 0.f;
-            }
-            *reinterpret_cast<float4*>(&Xs[k * F_XS + c4]) = v;
-        }
-        __syncthreads();
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k = 0; k < n_pad; ++k) {
-            const float b = Bs[ty * n_pad + k];
-            const float4 x = *reinterpret_cast<const float4*>(&Xs[k * F_XS + tx * 4]);
-            z[0] = fmaf(b, x.x, z[0]);
-            z[1] = fmaf(b, x.y, z[1]);
-            z[2] = fmaf(b, x.z, z[2]);
-            z[3] = fmaf(b, x.w, z[3]);
-        }
+        if (c + 1 < c_end) load_chunk(c + 1);
+        // pass 1: partial z over this thread's k-part, all R rows
+        {
+            float z[R];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float z2 = z[j] * z[j];
-            m2 += z2;
-            m4 = fmaf(z2, z2, m4);
+            for (int r = 0; r < R; ++r) z[r] = 0.f;
+            for (int q = q_lo; q < q_hi; ++q) {
+                const float4 x = *reinterpret_cast<const float4*>(&Xs[s1 * SX + 4 * q]);
+                const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                    for (int r4 = 0; r4 < R; r4 += 4) {
+                        const float4 b = *reinterpret_cast<const float4*>(&Bs[(4 * q + j) * R + r4]);
+                        z[r4 + 0] = fmaf(b.x, xv[j], z[r4 + 0]);
+                        z[r4 + 1] = fmaf(b.y, xv[j], z[r4 + 1]);
+                        z[r4 + 2] = fmaf(b.z, xv[j], z[r4 + 2]);
+                        z[r4 + 3] = fmaf(b.w, xv[j], z[r4 + 3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r4 = 0; r4 < R; r4 += 4)
+                *reinterpret_cast<float4*>(&zp[(h1 * CS + s1) * R + r4]) = make_float4(z[r4], z[r4 + 1], z[r4 + 2], z[r4 + 3]);
+        }
+        __syncthreads();
+        // z = sum of the parts; moments; z^3
+        for (int i = tid; i < CS * R; i += 256) {
+            const int s = i / R;
+            float z = 0.f;
+            for (int h = 0; h < H; ++h) z += zp[(h * CS + s) * R + (i % R)];
+            const float zz = z * z;
+            m2 += zz;
+            m4 = fmaf(zz, zz, m4);
             if (MOMENTS_ONLY) {
-                const float e = (t0 + tx * 4 + j < T) ? z2 - 1.f : 0.f;
+                const float e = (t0 + s < T) ? zz - 1.f : 0.f;
                 mq = fmaf(e, e, mq);
             } else {
-                Zs[(tx * 4 + j) * S_ZS + ty] = z2 * z[j];
+                z3[i] = zz * z;
             }
         }
         if (!MOMENTS_ONLY) {
             __syncthreads();
-            for (int t = 0; t < F_TC; ++t) {
-                const float zc = Zs[t * S_ZS + ty];
+            // pass 2: acc[r][4 q2 + j] += z^3_r(t) x~[t][4 q2 + j]
+            if (g2 < G) {
+                for (int t = g2; t < CS; t += G) {
+                    const float4 x = *reinterpret_cast<const float4*>(&Xs[t * SX + 4 * q2]);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (j >= kj) break;  // uniform exit: no predicated-off work for small n
-                    acc[j] = fmaf(zc, Xs[(tx + 16 * j) * F_XS + t], acc[j]);
+                    for (int r4 = 0; r4 < R; r4 += 4) {
+                        const float4 zc = *reinterpret_cast<const float4*>(&z3[t * R + r4]);
+                        const float zv[4] = {zc.x, zc.y, zc.z, zc.w};
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr) {
+                            acc[r4 + rr][0] = fmaf(zv[rr], x.x, acc[r4 + rr][0]);
+                            acc[r4 + rr][1] = fmaf(zv[rr], x.y, acc[r4 + rr][1]);
+                            acc[r4 + rr][2] = fmaf(zv[rr], x.z, acc[r4 + rr][2]);
+                            acc[r4 + rr][3] = fmaf(zv[rr], x.w, acc[r4 + rr][3]);
+                        }
+                    }
                 }
             }
         }
     }
+    // moments: threads with the same tid % R hold the same row
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
+    for (int o = R; o < 32; o <<= 1) {
         m2 += __shfl_xor_sync(0xffffffffu, m2, o);
         m4 += __shfl_xor_sync(0xffffffffu, m4, o);
         mq += __shfl_xor_sync(0xffffffffu, mq, o);
     }
-    if (ty >= M_act) return;
-    const int64_t prow = static_cast<int64_t>(split) * part_rows + ty;
-    if (tx == 0) {
-        part_mom[prow * 4 + 0] = m2;
-        part_mom[prow * 4 + 1] = m4;
-        part_mom[prow * 4 + 2] = mq;
-        part_mom[prow * 4 + 3] = 0.f;
+    __syncthreads();  // every reader of Xs / zp / z3 is done: the reduction area may alias them
+    if (lane < R) {
+        redm[(warp * R + lane) * 3 + 0] = m2;
+        redm[(warp * R + lane) * 3 + 1] = m4;
+        redm[(warp * R + lane) * 3 + 2] = mq;
+    }
+    if (!MOMENTS_ONLY && g2 < G) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            *reinterpret_cast<float4*>(&red[(g2 * R + r) * n_pad + 4 * q2]) =
+                make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    }
+    __syncthreads();
+    if (tid < R && tid < M_act) {
+        float a2 = 0.f, a4 = 0.f, aq = 0.f;
+        for (int w = 0; w < 8; ++w) {
+            a2 += redm[(w * R + tid) * 3 + 0];
+            a4 += redm[(w * R + tid) * 3 + 1];
+            aq += redm[(w * R + tid) * 3 + 2];
+        }
+        float* pm = part_mom + (static_cast<int64_t>(split) * part_rows + tid) * 4;
+        pm[0] = a2;
+        pm[1] = a4;
+        pm[2] = aq;
+        pm[3] = 0.f;
     }
     if (!MOMENTS_ONLY) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (j >= kj) break;
-            part_acc[prow * n_pad + tx + 16 * j] = acc[j];
+        for (int o = tid; o < R * n_pad; o += 256) {
+            const int r = o / n_pad, k = o % n_pad;
+            if (r >= M_act) continue;
+            float v = 0.f;
+            for (int g = 0; g < G; ++g) v += red[(g * R + r) * n_pad + k];
+            part_acc[(static_cast<int64_t>(split) * part_rows + r) * n_pad + k] = v;
         }
     }
 }
 
-cudaError_t launch_fused_fp32_small(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
-                                    const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
-                                    int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
-                                    int part_rows) {
-    const size_t smem = fp32_small_smem_bytes(n_pad);
+template <int R>
+cudaError_t launch_rows_variant(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
+                                const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
+                                int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
+                                int part_rows) {
+    const size_t smem = fp32_rows_smem_bytes(n_pad, R);
     cudaError_t e;
     if (moments_only) {
-        e = cudaFuncSetAttribute(fused_fp32_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(fused_fp32_rows_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        fused_fp32_small_kernel<true><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
-                                                                n_pad, T, chunks_per_split, part_acc, part_mom,
-                                                                part_rows);
+        fused_fp32_rows_kernel<R, true><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
+                                                                  n_pad, T, chunks_per_split, part_acc, part_mom,
+                                                                  part_rows);
     } else {
-        e = cudaFuncSetAttribute(fused_fp32_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(fused_fp32_rows_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        fused_fp32_small_kernel<false><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
-                                                                 n_pad, T, chunks_per_split, part_acc, part_mom,
-                                                                 part_rows);
+        fused_fp32_rows_kernel<R, false><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt,
+                                                                   ldx, n_pad, T, chunks_per_split, part_acc,
+                                                                   part_mom, part_rows);
     }
     return cudaGetLastError();
+}
+
+int fp32_rows_chunk(int n_pad) { return rows_cs(n_pad); }
+
+cudaError_t launch_fused_fp32_rows(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
+                                   const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
+                                   int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
+                                   int part_rows) {
+    if (part_rows == 4)
+        return launch_rows_variant<4>(s, moments_only, B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx, n_pad, T,
+                                      splits, chunks_per_split, part_acc, part_mom, part_rows);
+    if (part_rows == 16)
+        return launch_rows_variant<16>(s, moments_only, B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx, n_pad, T,
+                                       splits, chunks_per_split, part_acc, part_mom, part_rows);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,

@@ -13,26 +13,34 @@
 // used for the kurtosis of candidates, Eq. 2); the update variant accumulates the moments
 // only when asked (the first iterations, whose kurtosis trajectory is kept per restart).
 //
-// Warp roles (576 threads): warp 0 issues TMA loads, warp 1 allocates TMEM and issues MMAs
-// (one thread), warps 2..17 convert TMEM rows (warp w reads TMEM lanes 32*(w%4).., quarter
-// (w-2)/4 of the chunk's columns: four warps per scheduler keep the cube conversion, which at
-// small n is the longest stage of a chunk, off the critical path of the tensor pipe). Every wait is bounded (ICA_WAIT_NS): on timeout the CTA
-// raises the device status word, drains its outstanding copies and MMAs, frees TMEM and
-// returns.
+// Warp roles (608 threads): warp 0 issues TMA loads; warp 1 allocates TMEM and issues the first
+// products (one thread); warp 18 issues the second products (one thread); warps 2..17 convert
+// TMEM rows (warp w reads TMEM lanes 32*(w%4).., quarter (w-2)/4 of the chunk's columns). The two
+// issuing threads sit on different schedulers: measured on GB300, one thread issuing both
+// products spent about 100 cycles per tcgen05.mma while sharing its scheduler with four busy
+// epilogue warps, and splitting the issue cut the time of a 64 x 1024 x 2e6 step by a quarter.
+// Every wait is bounded (ICA_WAIT_NS): on timeout the CTA raises the device status word, drains
+// its outstanding copies and MMAs, frees TMEM and returns.
 #include "common.cuh"
 #include "internal.h"
 
 namespace ica {
 
-// Samples per chunk and number of Z / P buffers: with NB buffers the MMA thread issues the
-// first product NB-1 chunks ahead of the second, so the cube conversion of one chunk overlaps
-// the products of the next ones. TMEM holds D2 (n_pad columns) plus NB Z buffers of TC columns;
+// Samples per chunk and number of Z / P buffers: with NB buffers the first product runs up to
+// NB chunks ahead of the epilogue, so the cube conversion of one chunk overlaps the products of
+// the next ones. TMEM holds D2 (n_pad columns) plus NB Z buffers of TC columns;
 // shared memory must keep at least NB + 1 X~ stages in flight (NB stages are pinned by chunks
 // waiting for their second product).
 // Chunks are as wide as TMEM allows (fixed costs per chunk - barrier round trips and commits -
 // dominate at small n): n_pad <= 64 uses 192 samples (accumulator 64 columns + 2 x 192).
-int tc_chunk(int n_pad) { return n_pad <= 64 ? 192 : 64; }
-int tc_buffers(int n_pad) { return 2; }
+#ifndef ICA_TC_SMALL_CHUNK
+#define ICA_TC_SMALL_CHUNK 192
+#endif
+#ifndef ICA_TC_SMALL_NB
+#define ICA_TC_SMALL_NB 2
+#endif
+int tc_chunk(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_CHUNK : 64; }
+int tc_buffers(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_NB : 2; }
 // Optional K-major operand for the first product from a transposed copy of X~. Measured on GB300
 // the MN-major read of the X~ tile is as fast, so the copy is not used (saves its traffic).
 bool tc_transposed(int n_pad) { return false; }
@@ -40,7 +48,8 @@ bool tc_transposed(int n_pad) { return false; }
 namespace {
 constexpr int kBars = 40;
 constexpr int kEpiWarps = 16;
-constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kG2Warp = 2 + kEpiWarps;  // issues the second products
+constexpr int kThreads = 32 * (3 + kEpiWarps);
 constexpr uint32_t kScratchBytes = 8192u;  // barriers, TMEM slot, moment exchange
 struct TcLayout {
     uint32_t a_bytes, xsub_bytes, xn_bytes, xstage_bytes, p_bytes, stages, off_x, off_p, off_bar, total;
@@ -108,7 +117,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + off_bar);
     uint64_t* full = bars;          // [8]  X~ stage loaded
     uint64_t* empty = bars + 8;     // [8]  X~ stage released by the MMAs that read it
-    constexpr int LOOK = NB - 1;    // second product of chunk c is issued after the first of c+LOOK
     uint64_t* d1_full = bars + 16;  // [NB] Z chunk ready in TMEM
     uint64_t* d1_empty = bars + 19; // [NB] Z chunk read out by the 16 epilogue warps
     uint64_t* p_full = bars + 22;   // [NB] P chunk written to SMEM by the 16 epilogue warps
@@ -138,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&p_full[b], kEpiWarps);
         }
         mbar_init(d2_full, 1);
-        mbar_init(mma_done, 1);
+        mbar_init(mma_done, MOMENTS_ONLY ? 1 : 2);  // one commit per MMA-issuing thread
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
-    if (warp >= 2) {
+    if (warp >= 2 && warp < 2 + kEpiWarps) {
         // restart tile -> BF16, K-major, 128-byte swizzle: K-block kb (64 columns) at kb*16 KB
         const int et = threadIdx.x - 64;
         const int cpr = n_pad / 8;
@@ -177,6 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t tD2 = tmem;
     constexpr uint32_t kD1Col = TC == 192 ? 64u : (TC == 128 ? 128u : 256u);  // Z buffers after D2
+    static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
+    static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
 
     if (warp == 0) {
         // ------------------------------------------------------------------ TMA producer
@@ -206,57 +216,79 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------------ MMA issuer
+        // ------------------------------------------------------------------ first-product issuer
         if (lane == 0) {
             constexpr uint32_t id1 = idesc_bf16(128, TC, KT ? 0u : 1u);  // B: X~^T K-major, or X~ MN-major
-            const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(n_pad), 0);
             // Descriptors are built once; a K step only moves the start-address field (address >> 4,
             // bits 0-13), which cannot carry into the next field for shared addresses below 256 KB.
             const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
             const uint64_t b1_desc = KT ? sw128_desc(sX + xn_bytes, 16u, 1024u) : sw128_desc(sX, xsub_bytes, 1024u);
-            const uint64_t p_desc = sw128_desc(sP, 16u, 1024u);
-            const uint64_t x_desc = sw128_desc(sX, 16u, 1024u);
             const uint32_t stage16 = xstage_bytes >> 4;
             const int ksteps1 = n_pad / 16;
             bool ok = true;
-            for (int c = 0; c < nch + LOOK && ok; ++c) {
-                if (c < nch) {
-                    const int s = c % stages, b = c % NB;
-                    ok = mbar_wait(&full[s], static_cast<uint32_t>(c / stages) & 1u, abort_flag, status);
-                    if (ok && c >= NB)
-                        ok = mbar_wait(&d1_empty[b], static_cast<uint32_t>((c - NB) / NB) & 1u, abort_flag, status);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t d1 = tmem + kD1Col + static_cast<uint32_t>(b * TC);
-                    const uint64_t b1s = b1_desc + static_cast<uint64_t>(static_cast<uint32_t>(s) * stage16);
+            for (int c = 0; c < nch && ok; ++c) {
+                const int s = c % stages, b = c % NB;
+                ok = mbar_wait(&full[s], static_cast<uint32_t>(c / stages) & 1u, abort_flag, status);
+                if (ok && c >= NB)
+                    ok = mbar_wait(&d1_empty[b], static_cast<uint32_t>((c - NB) / NB) & 1u, abort_flag, status);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d1 = tmem + kD1Col + static_cast<uint32_t>(b * TC);
+                const uint64_t b1s = b1_desc + static_cast<uint64_t>(static_cast<uint32_t>(s) * stage16);
 #pragma unroll
-                    for (int ks = 0; ks < 16; ++ks) {
-                        if (ks >= ksteps1) break;
-                        const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
-                        const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
-                                                  : (static_cast<uint32_t>(ks) * 2048u) >> 4;
-                        umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
-                    }
-                    umma_commit(&d1_full[b]);
-                    if (MOMENTS_ONLY) umma_commit(&empty[s]);
+                for (int ks = 0; ks < 16; ++ks) {
+                    if (ks >= ksteps1) break;
+                    const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                    const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
+                                              : (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                    umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                 }
-                if (!MOMENTS_ONLY && c >= LOOK) {
-                    const int cp = c - LOOK, sp = cp % stages, bp = cp % NB;
-                    ok = mbar_wait(&p_full[bp], static_cast<uint32_t>(cp / NB) & 1u, abort_flag, status);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint64_t ps = p_desc + static_cast<uint64_t>((static_cast<uint32_t>(bp) * p_bytes) >> 4);
-                    const uint64_t xs = x_desc + static_cast<uint64_t>(static_cast<uint32_t>(sp) * stage16);
+                umma_commit(&d1_full[b]);
+                if (MOMENTS_ONLY) umma_commit(&empty[s]);  // no second product reads the stage
+            }
+            umma_commit(mma_done);
+            mbar_drain(mma_done, 0u, status);
+        }
+    } else if (warp == kG2Warp) {
+        // ------------------------------------------------------------------ second-product issuer
+        // A thread of its own (on another scheduler than the first-product issuer), so that the
+        // two instruction streams overlap; the products write different TMEM columns and every
+        // shared operand they share is ordered by the barriers (P(c) exists only after the
+        // first product of chunk c retired and the epilogue consumed it).
+        if (!MOMENTS_ONLY && lane == 0) {
+            const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(n_pad), 0);
+            const uint32_t dacc = tD2;
+            // Per-K-step descriptors of stage 0 / buffer 0, built once: inside the chunk loop an MMA
+            // costs two 64-bit adds (stage and buffer offsets) besides the instruction itself.
+            constexpr int KS2 = TC / 16;
+            uint64_t pd[KS2], xd[KS2];
 #pragma unroll
-                    for (int ks = 0; ks < TC / 16; ++ks) {
-                        const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
-                        const uint32_t b_off = ((ks >> 2) * xsub_bytes + (ks & 3) * 32u) >> 4;
-                        umma_bf16(tD2, ps + a_off, xs + b_off, id2, (cp > 0 || ks > 0) ? 1u : 0u);
-                    }
-                    umma_commit(&empty[sp]);  // releases the X~ stage and the P buffer
+            for (int j = 0; j < KS2; ++j) {
+                const uint32_t ks = static_cast<uint32_t>(j);
+                pd[j] = sw128_desc(sP + (ks >> 2) * 16384u + (ks & 3u) * 32u, 16u, 1024u);
+                xd[j] = sw128_desc(sX + (ks >> 2) * xsub_bytes + (ks & 3u) * 32u, 16u, 1024u);
+            }
+            const uint32_t stage16 = xstage_bytes >> 4;
+            bool ok = true;
+            int s = 0, b = 0;
+            uint32_t par = 0u;
+            for (int c = 0; c < nch && ok; ++c) {
+                ok = mbar_wait(&p_full[b], par, abort_flag, status);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t po = static_cast<uint64_t>((static_cast<uint32_t>(b) * p_bytes) >> 4);
+                const uint64_t xo = static_cast<uint64_t>(static_cast<uint32_t>(s) * stage16);
+                umma_bf16(dacc, pd[0] + po, xd[0] + xo, id2, c > 0 ? 1u : 0u);
+#pragma unroll
+                for (int j = 1; j < KS2; ++j) umma_bf16_acc(dacc, pd[j] + po, xd[j] + xo, id2);
+                umma_commit(&empty[s]);  // releases the X~ stage and the P buffer
+                if (++s == stages) s = 0;
+                if (++b == NB) {
+                    b = 0;
+                    par ^= 1u;
                 }
             }
-            if (!MOMENTS_ONLY) umma_commit(d2_full);
+            umma_commit(d2_full);
             umma_commit(mma_done);
             mbar_drain(mma_done, 0u, status);
         }
@@ -411,7 +443,7 @@ cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, con
         return moments ? launch_tc_impl<TCV, NBV, KTV, false, true>(ICA_TC_ARGS)                    \
                        : launch_tc_impl<TCV, NBV, KTV, false, false>(ICA_TC_ARGS);                  \
     } while (0)
-    if (TC == 192) ICA_TC_DISPATCH(192, 2, false);
+    if (n_pad <= 64) ICA_TC_DISPATCH(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB, false);
     if (KT) ICA_TC_DISPATCH(64, 2, true);
     ICA_TC_DISPATCH(64, 2, false);
 #undef ICA_TC_DISPATCH
