@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-step", type=int, default=0, metavar="T",
+                    help="instead of fits: time ica_fp_step (BF16) at the workload's N and M on T random "
+                         "samples (used for ncu captures of the fused kernel on data larger than L2)")
     return ap.parse_args()
 
 
@@ -320,8 +323,20 @@ def run_ours(args):
     it = kinds.get("iteration", {"launches": 0, "ms": 0.0, "flops": 0.0})
     achieved = it["flops"] / (it["ms"] / 1e3) / 1e12 if it["ms"] > 0 else 0.0
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    # DRAM traffic per iteration launch: ncu measured 260.1 MB read+written for one launch at
+    # n = 64, M = 1024, T = 2e6 against 256.0 MB of algorithmic X~ reads (ratio 1.016; the
+    # split partials are the rest). Scaled here to the fit's mean algorithmic X~ bytes per launch.
+    xt_bytes = 0.0
+    if stats:
+        for comp in stats[-1].get("components", []):
+            n_c = N - comp["i"]
+            xt_bytes += comp["iterations"] * ((n_c + 15) // 16 * 16) * T * 2.0
+    traffic = 1.016 * xt_bytes / max(1, it["launches"] / max(1, args.steps)) if xt_bytes else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "fused_tc_kernel (BF16 iteration)",
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "ncu dram read+write of one launch at n=64 M=1024 T=2e6 / algorithmic X~ bytes "
+                                "(1.016), times the fit's mean algorithmic bytes per launch",
+                "kernel": "fused_tc_kernel (BF16 iteration)",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "launches": it["launches"], "avg_launch_ms": it["ms"] / max(1, it["launches"]),
                 "share_of_step": it["ms"] / total_ms}
@@ -359,8 +374,43 @@ def run_ours(args):
     return 0
 
 
+def run_kernel_step(args):
+    """One fused BF16 update step (the iteration kernel plus the split combine), repeated."""
+    import torch
+
+    from paper_2408_17118_gb300 import ica
+
+    w = workload(args.config, args.seed)
+    n, M, T = w.X.shape[0], w.M, args.kernel_step
+    dev = torch.device("cuda", 0)
+    ctx = ica.Context(0)
+    g = torch.Generator(device=dev).manual_seed(args.seed)
+    n_pad = (n + 15) // 16 * 16
+    ld = (T + 7) // 8 * 8
+    Xt = torch.zeros((n_pad, ld), device=dev, dtype=torch.bfloat16)
+    Xt[:n] = torch.randn((n, ld), device=dev, generator=g).to(torch.bfloat16)
+    B = torch.zeros((M, n_pad), device=dev)
+    B[:, :n] = torch.nn.functional.normalize(torch.randn((M, n), device=dev, generator=g), dim=1)
+    for _ in range(max(args.warmup, 1)):
+        ica.ica_fp_step(ctx, ica.ICA_BF16, B, n, Xt, T)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ica.ica_fp_step(ctx, ica.ICA_BF16, B, n, Xt, T)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "kernel_step", "n": n, "M": M, "T": T, "ms_per_call": ms,
+                      "note": "ica_fp_step is synchronous: the time includes the call's host overhead"}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.kernel_step:
+        return run_kernel_step(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

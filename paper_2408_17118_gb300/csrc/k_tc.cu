@@ -47,7 +47,12 @@ bool tc_transposed(int n_pad) { return false; }
 
 namespace {
 constexpr int kBars = 40;
-constexpr int kEpiWarps = 16;
+#ifndef ICA_TC_EPI_WARPS
+#define ICA_TC_EPI_WARPS 16
+#endif
+constexpr int kEpiWarps = ICA_TC_EPI_WARPS;  // 4 lane quarters x kEpiWarps / 4 column groups
+constexpr int kGroups = kEpiWarps / 4;
+static_assert(kEpiWarps == 8 || kEpiWarps == 16, "two or four column groups");
 constexpr int kG2Warp = 2 + kEpiWarps;  // issues the second products
 constexpr int kThreads = 32 * (3 + kEpiWarps);
 constexpr uint32_t kScratchBytes = 8192u;  // barriers, TMEM slot, moment exchange
@@ -295,10 +300,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------------ epilogue warps
         const int q = warp & 3;
-        const int h = (warp - 2) >> 2;  // column quarter 0..3
+        const int h = (warp - 2) >> 2;  // column group 0..kGroups-1
         const int row = q * 32 + lane;
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-        constexpr int CW = TC / 4;
+        constexpr int CW = TC / kGroups;
         float2 s2 = make_float2(0.f, 0.f), s4 = make_float2(0.f, 0.f);
         float sq = 0.f;
         bool ok = true;
@@ -309,9 +314,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             float v[CW];
             const uint32_t d1 = tmem + kD1Col + static_cast<uint32_t>(b * TC) + lane_off + static_cast<uint32_t>(h * CW);
-            if constexpr (CW >= 32) tmem_ld32(d1, *reinterpret_cast<float(*)[32]>(&v[0]));
-            if constexpr (CW == 64) tmem_ld32(d1 + 32u, *reinterpret_cast<float(*)[32]>(&v[32]));
-            if constexpr (CW % 32 == 16) tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
+            // as few loads as possible: 64-, then 32-, then 16-column pieces
+            constexpr int N64 = CW / 64, N32 = (CW % 64) / 32, N16 = (CW % 32) / 16;
+            static_assert(CW % 16 == 0, "column group must be a multiple of 16");
+#pragma unroll
+            for (int i = 0; i < N64; ++i)
+                tmem_ld64(d1 + static_cast<uint32_t>(64 * i), *reinterpret_cast<float(*)[64]>(&v[64 * i]));
+            if constexpr (N32 == 1) tmem_ld32(d1 + static_cast<uint32_t>(64 * N64), *reinterpret_cast<float(*)[32]>(&v[64 * N64]));
+            if constexpr (N16 == 1)
+                tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (h == 0 && grow < M_act) {
             float m2 = s2.x + s2.y, m4 = s4.x + s4.y, mq = sq;
 #pragma unroll
-            for (int hh = 0; hh < 3; ++hh) {  // fixed order: quarters 1, 2, 3
+            for (int hh = 0; hh < kGroups - 1; ++hh) {  // fixed order: groups 1, 2, ...
                 const float* src = mom_sm + (hh * kTcRows + row) * 4;
                 m2 += src[0];
                 m4 += src[1];
