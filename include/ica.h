@@ -13,7 +13,8 @@
  *     workspace is set the library allocates no device memory (the optional plain FP32
  *     comparator creates a cuBLAS handle on first use, which allocates inside cuBLAS).
  *   - Work is enqueued on the context's stream (ica_set_stream). ica_order_fit synchronises
- *     that stream after every iteration (it reads the active-restart count); ica_whiten,
+ *     that stream on a sparse schedule of iterations (it reads the active-restart count, every
+ *     iteration at first, then every second and every fourth); ica_whiten,
  *     ica_deflation_basis, ica_fp_step and ica_kurtosis synchronise once at the end to read
  *     the device status word; ica_init_restarts and ica_reduce only enqueue.
  *   - The return value is an ica_status. Nothing is thrown across the ABI. After an error the
@@ -69,11 +70,27 @@ typedef struct {
     int profile;           /* 1: time every fused launch with CUDA events on the context stream
                               and report per-kind totals (launches, ms, algorithmic FLOPs) in
                               ica_last_stats */
+    /* Learned restart pruner (not part of the paper's method; see ica_mlp_* below). */
+    const float* prune_params; /* optional: ICA_MLP_PARAMS floats (device). After the first 5
+                              iterations of a component, restarts whose predicted probability of
+                              ending at the picked direction is below prune_tau leave the active
+                              set and the pick. If a pruned restart's kurtosis objective is at
+                              least the best kept one, or the pruner dropped every active
+                              restart, the component is fitted again without pruning from the
+                              same initial restarts (reported as "fallback" in ica_last_stats).
+                              NULL: no pruning. Ignored by ICA_PLAIN_FP32. */
+    float prune_tau;       /* keep-probability threshold (default 0.05) */
+    float* record_features; /* optional (device): n_components x M x ICA_MLP_IN raw pruner inputs
+                              of every restart (alpha at iterations 1..5, step distance at 1..5,
+                              n = N - i + 1, log T), for training the pruner */
+    float* record_labels;  /* optional (device, with record_features): n_components x M labels,
+                              1 when the restart ended at the picked direction
+                              (|b_r . b_p| >= 1 - 1e-3), else 0 */
 } ica_opts;
 
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 100,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
-   no profiling. */
+   no profiling, no pruner (prune_tau 0.05), no recording. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */
@@ -190,6 +207,45 @@ int ica_kurtosis(ica_ctx* ctx, int precision, const float* B, int M, int n, cons
      synchronises it once at the end to read the status word. */
 int ica_fp_step_noalloc(int precision, const float* B, int M, int n, const void* Xt, int64_t T,
                         int64_t ldx, float* Bnew, float* moments, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+   Learned restart pruner: a 12-64-64-1 perceptron (ReLU, sigmoid output) trained on the
+   trajectories the method itself records (record_features / record_labels above). Not part of
+   the paper. Parameter vector layout (ICA_MLP_PARAMS FP32 values, device):
+     mean[12], scale[12]        input standardisation x_hat = (x - mean) * scale
+     W1[64][12], b1[64]         h1 = relu(W1 x_hat + b1)
+     W2[64][64], b2[64]         h2 = relu(W2 h1 + b2)
+     w3[64], b3                 p = sigmoid(w3 . h2 + b3)
+   Feature rows (ICA_MLP_IN FP32 values): alpha at iterations 1..5, step distance at 1..5, n,
+   log T. The kernels keep FP32 master weights; with fp16 = 1 weights and activations are
+   rounded to FP16 (accumulation stays FP32), fp16 = 0 runs everything in FP32.
+   --------------------------------------------------------------------------------------- */
+#define ICA_MLP_IN 12
+#define ICA_MLP_HIDDEN 64
+#define ICA_MLP_PARAMS 5081
+
+/* He-initialised weights (Philox4x32-10 keyed by seed), zero biases, mean 0, scale 1. */
+int ica_mlp_init(ica_ctx* ctx, uint64_t seed, float* params);
+
+/* Sets mean and scale of params from rows x ICA_MLP_IN feature rows F (population moments). */
+int ica_mlp_standardize(ica_ctx* ctx, const float* F, int rows, float* params);
+
+/* prob[r] = network output for feature row r (rows >= 1). Only enqueues. */
+int ica_mlp_forward(ica_ctx* ctx, const float* params, const float* F, int rows, int fp16, float* prob);
+
+/* Device scratch bytes ica_mlp_train_step needs for `rows` samples. */
+size_t ica_mlp_scratch_bytes(int rows);
+
+/* One full-batch training step on rows samples (labels 0/1): weighted binary cross-entropy
+   L = -(1/rows) sum [pos_weight y log p + (1 - y) log(1 - p)], its gradient by
+   back-propagation, then (lr > 0) one Adam update (beta 0.9, 0.999, eps 1e-8, bias-corrected
+   with `step` >= 1) of every parameter except mean and scale. adam_m, adam_v: ICA_MLP_PARAMS
+   floats each, zero before the first step. loss (1 float) and grad (ICA_MLP_PARAMS floats,
+   mean and scale entries 0) are optional device outputs. scratch: caller-owned device memory of
+   at least ica_mlp_scratch_bytes(rows). Deterministic (fixed reduction order). Only enqueues. */
+int ica_mlp_train_step(ica_ctx* ctx, float* params, float* adam_m, float* adam_v, int step, const float* F,
+                       const float* labels, int rows, float lr, float pos_weight, int fp16, void* scratch,
+                       size_t scratch_bytes, float* loss, float* grad);
 
 #ifdef __cplusplus
 }

@@ -34,10 +34,20 @@ class ica_opts(C.Structure):
         ("B0", C.c_void_p),
         ("max_splits", C.c_int),
         ("profile", C.c_int),
+        ("prune_params", C.c_void_p),
+        ("prune_tau", C.c_float),
+        ("record_features", C.c_void_p),
+        ("record_labels", C.c_void_p),
     ]
 
 
-vp, i32, i64, u64, f64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
+# learned restart pruner (include/ica.h)
+ICA_MLP_IN = 12
+ICA_MLP_HIDDEN = 64
+ICA_MLP_PARAMS = 5081
+
+
+vp, i32, i64, u64, f64, sz, f32 = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t, C.c_float
 
 # name -> (restype, argtypes); exactly the functions declared in include/ica.h
 SIGNATURES = {
@@ -57,6 +67,11 @@ SIGNATURES = {
     "ica_fp_step": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_kurtosis": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_fp_step_noalloc": (i32, [i32, vp, i32, i32, vp, i64, i64, vp, vp, vp]),
+    "ica_mlp_init": (i32, [vp, u64, vp]),
+    "ica_mlp_standardize": (i32, [vp, vp, i32, vp]),
+    "ica_mlp_forward": (i32, [vp, vp, vp, i32, i32, vp]),
+    "ica_mlp_scratch_bytes": (sz, [i32]),
+    "ica_mlp_train_step": (i32, [vp, vp, vp, vp, i32, vp, vp, i32, f32, f32, i32, vp, sz, vp, vp]),
 }
 
 _lib = None

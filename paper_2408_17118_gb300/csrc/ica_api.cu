@@ -1,7 +1,8 @@
 // Host driver and C ABI of the ordering-ICA library. Implements Algorithm 2 (fast ordering ICA
 // in matrix form, with removal of converged rows and reduction of signals) on one GPU:
 // every arithmetic step runs in this library's kernels; the host only orders launches, picks
-// launch shapes and reads back the active-restart count once per iteration.
+// launch shapes and reads back the active-restart count on a sparse schedule.
+#include <cmath>
 #include <dlfcn.h>
 #include <math.h>
 #include <stdio.h>
@@ -58,10 +59,10 @@ struct ica_ctx {
 
 // kinds of timed fused launches
 // kinds of timed launches: the four fused kernels, then the remaining phases of a component
-enum { K_ITER = 0, K_KURT = 1, K_REFINE = 2, K_REFKURT = 3, K_FINALIZE = 4, K_COMPACT = 5, K_BASIS = 6,
+enum { K_ITER = 0, K_KURT = 1, K_REFINE = 2, K_REFKURT = 3, K_FINALIZE = 4, K_PRUNE = 5, K_BASIS = 6,
        K_REDUCE = 7, K_SELECT = 8, K_APPEND = 9, K_NKINDS = 10 };
 static const char* kKindName[K_NKINDS] = {"iteration", "kurtosis", "refine", "refine_kurtosis", "finalize",
-                                          "compact", "basis", "reduce", "select", "append"};
+                                          "prune", "basis", "reduce", "select", "append"};
 
 #define CK(call)                                      \
     do {                                              \
@@ -85,7 +86,7 @@ struct Layout {
     int n_pad_max = 0, M_pad = 0, part_rows_max = 0;
     int64_t ldx = 0;
     int tcols = 0;  // row length (elements) of the transposed BF16 copy
-    size_t status, counts, Xt32, Xt16, Xt16t, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots,
+    size_t status, counts, Xt32, Xt16, Xt16t, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots, pruned,
         part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, comp_rows, total;
 };
 
@@ -122,6 +123,7 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.ups = take(sizeof(double) * L.M_pad);
     L.excl = take(sizeof(int) * L.M_pad);
     L.slots = take(sizeof(int) * 64);
+    L.pruned = take(sizeof(int) * L.M_pad);
     L.part_acc = take(sizeof(float) * static_cast<size_t>(L.part_rows_max) * L.n_pad_max);
     L.part_mom = take(sizeof(float) * static_cast<size_t>(L.part_rows_max) * 4);
     L.G = take(sizeof(double) * nN);
@@ -406,6 +408,10 @@ void ica_default_opts(ica_opts* o) {
     o->fp32_tol_floor = 1e-6;
     o->B0 = nullptr;
     o->max_splits = 0;
+    o->prune_params = nullptr;
+    o->prune_tau = 0.05f;
+    o->record_features = nullptr;
+    o->record_labels = nullptr;
 }
 
 const char* ica_status_string(int st) {
@@ -694,7 +700,9 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     cudaEvent_t fit_begin = fit_ev.e[0], fit_end = fit_ev.e[1];
     CK(cudaEventRecord(fit_begin, s));
     const double dT = static_cast<double>(T);
-    std::vector<int> comp_iters, comp_refine;
+    std::vector<int> comp_iters, comp_refine, comp_pruned, comp_fallback;
+    const bool prune_opt = o.prune_params != nullptr && o.precision != ICA_PLAIN_FP32;
+    int* pruned = at<int>(c, L.pruned);
     std::vector<std::vector<int>> comp_hist;
     int found = 0;
     for (int i = 0; i < n_components; ++i) {
@@ -710,72 +718,113 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             return ICA_OK;
         });
         if (rc) return rc;
-        // initial restarts
-        KL(launch_init_restarts(s, seed, i, M, n, n_pad, o.B0 ? o.B0 + static_cast<int64_t>(i) * M * N : nullptr, N,
-                                B32));
-        CK(cudaMemsetAsync(itc, 0, sizeof(int) * M, s));
-        CK(cudaMemsetAsync(traj, 0, sizeof(float) * M * kTrajLen * 2, s));
-        KL(launch_iota(s, act[0], M, counts + 0));
-        FusedArgs fa;
-        fa.precision = o.precision;
-        fa.B32 = B32;
-        fa.ldb = n_pad;
-        fa.n_pad = n_pad;
-        fa.T = T;
-        fa.Xt32 = Xt32;
-        fa.Xt16 = Xt16;
-        fa.Xt16t = want_t ? at<uint16_t>(c, L.Xt16t) : nullptr;
-        fa.tcols = L.tcols;
-        fa.ldx = ldx;
-        fa.max_splits = o.max_splits;
-        // fixed-point iterations with removal of converged rows (Algorithm 2, Section 3.2)
-        int cur = 0, M_host = M, t = 0;
+        // Attempt 0 may run the learned pruner after kTrajLen iterations; when the pruned restarts
+        // look at least as good as the kept ones (prune_check), the component is fitted again
+        // without pruning from the same initial restarts (attempt 1).
+        int t = 0, rt = 0, n_pruned = 0, fell_back = 0;
         std::vector<int> hist;
-        while (t < iters && M_host > 0) {
-            StepShape sh;
-            fa.act = act[cur];
-            fa.count_dev = counts + cur;
-            fa.M_act = M_host;
-            fa.moments_only = false;
-            fa.moments = t < kTrajLen;
-            rc = timed(K_ITER, 4.0 * n * M_host * dT, [&] { return run_fused(c, L, fa, &sh); });
-            if (rc) return rc;
-            rc = timed(K_FINALIZE, 0.0, [&] {
-                KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
-                                   n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
-                                   o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
-                                   counts + (cur ^ 1), crows + 2 * i, done_ctr));
-                return ICA_OK;
-            });
-            if (rc) return rc;
-            cur ^= 1;
-            ++t;
-            if (sync_due(t)) {
-                rc = read_count(counts + cur, &M_host);
+        bool pruned_now = false, dropped_all = false;
+        FusedArgs fa;
+        for (int attempt = 0;; ++attempt) {
+            const bool prune_this = prune_opt && attempt == 0;
+            pruned_now = false;
+            dropped_all = false;
+            hist.clear();
+            if (prune_opt) CK(cudaMemsetAsync(pruned, 0, sizeof(int) * M, s));
+            // initial restarts
+            KL(launch_init_restarts(s, seed, i, M, n, n_pad, o.B0 ? o.B0 + static_cast<int64_t>(i) * M * N : nullptr, N,
+                                    B32));
+            CK(cudaMemsetAsync(itc, 0, sizeof(int) * M, s));
+            CK(cudaMemsetAsync(traj, 0, sizeof(float) * M * kTrajLen * 2, s));
+            KL(launch_iota(s, act[0], M, counts + 0));
+            fa = FusedArgs();
+            fa.precision = o.precision;
+            fa.B32 = B32;
+            fa.ldb = n_pad;
+            fa.n_pad = n_pad;
+            fa.T = T;
+            fa.Xt32 = Xt32;
+            fa.Xt16 = Xt16;
+            fa.Xt16t = want_t ? at<uint16_t>(c, L.Xt16t) : nullptr;
+            fa.tcols = L.tcols;
+            fa.ldx = ldx;
+            fa.max_splits = o.max_splits;
+            // fixed-point iterations with removal of converged rows (Algorithm 2, Section 3.2)
+            int cur = 0, M_host = M;
+            t = 0;
+            while (t < iters && M_host > 0) {
+                StepShape sh;
+                fa.act = act[cur];
+                fa.count_dev = counts + cur;
+                fa.M_act = M_host;
+                fa.moments_only = false;
+                fa.moments = t < kTrajLen;
+                rc = timed(K_ITER, 4.0 * n * M_host * dT, [&] { return run_fused(c, L, fa, &sh); });
                 if (rc) return rc;
-                hist.push_back(M_host);
+                rc = timed(K_FINALIZE, 0.0, [&] {
+                    KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
+                                       n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
+                                       o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
+                                       counts + (cur ^ 1), crows + 2 * i, done_ctr));
+                    return ICA_OK;
+                });
+                if (rc) return rc;
+                cur ^= 1;
+                ++t;
+                if (sync_due(t)) {
+                    rc = read_count(counts + cur, &M_host);
+                    if (rc) return rc;
+                    hist.push_back(M_host);
+                }
+                if (prune_this && t == kTrajLen && t < iters) {
+                    // learned pruner on the first kTrajLen iterations' trajectories
+                    int before = M_host;
+                    rc = timed(K_PRUNE, 0.0, [&] {
+                        KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, n,
+                                        std::log(static_cast<double>(T)), o.prune_tau, flags, pruned));
+                        KL(launch_compact_keep(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1)));
+                        return ICA_OK;
+                    });
+                    if (rc) return rc;
+                    cur ^= 1;
+                    rc = read_count(counts + (cur ^ 1), &before);  // exact count before pruning
+                    if (rc) return rc;
+                    rc = read_count(counts + cur, &M_host);
+                    if (rc) return rc;
+                    n_pruned = before - M_host;
+                    hist.push_back(M_host);
+                    pruned_now = true;
+                    dropped_all = before > 0 && M_host == 0;
+                }
             }
-        }
-        // kurtosis of every candidate: converged rows plus rows still running after `iters`
-        {
-            StepShape sh;
-            fa.act = nullptr;
-            fa.count_dev = nullptr;
-            fa.M_act = M;
-            fa.moments_only = true;
-            rc = timed(K_KURT, 2.0 * n * M * dT, [&] { return run_fused(c, L, fa, &sh); });
+            // kurtosis of every candidate: converged rows plus rows still running after `iters`
+            {
+                StepShape sh;
+                fa.act = nullptr;
+                fa.count_dev = nullptr;
+                fa.M_act = M;
+                fa.moments_only = true;
+                rc = timed(K_KURT, 2.0 * n * M * dT, [&] { return run_fused(c, L, fa, &sh); });
+                if (rc) return rc;
+                KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, nullptr, M, inv_T,
+                                        alpha, ups));
+            }
+            if (!pruned_now) break;
+            int fb = 0;
+            KL(launch_prune_check(s, ups, pruned, M, counts + 4));
+            rc = read_count(counts + 4, &fb);
             if (rc) return rc;
-            KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, nullptr, M, inv_T,
-                                    alpha, ups));
+            if (!fb && !dropped_all) break;
+            fell_back = 1;  // the pruned restarts may hold the optimum: refit without pruning
         }
-        int rt = 0;
+        const int* excl0 = pruned_now ? pruned : nullptr;  // restarts dropped by the pruner
         if (!bf16) {
-            KL(launch_argmax(s, ups, nullptr, nullptr, nullptr, M, slots));
+            KL(launch_argmax(s, ups, excl0, nullptr, nullptr, M, slots));
         } else {
             // distinct top-k candidates, FP32 refinement, FP32 kurtosis, argmax among them
             const int k = o.refine_topk;
             rc = timed(K_SELECT, 0.0, [&] {
-                KL(launch_select_clear(s, excl, M, cand, k));
+                KL(launch_select_clear(s, excl, excl0, M, cand, k));
                 for (int j = 0; j < k; ++j) {
                     KL(launch_argmax(s, ups, excl, nullptr, nullptr, M, cand + j));
                     KL(launch_exclude(s, B32, n_pad, n, M, cand + j, excl, 1.0 - 1e-3));
@@ -822,6 +871,10 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                                     inv_T, alpha, ups));
             KL(launch_argmax(s, ups, nullptr, cand_list, counts + 2, k, slots));
         }
+        if (o.record_features && o.record_labels)
+            KL(launch_record(s, traj, B32, n_pad, n, M, slots, std::log(static_cast<double>(T)),
+                             o.record_features + static_cast<int64_t>(i) * M * kMlpIn,
+                             o.record_labels + static_cast<int64_t>(i) * M));
         // w_i = b_p G appended to W (Algorithm 2)
         rc = timed(K_APPEND, 0.0, [&] {
             KL(launch_append(s, G, n, N, B32, n_pad, slots, alpha, ups, W_out, i, kurt_out + i, cstats + 4 * i));
@@ -830,6 +883,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         if (rc) return rc;
         comp_iters.push_back(t);
         comp_refine.push_back(rt);
+        comp_pruned.push_back(n_pruned);
+        comp_fallback.push_back(fell_back);
         comp_hist.push_back(hist);
         if (o.profile) {
             CK(cudaStreamSynchronize(s));
@@ -881,9 +936,10 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         char buf[256];
         snprintf(buf, sizeof(buf),
                  "%s{\"i\": %d, \"iterations\": %d, \"winner\": %d, \"alpha\": %.12g, \"upsilon\": %.12g, "
-                 "\"refine_iterations\": %d, \"rows_updated\": %lld, \"refine_rows\": %lld, \"active\": [",
+                 "\"refine_iterations\": %d, \"rows_updated\": %lld, \"refine_rows\": %lld, \"pruned\": %d, "
+                 "\"fallback\": %d, \"active\": [",
                  i ? ", " : "", i + 1, comp_iters[i], static_cast<int>(p), a_p, u_p, comp_refine[i], rows_h[2 * i],
-                 rows_h[2 * i + 1]);
+                 rows_h[2 * i + 1], comp_pruned[i], comp_fallback[i]);
         js += buf;
         for (size_t h = 0; h < comp_hist[i].size(); ++h) {
             snprintf(buf, sizeof(buf), "%s%d", h ? ", " : "", comp_hist[i][h]);
@@ -927,3 +983,47 @@ int ica_last_stats(ica_ctx* c, char* buf, size_t cap) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Learned restart pruner: network kernels (k_mlp.cu) behind the C ABI.
+// ---------------------------------------------------------------------------------------------
+static_assert(ICA_MLP_PARAMS == ica::kMlpParams && ICA_MLP_IN == ica::kMlpIn, "pruner layout");
+
+int ica_mlp_init(ica_ctx* c, uint64_t seed, float* params) {
+    if (!c || !params) return ICA_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    KL(launch_mlp_init(c->stream, seed, params));
+    return ICA_OK;
+}
+
+int ica_mlp_standardize(ica_ctx* c, const float* F, int rows, float* params) {
+    if (!c || !F || !params || rows < 1) return ICA_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    KL(launch_mlp_standardize(c->stream, F, rows, params));
+    return ICA_OK;
+}
+
+int ica_mlp_forward(ica_ctx* c, const float* params, const float* F, int rows, int fp16, float* prob) {
+    if (!c || !params || !F || !prob || rows < 1) return ICA_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    KL(launch_mlp_forward(c->stream, params, F, rows, fp16 != 0, prob));
+    return ICA_OK;
+}
+
+size_t ica_mlp_scratch_bytes(int rows) { return rows < 1 ? 0 : mlp_scratch_bytes(rows); }
+
+int ica_mlp_train_step(ica_ctx* c, float* params, float* adam_m, float* adam_v, int step, const float* F,
+                       const float* labels, int rows, float lr, float pos_weight, int fp16, void* scratch,
+                       size_t scratch_bytes, float* loss, float* grad) {
+    if (!c || !params || !adam_m || !adam_v || !F || !labels || rows < 1 || step < 1 || !scratch ||
+        !(lr >= 0.f) || !(pos_weight > 0.f))
+        return ICA_ERR_ARG;
+    if (scratch_bytes < mlp_scratch_bytes(rows)) return ICA_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(scratch) % 16) return ICA_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    KL(launch_mlp_train_step(c->stream, params, adam_m, adam_v, step, F, labels, rows, lr, pos_weight, fp16 != 0,
+                             static_cast<float*>(scratch), loss, grad));
+    c->launches += 2;  // three kernels: forward/backward, gradient slices, Adam
+    c->launches_total += 2;
+    return ICA_OK;
+}

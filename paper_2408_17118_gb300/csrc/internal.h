@@ -33,7 +33,7 @@ cudaError_t launch_compact_cand(cudaStream_t s, const int* cand, int k, int* lis
 cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int splits, int part_rows,
                                  const int* act_idx, const int* count_dev, int count, double inv_T, double* alpha,
                                  double* ups);
-cudaError_t launch_select_clear(cudaStream_t s, int* excluded, int M, int* cand, int kmax);
+cudaError_t launch_select_clear(cudaStream_t s, int* excluded, const int* init, int M, int* cand, int kmax);
 cudaError_t launch_argmax(cudaStream_t s, const double* ups, const int* excluded, const int* subset,
                           const int* count_dev, int count, int* out_slot);
 cudaError_t launch_exclude(cudaStream_t s, const float* B32, int ldb, int n, int M, const int* sel_slot,
@@ -81,6 +81,26 @@ cudaError_t launch_fused_fp32_rows(cudaStream_t s, bool moments_only, const floa
                                    const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
                                    int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
                                    int part_rows);
+
+// ---- k_mlp.cu (learned restart pruner) ----
+constexpr int kMlpIn = 12, kMlpHid = 64;
+constexpr int kMlpParams = 2 * kMlpIn + kMlpHid * kMlpIn + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid + 1;
+constexpr int kActRow = 272;  // floats of training activations per sample
+int mlp_slices(int rows);
+size_t mlp_scratch_bytes(int rows);
+cudaError_t launch_mlp_init(cudaStream_t s, uint64_t seed, float* params);
+cudaError_t launch_mlp_standardize(cudaStream_t s, const float* F, int rows, float* params);
+cudaError_t launch_mlp_forward(cudaStream_t s, const float* params, const float* F, int rows, bool fp16, float* prob);
+cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float* v, int step, const float* F,
+                                  const float* y, int rows, float lr, float pos_weight, bool fp16, float* scratch,
+                                  float* loss_out, float* grad_out);
+cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
+                         const int* count_dev, int count_host, int n, double logT, float tau, int* keep, int* pruned);
+cudaError_t launch_record(cudaStream_t s, const float* traj, const float* B32, int ldb, int n, int M, const int* slot,
+                          double logT, float* F_out, float* y_out);
+cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, int M, int* out);
+cudaError_t launch_compact_keep(cudaStream_t s, const int* keep, const int* act_in, const int* count_in_dev,
+                                int count_host, int* act_out, int* count_out_dev);
 
 // ---- k_tc.cu ----
 int tc_chunk(int n_pad);

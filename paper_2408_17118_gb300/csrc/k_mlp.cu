@@ -1,0 +1,416 @@
+// Learned restart pruner (not part of the paper's method): a 12-64-64-1 perceptron that reads
+// the first five iterations of a restart (kurtosis alpha of Eq. 2 and the step distance of the
+// convergence test) plus n and log T, and predicts whether the restart ends at the direction the
+// component picks. Inference and training run here: FP16 weights and activations (the "fp16"
+// switch; 0 keeps everything FP32 for gradient checks), FP32 accumulation, FP32 master weights
+// and Adam moments.
+//
+// Parameter vector (FP32, kMlpParams floats): mean[12], scale[12], W1[64][12], b1[64],
+// W2[64][64], b2[64], w3[64], b3. Training scratch: per sample a row of kActRow floats
+// (x_hat 12, h1 64, d1 64, h2 64, d2 64, dz 1), sample-major, so that the gradient kernel reads
+// the activations of one sample with coalesced loads.
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ica {
+
+namespace {
+constexpr int IN = kMlpIn, HID = kMlpHid;
+constexpr int OFF_MEAN = 0, OFF_SCALE = 12, OFF_W1 = 24, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
+              OFF_B2 = OFF_W2 + HID * HID, OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID;
+static_assert(OFF_B3 + 1 == kMlpParams, "parameter layout");
+constexpr int A_X = 0, A_H1 = 12, A_D1 = A_H1 + HID, A_H2 = A_D1 + HID, A_D2 = A_H2 + HID, A_DZ = A_D2 + HID;
+static_assert(A_DZ + 1 <= kActRow, "activation row");
+
+// Rounds to FP16 and back when the kernel runs in FP16 mode.
+template <bool H>
+__device__ __forceinline__ float q(float x) {
+    if constexpr (H) return __half2float(__float2half_rn(x));
+    return x;
+}
+
+// Weights (rounded in FP16 mode) in shared memory, shared by a block.
+struct SmemNet {
+    float w1[HID * IN], b1[HID], w2[HID * HID], b2[HID], w3[HID], b3, mean[IN], scale[IN];
+};
+
+template <bool H>
+__device__ void load_net(const float* __restrict__ p, SmemNet& s) {
+    for (int i = threadIdx.x; i < HID * HID; i += blockDim.x) s.w2[i] = q<H>(p[OFF_W2 + i]);
+    for (int i = threadIdx.x; i < HID * IN; i += blockDim.x) s.w1[i] = q<H>(p[OFF_W1 + i]);
+    for (int i = threadIdx.x; i < HID; i += blockDim.x) {
+        s.b1[i] = q<H>(p[OFF_B1 + i]);
+        s.b2[i] = q<H>(p[OFF_B2 + i]);
+        s.w3[i] = q<H>(p[OFF_W3 + i]);
+    }
+    if (threadIdx.x < IN) {
+        s.mean[threadIdx.x] = p[OFF_MEAN + threadIdx.x];
+        s.scale[threadIdx.x] = p[OFF_SCALE + threadIdx.x];
+    }
+    if (threadIdx.x == 0) s.b3 = q<H>(p[OFF_B3]);
+    __syncthreads();
+}
+
+// Forward pass of one sample; h1 and h2 (post-ReLU) optionally written to act.
+template <bool H>
+__device__ float forward_one(const SmemNet& s, const float* x_raw, float* x_hat, float* act) {
+    float x[IN];
+#pragma unroll
+    for (int i = 0; i < IN; ++i) {
+        x[i] = q<H>((x_raw[i] - s.mean[i]) * s.scale[i]);
+        if (x_hat) x_hat[i] = x[i];
+    }
+    float h1[HID];
+#pragma unroll
+    for (int j = 0; j < HID; ++j) {
+        float a = s.b1[j];
+#pragma unroll
+        for (int i = 0; i < IN; ++i) a = fmaf(s.w1[j * IN + i], x[i], a);
+        h1[j] = q<H>(fmaxf(a, 0.f));
+        if (act) act[A_H1 + j] = h1[j];
+    }
+    float z = s.b3;
+#pragma unroll 4
+    for (int k = 0; k < HID; ++k) {
+        float a = s.b2[k];
+#pragma unroll
+        for (int j = 0; j < HID; ++j) a = fmaf(s.w2[k * HID + j], h1[j], a);
+        const float h2 = q<H>(fmaxf(a, 0.f));
+        if (act) act[A_H2 + k] = h2;
+        z = fmaf(s.w3[k], h2, z);
+    }
+    return z;
+}
+
+__device__ __forceinline__ float sigmoidf(float z) { return 1.f / (1.f + __expf(-z)); }
+
+template <bool H>
+__global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ params, const float* __restrict__ F,
+                                                          int rows, float* __restrict__ prob) {
+    __shared__ SmemNet s;
+    load_net<H>(params, s);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    float xr[IN];
+#pragma unroll
+    for (int i = 0; i < IN; ++i) xr[i] = F[static_cast<int64_t>(r) * IN + i];
+    prob[r] = sigmoidf(forward_one<H>(s, xr, nullptr, nullptr));
+}
+
+// Forward + backward of one sample per thread: writes its activation row and its loss term.
+template <bool H>
+__global__ void __launch_bounds__(128) mlp_train_fwd_kernel(const float* __restrict__ params, const float* __restrict__ F,
+                                                            const float* __restrict__ y, int rows, float pos_weight,
+                                                            float* __restrict__ act, float* __restrict__ loss_part) {
+    __shared__ SmemNet s;
+    __shared__ float red[128];
+    load_net<H>(params, s);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    float lterm = 0.f;
+    if (r < rows) {
+        float* a = act + static_cast<int64_t>(r) * kActRow;
+        float xr[IN];
+#pragma unroll
+        for (int i = 0; i < IN; ++i) xr[i] = F[static_cast<int64_t>(r) * IN + i];
+        const float z = forward_one<H>(s, xr, a + A_X, a);
+        const float p = sigmoidf(z);
+        const float yy = y[r];
+        // -[w y log p + (1 - y) log(1 - p)] with log p = -softplus(-z), log(1 - p) = -softplus(z)
+        const float sp_neg = fmaxf(-z, 0.f) + log1pf(__expf(-fabsf(z)));
+        const float sp_pos = fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+        lterm = pos_weight * yy * sp_neg + (1.f - yy) * sp_pos;
+        const float dz = (p * (pos_weight * yy + 1.f - yy) - pos_weight * yy) / static_cast<float>(rows);
+        a[A_DZ] = dz;
+        float d2[HID];
+#pragma unroll
+        for (int k = 0; k < HID; ++k) {
+            d2[k] = a[A_H2 + k] > 0.f ? dz * s.w3[k] : 0.f;
+            a[A_D2 + k] = d2[k];
+        }
+#pragma unroll 4
+        for (int j = 0; j < HID; ++j) {
+            float g = 0.f;
+#pragma unroll
+            for (int k = 0; k < HID; ++k) g = fmaf(d2[k], s.w2[k * HID + j], g);
+            a[A_D1 + j] = a[A_H1 + j] > 0.f ? g : 0.f;
+        }
+    }
+    red[threadIdx.x] = lterm;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// Gradient of every learnable parameter over a slice of the samples (deterministic order).
+__global__ void mlp_grad_kernel(const float* __restrict__ act, int rows, int slice, float* __restrict__ gpart) {
+    const int pidx = blockIdx.x * blockDim.x + threadIdx.x;  // learnable index 0 .. kMlpParams-25
+    if (pidx >= kMlpParams - 2 * IN) return;
+    const int P = pidx + 2 * IN;
+    int ua, ub;  // activation columns multiplied (ub < 0: bias, the factor is 1)
+    if (P < OFF_B1) {
+        ua = A_D1 + (P - OFF_W1) / IN;
+        ub = A_X + (P - OFF_W1) % IN;
+    } else if (P < OFF_W2) {
+        ua = A_D1 + (P - OFF_B1);
+        ub = -1;
+    } else if (P < OFF_B2) {
+        ua = A_D2 + (P - OFF_W2) / HID;
+        ub = A_H1 + (P - OFF_W2) % HID;
+    } else if (P < OFF_W3) {
+        ua = A_D2 + (P - OFF_B2);
+        ub = -1;
+    } else if (P < OFF_B3) {
+        ua = A_DZ;
+        ub = A_H2 + (P - OFF_W3);
+    } else {
+        ua = A_DZ;
+        ub = -1;
+    }
+    const int s0 = blockIdx.y * slice, s1 = min(rows, s0 + slice);
+    float g = 0.f;
+    for (int r = s0; r < s1; ++r) {
+        const float* a = act + static_cast<int64_t>(r) * kActRow;
+        g = fmaf(a[ua], ub >= 0 ? a[ub] : 1.f, g);
+    }
+    gpart[static_cast<int64_t>(blockIdx.y) * kMlpParams + P] = g;
+}
+
+// Sum of the slices (fixed order), optional copy of the gradient, Adam update; the loss is the
+// fixed-order sum of the per-block parts divided by rows.
+__global__ void mlp_adam_kernel(float* __restrict__ params, float* __restrict__ m, float* __restrict__ v,
+                                const float* __restrict__ gpart, int slices, int step, float lr,
+                                float* __restrict__ grad_out, const float* __restrict__ loss_part, int nparts, int rows,
+                                float* __restrict__ loss_out) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P == 0 && loss_out) {
+        float l = 0.f;
+        for (int i = 0; i < nparts; ++i) l += loss_part[i];
+        *loss_out = l / static_cast<float>(rows);
+    }
+    if (P >= kMlpParams) return;
+    float g = 0.f;
+    if (P >= 2 * IN)
+        for (int sl = 0; sl < slices; ++sl) g += gpart[static_cast<int64_t>(sl) * kMlpParams + P];
+    if (grad_out) grad_out[P] = g;
+    if (lr <= 0.f || P < 2 * IN) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float mm = b1 * m[P] + (1.f - b1) * g;
+    const float vv = b2 * v[P] + (1.f - b2) * g * g;
+    m[P] = mm;
+    v[P] = vv;
+    const float mh = mm / (1.f - powf(b1, static_cast<float>(step)));
+    const float vh = vv / (1.f - powf(b2, static_cast<float>(step)));
+    params[P] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// He initialisation from Philox4x32-10 (key = seed): W ~ N(0, 2 / fan_in), biases 0, mean 0,
+// scale 1.
+__global__ void mlp_init_kernel(uint64_t seed, float* __restrict__ params) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= kMlpParams) return;
+    float v = 0.f;
+    float fan = 0.f;
+    if (P >= OFF_SCALE && P < OFF_W1) v = 1.f;
+    if (P >= OFF_W1 && P < OFF_B1) fan = IN;
+    if (P >= OFF_W2 && P < OFF_B2) fan = HID;
+    if (P >= OFF_W3 && P < OFF_B3) fan = HID;
+    if (fan > 0.f) {
+        const uint4 c = philox4x32_10(make_uint4(static_cast<uint32_t>(P), 0x6d6c70u, 0u, 0u),
+                                      make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+        const double u1 = uniform52(c.x, c.y), u2 = uniform52(c.z, c.w);
+        const double g = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+        v = static_cast<float>(g * sqrt(2.0 / fan));
+    }
+    params[P] = v;
+}
+
+// Feature standardisation from a set of feature rows: one block per column, fixed order.
+__global__ void mlp_standardize_kernel(const float* __restrict__ F, int rows, float* __restrict__ params) {
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    double sacc = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) sacc += F[static_cast<int64_t>(r) * IN + c];
+    red[threadIdx.x] = sacc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double mean = red[0] / rows;
+    __syncthreads();
+    double vacc = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double d = F[static_cast<int64_t>(r) * IN + c] - mean;
+        vacc += d * d;
+    }
+    red[threadIdx.x] = vacc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        params[OFF_MEAN + c] = static_cast<float>(mean);
+        params[OFF_SCALE + c] = static_cast<float>(1.0 / fmax(sqrt(red[0] / rows), 1e-6));
+    }
+}
+
+// Raw features of restart r: alpha and step distance of the first kTrajLen iterations, n, log T.
+__device__ __forceinline__ void restart_features(const float* __restrict__ traj, int r, float n, float logT, float* x) {
+#pragma unroll
+    for (int t = 0; t < kTrajLen; ++t) {
+        x[t] = traj[(static_cast<int64_t>(r) * kTrajLen + t) * 2 + 0];
+        x[kTrajLen + t] = traj[(static_cast<int64_t>(r) * kTrajLen + t) * 2 + 1];
+    }
+    x[10] = n;
+    x[11] = logT;
+}
+
+// Inference on the active restarts inside a fit: keep flag (p >= tau) per active slot j, and
+// the pruned mark of every restart it drops.
+__global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ params, const float* __restrict__ traj,
+                                                    const int* __restrict__ act_idx, const int* __restrict__ count_dev,
+                                                    int count_host, float n, float logT, float tau,
+                                                    int* __restrict__ keep, int* __restrict__ pruned) {
+    __shared__ SmemNet s;
+    load_net<true>(params, s);
+    const int count = count_dev ? *count_dev : count_host;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const int r = act_idx ? act_idx[j] : j;
+    float x[IN];
+    restart_features(traj, r, n, logT, x);
+    const float p = sigmoidf(forward_one<true>(s, x, nullptr, nullptr));
+    const int k = p >= tau ? 1 : 0;
+    keep[j] = k;
+    if (!k) pruned[r] = 1;
+}
+
+// Training record of one component: raw features of every restart and whether the restart
+// ended at the picked direction (|b_r . b_p| >= 1 - 1e-3 on normalised rows).
+__global__ void record_kernel(const float* __restrict__ traj, const float* __restrict__ B32, int ldb, int n_dim, int M,
+                              const int* __restrict__ slot, float n, float logT, float* __restrict__ F_out,
+                              float* __restrict__ y_out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    float x[IN];
+    restart_features(traj, r, n, logT, x);
+#pragma unroll
+    for (int i = 0; i < IN; ++i) F_out[static_cast<int64_t>(r) * IN + i] = x[i];
+    const int p = *slot;
+    float dot = 0.f, nr = 0.f, np = 0.f;
+    for (int k = 0; k < n_dim; ++k) {
+        const float a = B32[static_cast<int64_t>(r) * ldb + k], b = B32[static_cast<int64_t>(p) * ldb + k];
+        dot = fmaf(a, b, dot);
+        nr = fmaf(a, a, nr);
+        np = fmaf(b, b, np);
+    }
+    y_out[r] = fabsf(dot) >= (1.f - 1e-3f) * sqrtf(nr * np) ? 1.f : 0.f;
+}
+
+// Fallback test of a pruned component: 1 when some pruned restart has a kurtosis objective at
+// least as large as the best kept one (the network may have dropped the global optimum).
+__global__ void prune_check_kernel(const double* __restrict__ ups, const int* __restrict__ pruned, int M,
+                                   int* __restrict__ out) {
+    __shared__ double bp[256], bk[256];
+    double mp = -INFINITY, mk = -INFINITY;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) {
+        const double u = ups[r];
+        if (pruned[r])
+            mp = fmax(mp, u);
+        else
+            mk = fmax(mk, u);
+    }
+    bp[threadIdx.x] = mp;
+    bk[threadIdx.x] = mk;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            bp[threadIdx.x] = fmax(bp[threadIdx.x], bp[threadIdx.x + o]);
+            bk[threadIdx.x] = fmax(bk[threadIdx.x], bk[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = bp[0] >= bk[0] ? 1 : 0;
+}
+}  // namespace
+
+size_t mlp_scratch_bytes(int rows) {
+    const int slices = mlp_slices(rows);
+    return sizeof(float) * (static_cast<size_t>(rows) * kActRow + static_cast<size_t>(slices) * kMlpParams +
+                            static_cast<size_t>((rows + 127) / 128) + 64);
+}
+
+int mlp_slices(int rows) {
+    int s = (rows + 511) / 512;
+    return s < 1 ? 1 : (s > 32 ? 32 : s);
+}
+
+cudaError_t launch_mlp_init(cudaStream_t s, uint64_t seed, float* params) {
+    mlp_init_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(seed, params);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_standardize(cudaStream_t s, const float* F, int rows, float* params) {
+    mlp_standardize_kernel<<<IN, 256, 0, s>>>(F, rows, params);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(cudaStream_t s, const float* params, const float* F, int rows, bool fp16, float* prob) {
+    const int blocks = (rows + 127) / 128;
+    if (fp16)
+        mlp_forward_kernel<true><<<blocks, 128, 0, s>>>(params, F, rows, prob);
+    else
+        mlp_forward_kernel<false><<<blocks, 128, 0, s>>>(params, F, rows, prob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float* v, int step, const float* F,
+                                  const float* y, int rows, float lr, float pos_weight, bool fp16, float* scratch,
+                                  float* loss_out, float* grad_out) {
+    const int blocks = (rows + 127) / 128;
+    const int slices = mlp_slices(rows);
+    const int slice = (rows + slices - 1) / slices;
+    float* act = scratch;
+    float* gpart = act + static_cast<size_t>(rows) * kActRow;
+    float* loss_part = gpart + static_cast<size_t>(slices) * kMlpParams;
+    if (fp16)
+        mlp_train_fwd_kernel<true><<<blocks, 128, 0, s>>>(params, F, y, rows, pos_weight, act, loss_part);
+    else
+        mlp_train_fwd_kernel<false><<<blocks, 128, 0, s>>>(params, F, y, rows, pos_weight, act, loss_part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mlp_grad_kernel<<<dim3((kMlpParams - 2 * IN + 127) / 128, slices), 128, 0, s>>>(act, rows, slice, gpart);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(params, m, v, gpart, slices, step, lr, grad_out, loss_part,
+                                                             blocks, rows, loss_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
+                         const int* count_dev, int count_host, int n, double logT, float tau, int* keep, int* pruned) {
+    prune_kernel<<<(count_host + 127) / 128, 128, 0, s>>>(params, traj, act_idx, count_dev, count_host,
+                                                          static_cast<float>(n), static_cast<float>(logT), tau, keep,
+                                                          pruned);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record(cudaStream_t s, const float* traj, const float* B32, int ldb, int n, int M, const int* slot,
+                          double logT, float* F_out, float* y_out) {
+    record_kernel<<<(M + 127) / 128, 128, 0, s>>>(traj, B32, ldb, n, M, slot, static_cast<float>(n),
+                                                  static_cast<float>(logT), F_out, y_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, int M, int* out) {
+    prune_check_kernel<<<1, 256, 0, s>>>(ups, pruned, M, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ica

@@ -388,14 +388,49 @@ cudaError_t launch_kurt_finalize(cudaStream_t s, const float* part_mom, int spli
 // Distinct top-k: repeat {argmax over non-excluded rows; exclude every row whose direction
 // matches the pick up to sign (|cos| >= threshold)}.
 // ------------------------------------------------------------------------------------------
-__global__ void select_clear_kernel(int* excluded, int M, int* cand, int kmax) {
+__global__ void select_clear_kernel(int* excluded, const int* init, int M, int* cand, int kmax) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) excluded[i] = 0;
+    if (i < M) excluded[i] = init ? init[i] : 0;
     if (i < kmax) cand[i] = -1;
 }
-cudaError_t launch_select_clear(cudaStream_t s, int* excluded, int M, int* cand, int kmax) {
+// Excluded mask := init (restarts dropped by the pruner) or zero; candidate slots := -1.
+cudaError_t launch_select_clear(cudaStream_t s, int* excluded, const int* init, int M, int* cand, int kmax) {
     const int n = M > kmax ? M : kmax;
-    select_clear_kernel<<<(n + 255) / 256, 256, 0, s>>>(excluded, M, cand, kmax);
+    select_clear_kernel<<<(n + 255) / 256, 256, 0, s>>>(excluded, init, M, cand, kmax);
+    return cudaGetLastError();
+}
+
+// Stable compaction of the active list by keep flags (one CTA of 1024 threads, each owning a
+// contiguous slice): used when the pruner drops restarts.
+__global__ void __launch_bounds__(1024) compact_keep_kernel(const int* __restrict__ keep,
+                                                            const int* __restrict__ act_in,
+                                                            const int* __restrict__ count_in_dev, int count_host,
+                                                            int* __restrict__ act_out, int* count_out_dev) {
+    __shared__ int warp_tot[32];
+    const int count = count_in_dev ? *count_in_dev : count_host;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (count + 1023) / 1024;
+    const int b = t * per, e = min(count, b + per);
+    int local = 0;
+    for (int i = b; i < e; ++i) local += keep[i] != 0;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int ww = 0; ww < w; ++ww) before += warp_tot[ww];
+    int pos = before + incl - local;
+    for (int i = b; i < e; ++i)
+        if (keep[i]) act_out[pos++] = act_in ? act_in[i] : i;
+    if (t == 1023) *count_out_dev = before + incl;
+}
+cudaError_t launch_compact_keep(cudaStream_t s, const int* keep, const int* act_in, const int* count_in_dev,
+                                int count_host, int* act_out, int* count_out_dev) {
+    compact_keep_kernel<<<1, 1024, 0, s>>>(keep, act_in, count_in_dev, count_host, act_out, count_out_dev);
     return cudaGetLastError();
 }
 

@@ -11,7 +11,7 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import ICA_BF16, ICA_FP32, ICA_PLAIN_FP32, ica_opts  # noqa: F401
+from ._lib import ICA_BF16, ICA_FP32, ICA_MLP_IN, ICA_MLP_PARAMS, ICA_PLAIN_FP32, ica_opts  # noqa: F401
 
 
 class IcaError(RuntimeError):
@@ -105,15 +105,27 @@ def ica_whiten(ctx: Context, X: torch.Tensor, Xw: torch.Tensor | None = None):
 
 
 def ica_order_fit(ctx: Context, Xw: torch.Tensor, M: int, n_components: int, iters: int, tol: float, seed: int,
-                  opts: ica_opts | None = None, B0: torch.Tensor | None = None):
+                  opts: ica_opts | None = None, B0: torch.Tensor | None = None,
+                  prune_params: torch.Tensor | None = None, record: bool = False):
     """Fast ordering ICA on whitened Xw (N x T float32). Returns (W float64 n_found x N,
-    kurtosis float64 n_found)."""
+    kurtosis float64 n_found); with record=True also (features n_components x M x 12,
+    labels n_components x M) for training the restart pruner."""
     N, T = Xw.shape
     opts = ica_default_opts() if opts is None else opts
     if B0 is not None:
         if B0.shape != (n_components, M, N):
             raise ValueError("B0 must be n_components x M x N")
         opts.B0 = _ptr(B0, torch.float32, "B0")
+    if prune_params is not None:
+        if prune_params.numel() != ICA_MLP_PARAMS:
+            raise ValueError(f"prune_params must hold {ICA_MLP_PARAMS} floats")
+        opts.prune_params = _ptr(prune_params, torch.float32, "prune_params")
+    rec = None
+    if record:
+        rec = (torch.zeros((n_components, M, ICA_MLP_IN), dtype=torch.float32, device=Xw.device),
+               torch.zeros((n_components, M), dtype=torch.float32, device=Xw.device))
+        opts.record_features = rec[0].data_ptr()
+        opts.record_labels = rec[1].data_ptr()
     ctx.ensure_workspace(N, T, M, opts)
     W = torch.zeros((n_components, N), dtype=torch.float64, device=Xw.device)
     kurt = torch.zeros(n_components, dtype=torch.float64, device=Xw.device)
@@ -121,6 +133,8 @@ def ica_order_fit(ctx: Context, Xw: torch.Tensor, M: int, n_components: int, ite
     _check(ctx.lib.ica_order_fit(ctx.handle, _ptr(Xw, torch.float32, "Xw"), N, T, M, n_components, iters, float(tol),
                                  int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(opts), _ptr(W), _ptr(kurt), C.byref(nf)),
            "ica_order_fit")
+    if record:
+        return W[: nf.value], kurt[: nf.value], rec
     return W[: nf.value], kurt[: nf.value]
 
 
@@ -211,3 +225,46 @@ def ica_fp_step_noalloc(precision: int, B: torch.Tensor, n: int, Xt: torch.Tenso
     _check(_lib.load().ica_fp_step_noalloc(precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(Bnew),
                                            _ptr(mom), C.c_void_p(stream.cuda_stream)), "ica_fp_step_noalloc")
     return Bnew, mom
+
+
+# ------------------------------------------------------------------ learned restart pruner
+def ica_mlp_init(ctx: Context, seed: int, params: torch.Tensor | None = None) -> torch.Tensor:
+    params = torch.empty(ICA_MLP_PARAMS, dtype=torch.float32, device=f"cuda:{ctx.device}") if params is None else params
+    _check(ctx.lib.ica_mlp_init(ctx.handle, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(params, torch.float32, "params")),
+           "ica_mlp_init")
+    return params
+
+
+def ica_mlp_standardize(ctx: Context, F: torch.Tensor, params: torch.Tensor):
+    rows = F.shape[0]
+    _check(ctx.lib.ica_mlp_standardize(ctx.handle, _ptr(F, torch.float32, "F"), rows,
+                                       _ptr(params, torch.float32, "params")), "ica_mlp_standardize")
+
+
+def ica_mlp_forward(ctx: Context, params: torch.Tensor, F: torch.Tensor, fp16: bool = True) -> torch.Tensor:
+    rows = F.shape[0]
+    prob = torch.empty(rows, dtype=torch.float32, device=F.device)
+    _check(ctx.lib.ica_mlp_forward(ctx.handle, _ptr(params, torch.float32, "params"), _ptr(F, torch.float32, "F"),
+                                   rows, int(fp16), _ptr(prob)), "ica_mlp_forward")
+    return prob
+
+
+def ica_mlp_scratch_bytes(rows: int) -> int:
+    return int(_lib.load().ica_mlp_scratch_bytes(rows))
+
+
+def ica_mlp_train_step(ctx: Context, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
+                       F: torch.Tensor, y: torch.Tensor, lr: float, pos_weight: float = 1.0, fp16: bool = True,
+                       scratch: torch.Tensor | None = None, want_grad: bool = False):
+    """One training step; returns (loss tensor [1], grad tensor or None, scratch)."""
+    rows = F.shape[0]
+    need = ica_mlp_scratch_bytes(rows)
+    if scratch is None or scratch.numel() < need:
+        scratch = torch.empty(need, dtype=torch.uint8, device=F.device)
+    loss = torch.empty(1, dtype=torch.float32, device=F.device)
+    grad = torch.empty(ICA_MLP_PARAMS, dtype=torch.float32, device=F.device) if want_grad else None
+    _check(ctx.lib.ica_mlp_train_step(ctx.handle, _ptr(params, torch.float32, "params"), _ptr(m), _ptr(v), int(step),
+                                      _ptr(F, torch.float32, "F"), _ptr(y, torch.float32, "y"), rows, float(lr),
+                                      float(pos_weight), int(fp16), C.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                      _ptr(loss), _ptr(grad)), "ica_mlp_train_step")
+    return loss, grad, scratch
