@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["c1", "c2", "c3", "c5"], default="c2")
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c5", "batch"], default="c2")
+    ap.add_argument("--workers", type=int, default=8, help="concurrent fits of --config batch")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -407,8 +408,69 @@ def run_kernel_step(args):
     return 0
 
 
+def run_batch(args):
+    """32 data sets of uneven N (16..128) and T (2e4..4e5, log-uniform), M = 512 restarts each,
+    all components: whitening of every set plus one ica_order_fit_batched call per step, timed
+    against the same sets fitted one after another (workers = 1)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2408_17118_gb300 import ica
+
+    dev = torch.device("cuda", 0)
+    ws = synth.batch_of_datasets(count=32, seed=args.seed)
+    M, iters, tol = ws[0].M, ws[0].iters, ws[0].tol
+    Xs = [torch.from_numpy(w.X).to(dev) for w in ws]
+    ctx = ica.Context(0)
+    opts = ica.ica_default_opts(precision=ica.ICA_BF16)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(workers):
+        Xws = [ica.ica_whiten(ctx, X)[0] for X in Xs]
+        ica.ica_order_fit_batched(ctx, Xws, M, iters, tol, 1234, opts, workers=workers)
+        return json.loads(ica.ica_last_stats(ctx))
+
+    def flops_of(st):
+        return sum(sum(v["flops"] for v in d["fused"].values()) for d in st["datasets"])
+
+    res = {}
+    for workers in (args.workers, 1):
+        for _ in range(max(1, args.warmup)):
+            step(workers)
+        times, fl, last = [], 0.0, None
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            last = step(workers)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            fl += flops_of(last)
+        res[workers] = {"ms_per_step": float(np.median(times)), "tflops": fl / (sum(times) / 1e3) / 1e12,
+                        "cta_div": last["batched"]["cta_div"], "tune_ms": last["batched"]["tune_ms"]}
+    main = res[args.workers]
+    line = {"metric": METRIC, "value": main["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded generators, synth/)",
+            "config": {"workload": "32 data sets, N in {16,32,48,64,96,128}, T log-uniform in [2e4, 4e5], M=512, "
+                                   "all components, iters<=30, tol=1e-6", "workers": args.workers,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "time_to_all_components_s": main["ms_per_step"] / 1e3,
+            "one_at_a_time": {"time_to_all_components_s": res[1]["ms_per_step"] / 1e3, "tflops": res[1]["tflops"]},
+            "speedup_vs_one_at_a_time": res[1]["ms_per_step"] / main["ms_per_step"],
+            "autotuned_cta_div": main["cta_div"], "tune_ms": main["tune_ms"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.config == "batch":
+        return run_batch(args)
     if args.kernel_step:
         return run_kernel_step(args)
     if args.impl == "reference":

@@ -96,6 +96,11 @@ void ica_default_opts(ica_opts* opts);
 /* Human-readable name of a status code (static string). */
 const char* ica_status_string(int status);
 
+/* Text of the last CUDA runtime failure behind an ICA_ERR_CUDA returned to the calling host
+   thread (the failing call and its error string); empty if none. Valid until the next call of
+   this library from the same thread. */
+const char* ica_last_error(void);
+
 /* Create a context bound to CUDA device `device` (host pointer *out receives it). Allocates a
    small pinned host buffer for device->host counters. ICA_ERR_CUDA if the device is absent. */
 int ica_create(ica_ctx** out, int device);
@@ -207,6 +212,35 @@ int ica_kurtosis(ica_ctx* ctx, int precision, const float* B, int M, int n, cons
      synchronises it once at the end to read the status word. */
 int ica_fp_step_noalloc(int precision, const float* B, int M, int n, const void* Xt, int64_t T,
                         int64_t ldx, float* Bnew, float* moments, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+   Many data sets in one call. Not in the paper: the data sets of a batch (uneven N and T) are
+   fitted concurrently by `workers` worker contexts, each with its own stream and a slice of the
+   caller's workspace (set with ica_set_workspace, at least ica_batched_workspace_bytes). An
+   autotuner times concurrent fused steps of the median data set for three GPU shares per
+   launch (a full wave of CTAs, a half, a quarter) once per (workers, shape) and keeps the
+   fastest. Data set k uses seed + k. The call returns after every fit finished; the caller's
+   stream (ica_set_stream) is ordered before the first and after the last worker launch.
+   opts->B0, record_features and record_labels must be NULL. ica_last_stats reports the
+   batch (workers, chosen share, tuning times, wall time) and every data set's stats.
+   --------------------------------------------------------------------------------------- */
+typedef struct {
+    const float* Xw;     /* whitened data, N x T row-major FP32 (device) */
+    int N;               /* 1..256 */
+    int64_t T;           /* >= 2N */
+    int n_components;    /* 1..N */
+    double* W_out;       /* n_components x N FP64 (device), as ica_order_fit */
+    double* kurt_out;    /* n_components FP64 (device) */
+    int* n_found;        /* host int */
+} ica_dataset;
+
+/* Workspace bytes for a batch (0 on invalid sizes); workers <= 0 means the default (8). */
+size_t ica_batched_workspace_bytes(const ica_dataset* sets, int count, int M, const ica_opts* opts, int workers);
+
+/* Fits every data set of the batch (Algorithm 2, as ica_order_fit, M restarts each). Returns
+   the first non-OK status of any data set (outputs of the others are valid). */
+int ica_order_fit_batched(ica_ctx* ctx, const ica_dataset* sets, int count, int M, int iters, double tol,
+                          uint64_t seed, const ica_opts* opts, int workers);
 
 /* ---------------------------------------------------------------------------------------
    Learned restart pruner: a 12-64-64-1 perceptron (ReLU, sigmoid output) trained on the

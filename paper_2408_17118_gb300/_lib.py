@@ -41,6 +41,18 @@ class ica_opts(C.Structure):
     ]
 
 
+class ica_dataset(C.Structure):
+    _fields_ = [
+        ("Xw", C.c_void_p),
+        ("N", C.c_int),
+        ("T", C.c_int64),
+        ("n_components", C.c_int),
+        ("W_out", C.c_void_p),
+        ("kurt_out", C.c_void_p),
+        ("n_found", C.POINTER(C.c_int)),
+    ]
+
+
 # learned restart pruner (include/ica.h)
 ICA_MLP_IN = 12
 ICA_MLP_HIDDEN = 64
@@ -53,6 +65,7 @@ vp, i32, i64, u64, f64, sz, f32 = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.
 SIGNATURES = {
     "ica_default_opts": (None, [C.POINTER(ica_opts)]),
     "ica_status_string": (C.c_char_p, [i32]),
+    "ica_last_error": (C.c_char_p, []),
     "ica_create": (i32, [C.POINTER(vp), i32]),
     "ica_destroy": (i32, [vp]),
     "ica_set_stream": (i32, [vp, vp]),
@@ -67,6 +80,8 @@ SIGNATURES = {
     "ica_fp_step": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_kurtosis": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_fp_step_noalloc": (i32, [i32, vp, i32, i32, vp, i64, i64, vp, vp, vp]),
+    "ica_batched_workspace_bytes": (sz, [C.POINTER(ica_dataset), i32, i32, C.POINTER(ica_opts), i32]),
+    "ica_order_fit_batched": (i32, [vp, C.POINTER(ica_dataset), i32, i32, i32, f64, u64, C.POINTER(ica_opts), i32]),
     "ica_mlp_init": (i32, [vp, u64, vp]),
     "ica_mlp_standardize": (i32, [vp, vp, i32, vp]),
     "ica_mlp_forward": (i32, [vp, vp, vp, i32, i32, vp]),

@@ -2,6 +2,9 @@
 // in matrix form, with removal of converged rows and reduction of signals) on one GPU:
 // every arithmetic step runs in this library's kernels; the host only orders launches, picks
 // launch shapes and reads back the active-restart count on a sparse schedule.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <dlfcn.h>
 #include <math.h>
@@ -9,6 +12,7 @@
 #include <string.h>
 
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -55,6 +59,14 @@ struct ica_ctx {
     std::vector<Rec> recs;
     double kind_ms[10] = {}, kind_flops[10] = {};
     long long kind_n[10] = {};
+    // share of the GPU (CTAs per launch, as a fraction of one wave) that fused launches aim
+    // for: 1 when the fit owns the GPU, smaller when several fits run concurrently
+    int cta_div = 1;
+    // concurrent fits of ica_order_fit_batched: worker contexts with their own streams, and the
+    // autotuned CTA share per (workers, shape) key
+    std::vector<ica_ctx*> workers;
+    std::vector<cudaStream_t> worker_streams;
+    std::vector<std::pair<long long, int>> tuned;
 };
 
 // kinds of timed fused launches
@@ -64,10 +76,18 @@ enum { K_ITER = 0, K_KURT = 1, K_REFINE = 2, K_REFKURT = 3, K_FINALIZE = 4, K_PR
 static const char* kKindName[K_NKINDS] = {"iteration", "kurtosis", "refine", "refine_kurtosis", "finalize",
                                           "prune", "basis", "reduce", "select", "append"};
 
-#define CK(call)                                      \
-    do {                                              \
-        cudaError_t _e = (call);                      \
-        if (_e != cudaSuccess) return ICA_ERR_CUDA;   \
+// Text of the last CUDA failure seen by this host thread (ica_last_error).
+static thread_local std::string g_last_error;
+static void note_cuda_error(cudaError_t e, const char* what, int line) {
+    g_last_error = std::string(cudaGetErrorString(e)) + " in " + what + " (ica_api.cu:" + std::to_string(line) + ")";
+}
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t _e = (call);                          \
+        if (_e != cudaSuccess) {                          \
+            note_cuda_error(_e, #call, __LINE__);         \
+            return ICA_ERR_CUDA;                          \
+        }                                                 \
     } while (0)
 // a launch of one of this library's kernels (counted)
 #define KL(call)             \
@@ -244,7 +264,7 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
         const int TC = tc_chunk(a.n_pad);
         const int64_t total = (a.T + TC - 1) / TC;
         const int tiles = (a.M_act + kTcRows - 1) / kTcRows;
-        choose_splits(total, tiles, 152, a.max_splits, &shape->splits, &shape->cps);  // one CTA per SM, one wave
+        choose_splits(total, tiles, 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps);  // one wave
         shape->part_rows = tiles * kTcRows;
         CUtensorMap map, map_t;
         int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
@@ -263,14 +283,14 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
         const int64_t total = (a.T + 63) / 64;
         if (a.M_act <= kFp32SmallRows) {  // a few candidates: bound by streaming X~
             const int64_t total_rows_chunks = (a.T + fp32_rows_chunk(a.n_pad) - 1) / fp32_rows_chunk(a.n_pad);
-            choose_splits(total_rows_chunks, 1, 2 * 152, a.max_splits, &shape->splits, &shape->cps);
+            choose_splits(total_rows_chunks, 1, 2 * 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps);
             shape->part_rows = fp32_rows_tile(a.M_act);
             KL(launch_fused_fp32_rows(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx,
                                       a.n_pad, a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
             return ICA_OK;
         }
         const int tiles = (a.M_act + kFp32Rows - 1) / kFp32Rows;
-        choose_splits(total, tiles, 4 * 152, a.max_splits, &shape->splits, &shape->cps);
+        choose_splits(total, tiles, 4 * 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps);
         shape->part_rows = tiles * kFp32Rows;
         KL(launch_fused_fp32(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx, a.n_pad,
                              a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
@@ -456,6 +476,8 @@ int ica_create(ica_ctx** out, int device) {
 
 int ica_destroy(ica_ctx* c) {
     if (!c) return ICA_OK;
+    for (ica_ctx* w : c->workers) ica_destroy(w);
+    for (cudaStream_t st : c->worker_streams) cudaStreamDestroy(st);
     if (c->cublas && c->cublas_destroy) c->cublas_destroy(c->cublas);
     if (c->cublas_lib) dlclose(c->cublas_lib);
     if (c->host_i) cudaFreeHost(c->host_i);
@@ -1027,3 +1049,229 @@ int ica_mlp_train_step(ica_ctx* c, float* params, float* adam_m, float* adam_v, 
     c->launches_total += 2;
     return ICA_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// Many data sets in one call (ica_order_fit_batched): `workers` fits run concurrently, each on
+// a worker context with its own stream and a slice of the caller's workspace; data sets are
+// handed to the workers in order from an atomic counter. Before the fits an autotuner picks the
+// share of the GPU each fused launch aims for (one wave, a half or a quarter of the SMs) by
+// timing concurrent fused steps of a representative data set on all worker streams.
+// ---------------------------------------------------------------------------------------------
+namespace {
+size_t batched_slot_bytes(const ica_dataset* sets, int count, int M, const ica_opts* o) {
+    size_t mx = 0;
+    for (int k = 0; k < count; ++k) {
+        const size_t b = ica_workspace_bytes(sets[k].N, sets[k].T, M, o);
+        if (b == 0) return 0;
+        if (b > mx) mx = b;
+    }
+    return align_up(mx);
+}
+
+int batched_workers(int count, int workers) {
+    int w = workers > 0 ? workers : 8;
+    if (w > count) w = count;
+    if (w > 32) w = 32;
+    return w < 1 ? 1 : w;
+}
+
+// Times `reps` concurrent fused update steps (all M rows, zero data: the tensor-core work does
+// not depend on the values) on every worker stream for each CTA share; returns the best share.
+int autotune_cta_div(ica_ctx* c, int nw, const ica_dataset& rep, int M, int precision, std::vector<float>* times) {
+    const int cands[3] = {1, 2, 4};
+    const int prec = precision == ICA_PLAIN_FP32 ? ICA_FP32 : precision;
+    const int n_pad = round_up(rep.N, 16);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct Guard {
+        cudaEvent_t a, b;
+        ~Guard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } g{e0, e1};
+    std::vector<cudaEvent_t> done(nw);
+    for (auto& e : done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    struct Guard2 {
+        std::vector<cudaEvent_t>& v;
+        ~Guard2() {
+            for (auto e : v) cudaEventDestroy(e);
+        }
+    } g2{done};
+    const Layout L = make_layout(rep.N, rep.T, M, prec);
+    for (int w = 0; w < nw; ++w) {
+        ica_ctx* k = c->workers[w];
+        CK(cudaMemsetAsync(k->ws, 0, L.total, k->stream));
+    }
+    CK(cudaDeviceSynchronize());
+    int best = 1;
+    float best_ms = 0.f;
+    for (int ci = 0; ci < 3; ++ci) {
+        CK(cudaEventRecord(e0, c->stream));
+        for (int w = 0; w < nw; ++w) {
+            ica_ctx* k = c->workers[w];
+            k->cta_div = cands[ci];
+            CK(cudaStreamWaitEvent(k->stream, e0, 0));
+            FusedArgs fa;
+            fa.precision = prec;
+            fa.B32 = at<float>(k, L.B32);
+            fa.ldb = n_pad;
+            fa.M_act = M;
+            fa.n_pad = n_pad;
+            fa.T = rep.T;
+            fa.Xt32 = at<float>(k, L.Xt32);
+            fa.Xt16 = at<uint16_t>(k, L.Xt16);
+            fa.ldx = L.ldx;
+            for (int r = 0; r < 3; ++r) {
+                StepShape sh;
+                const int rc = run_fused(k, L, fa, &sh);
+                if (rc) return -rc;
+            }
+            CK(cudaEventRecord(done[w], k->stream));
+            CK(cudaStreamWaitEvent(c->stream, done[w], 0));
+        }
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (times) times->push_back(ms);
+        if (ci == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = cands[ci];
+        }
+    }
+    return best;
+}
+}  // namespace
+
+size_t ica_batched_workspace_bytes(const ica_dataset* sets, int count, int M, const ica_opts* opts, int workers) {
+    if (!sets || count < 1 || M < 1) return 0;
+    const size_t slot = batched_slot_bytes(sets, count, M, opts);
+    return slot ? slot * static_cast<size_t>(batched_workers(count, workers)) : 0;
+}
+
+int ica_order_fit_batched(ica_ctx* c, const ica_dataset* sets, int count, int M, int iters, double tol, uint64_t seed,
+                          const ica_opts* opts, int workers) {
+    if (!c || !sets || count < 1 || M < 1 || M > 65536 || iters < 1 || !(tol > 0.0)) return ICA_ERR_ARG;
+    ica_opts d;
+    ica_default_opts(&d);
+    const ica_opts& o = opts ? *opts : d;
+    if (o.B0 || o.record_features || o.record_labels) return ICA_ERR_ARG;  // per-fit buffers have no batched form
+    for (int k = 0; k < count; ++k) {
+        const ica_dataset& ds = sets[k];
+        if (!ds.Xw || !ds.W_out || !ds.kurt_out || !ds.n_found || ds.N < 1 || ds.N > kMaxN ||
+            ds.T < 2 * static_cast<int64_t>(ds.N) || ds.n_components < 1 || ds.n_components > ds.N)
+            return ICA_ERR_ARG;
+    }
+    const int nw = batched_workers(count, workers);
+    const size_t slot = batched_slot_bytes(sets, count, M, &o);
+    if (!slot) return ICA_ERR_ARG;
+    if (!c->ws || c->ws_bytes < slot * nw) return ICA_ERR_WORKSPACE;
+    CK(cudaSetDevice(c->device));
+    while (static_cast<int>(c->workers.size()) < nw) {
+        ica_ctx* w = nullptr;
+        const int rc = ica_create(&w, c->device);
+        if (rc) return rc;
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            ica_destroy(w);
+            return ICA_ERR_CUDA;
+        }
+        w->stream = st;
+        c->workers.push_back(w);
+        c->worker_streams.push_back(st);
+    }
+    for (int w = 0; w < nw; ++w) {
+        c->workers[w]->ws = c->ws + slot * w;
+        c->workers[w]->ws_bytes = slot;
+    }
+    // representative data set for the autotuner: the median by samples x dimension
+    std::vector<int> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return static_cast<double>(sets[a].N) * sets[a].T < static_cast<double>(sets[b].N) * sets[b].T;
+    });
+    const ica_dataset& rep = sets[order[count / 2]];
+    const long long key = static_cast<long long>(nw) * 1000003LL + round_up(rep.N, 16) * 131LL +
+                          static_cast<long long>(std::log2(static_cast<double>(rep.T)));
+    int div = 0;
+    std::vector<float> tune_ms;
+    for (auto& kv : c->tuned)
+        if (kv.first == key) div = kv.second;
+    if (!div) {
+        div = autotune_cta_div(c, nw, rep, M, o.precision, &tune_ms);
+        if (div < 0) return -div;
+        c->tuned.push_back({key, div});
+    }
+    // the fits
+    cudaEvent_t start;
+    CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    CK(cudaEventRecord(start, c->stream));
+    for (int w = 0; w < nw; ++w) {
+        c->workers[w]->cta_div = nw == 1 ? 1 : div;
+        if (cudaStreamWaitEvent(c->workers[w]->stream, start, 0) != cudaSuccess) {
+            cudaEventDestroy(start);
+            return ICA_ERR_CUDA;
+        }
+    }
+    cudaEventDestroy(start);
+    std::atomic<int> next{0};
+    std::vector<int> rcs(count, ICA_OK);
+    std::vector<std::string> st(count);
+    std::vector<long long> launches(nw, 0);
+    std::vector<std::string> errs(count);
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nw; ++w) {
+        pool.emplace_back([&, w] {
+            ica_ctx* k = c->workers[w];
+            cudaSetDevice(k->device);
+            for (;;) {
+                const int i = next.fetch_add(1);
+                if (i >= count) break;
+                const ica_dataset& ds = sets[i];
+                rcs[i] = ica_order_fit(k, ds.Xw, ds.N, ds.T, M, ds.n_components, iters, tol, seed + static_cast<uint64_t>(i),
+                                       &o, ds.W_out, ds.kurt_out, ds.n_found);
+                st[i] = rcs[i] == ICA_OK ? k->stats : std::string("null");
+                if (rcs[i]) errs[i] = g_last_error;
+                launches[w] += k->launches;
+            }
+        });
+    }
+    for (auto& th : pool) th.join();
+    const double wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int w = 0; w < nw; ++w) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaEventRecord(e, c->workers[w]->stream));
+        CK(cudaStreamWaitEvent(c->stream, e, 0));
+        cudaEventDestroy(e);
+    }
+    c->launches = 0;
+    for (long long l : launches) c->launches += l;
+    std::string js = "{\"batched\": {";
+    char buf[256];
+    snprintf(buf, sizeof(buf), "\"count\": %d, \"workers\": %d, \"cta_div\": %d, \"wall_ms\": %.3f, \"launches\": %lld, \"tune_ms\": [",
+             count, nw, div, wall_ms, c->launches);
+    js += buf;
+    for (size_t k = 0; k < tune_ms.size(); ++k) {
+        snprintf(buf, sizeof(buf), "%s%.4f", k ? ", " : "", tune_ms[k]);
+        js += buf;
+    }
+    js += "]}, \"datasets\": [";
+    for (int k = 0; k < count; ++k) {
+        js += k ? ", " : "";
+        js += st[k];
+    }
+    js += "]}";
+    c->stats = js;
+    for (int k = 0; k < count; ++k)
+        if (rcs[k]) {
+            g_last_error = "data set " + std::to_string(k) + ": " + errs[k];
+            return rcs[k];
+        }
+    return ICA_OK;
+}
+
+const char* ica_last_error(void) { return g_last_error.c_str(); }

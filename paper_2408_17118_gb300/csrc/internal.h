@@ -9,6 +9,24 @@
 namespace ica {
 
 constexpr int kMaxN = 256;            // channels (and reduced dimension) supported
+// Raises a kernel's dynamic shared memory limit to the largest the device allows (the opt-in
+// per-block maximum minus the kernel's static shared memory). Kernels whose launches need
+// different amounts always set this one value, so that host threads launching the same kernel
+// concurrently with different sizes never race on the attribute.
+template <typename F>
+inline cudaError_t allow_max_dyn_smem(F* fn) {
+    static const int optin = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return v;
+    }();
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - static_cast<int>(a.sharedSizeBytes));
+}
 constexpr int kMaxCTAs = 4 * 152;     // cap on (split x restart-tile) CTAs of one fused launch
 constexpr int kTrajLen = 5;           // iterations of per-restart features kept (pruner input)
 constexpr int kFp32Rows = 64;         // restart rows per CTA, FP32 fused kernel

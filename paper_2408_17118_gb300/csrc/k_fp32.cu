@@ -374,15 +374,13 @@ cudaError_t launch_rows_variant(cudaStream_t s, bool moments_only, const float* 
     const size_t smem = fp32_rows_smem_bytes(n_pad, R);
     cudaError_t e;
     if (moments_only) {
-        e = cudaFuncSetAttribute(fused_fp32_rows_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
+        e = allow_max_dyn_smem(fused_fp32_rows_kernel<R, true>);
         if (e != cudaSuccess) return e;
         fused_fp32_rows_kernel<R, true><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
                                                                   n_pad, T, chunks_per_split, part_acc, part_mom,
                                                                   part_rows);
     } else {
-        e = cudaFuncSetAttribute(fused_fp32_rows_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
+        e = allow_max_dyn_smem(fused_fp32_rows_kernel<R, false>);
         if (e != cudaSuccess) return e;
         fused_fp32_rows_kernel<R, false><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt,
                                                                    ldx, n_pad, T, chunks_per_split, part_acc,
@@ -413,14 +411,12 @@ cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B3
     const dim3 grid(splits, (M_act + F_MT - 1) / F_MT);
     cudaError_t e;
     if (moments_only) {
-        e = cudaFuncSetAttribute(fused_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
+        e = allow_max_dyn_smem(fused_fp32_kernel<true>);
         if (e != cudaSuccess) return e;
         fused_fp32_kernel<true><<<grid, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act, Xt, ldx, n_pad, T,
                                                         chunks_per_split, part_acc, part_mom, part_rows);
     } else {
-        e = cudaFuncSetAttribute(fused_fp32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
+        e = allow_max_dyn_smem(fused_fp32_kernel<false>);
         if (e != cudaSuccess) return e;
         fused_fp32_kernel<false><<<grid, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act, Xt, ldx, n_pad, T,
                                                          chunks_per_split, part_acc, part_mom, part_rows);

@@ -263,8 +263,7 @@ cudaError_t launch_jacobi(cudaStream_t s, double* A, double* V, double* lam, int
     const size_t smem = 2ull * m * m * sizeof(double);
     const int use_smem = smem <= 160 * 1024;
     if (use_smem) {
-        cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = allow_max_dyn_smem(jacobi_kernel);
         if (e != cudaSuccess) return e;
     }
     int threads = m * m / 2;

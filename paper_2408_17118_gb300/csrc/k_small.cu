@@ -275,8 +275,7 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
     const float fT = static_cast<float>(inv_T), ftol = static_cast<float>(tol);
     if (M_act <= 64 && splits > 16) {
         const size_t smem = sizeof(float) * 32 * (2 * n_pad + 4);
-        cudaError_t e = cudaFuncSetAttribute(finalize_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = allow_max_dyn_smem(finalize_kernel<32>);
         if (e != cudaSuccess) return e;
         finalize_kernel<32><<<M_act, 1024, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                                                       count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,

@@ -429,8 +429,7 @@ static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const
     const TcLayout L = tc_layout(n_pad, MO, TC, NB, KT);
     if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
     if (KT && !xmap_t) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TC, NB, KT, MO, MOM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.total));
+    cudaError_t e = allow_max_dyn_smem(fused_tc_kernel<TC, NB, KT, MO, MOM>);
     if (e != cudaSuccess) return e;
     const dim3 grid(splits, (M_act + kTcRows - 1) / kTcRows);
     fused_tc_kernel<TC, NB, KT, MO, MOM><<<grid, kThreads, L.total, s>>>(

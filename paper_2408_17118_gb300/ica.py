@@ -11,14 +11,15 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import ICA_BF16, ICA_FP32, ICA_MLP_IN, ICA_MLP_PARAMS, ICA_PLAIN_FP32, ica_opts  # noqa: F401
+from ._lib import ICA_BF16, ICA_FP32, ICA_MLP_IN, ICA_MLP_PARAMS, ICA_PLAIN_FP32, ica_dataset, ica_opts  # noqa: F401
 
 
 class IcaError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib = _lib.load()
         msg = lib.ica_status_string(status).decode()
-        super().__init__(f"{where}: {msg} (status {status})")
+        detail = lib.ica_last_error().decode() if status == 2 else ""
+        super().__init__(f"{where}: {msg} (status {status})" + (f": {detail}" if detail else ""))
         self.status = status
 
 
@@ -136,6 +137,36 @@ def ica_order_fit(ctx: Context, Xw: torch.Tensor, M: int, n_components: int, ite
     if record:
         return W[: nf.value], kurt[: nf.value], rec
     return W[: nf.value], kurt[: nf.value]
+
+
+def ica_order_fit_batched(ctx: Context, Xws: list, M: int, iters: int, tol: float, seed: int,
+                          opts: ica_opts | None = None, n_components: list | None = None, workers: int = 0):
+    """Fits every whitened data set of the list (N_k x T_k float32 CUDA tensors) concurrently.
+    Returns a list of (W float64 n_found x N_k, kurtosis float64 n_found)."""
+    opts = ica_default_opts() if opts is None else opts
+    count = len(Xws)
+    sets = (ica_dataset * count)()
+    outs, founds = [], [C.c_int(0) for _ in range(count)]
+    for k, Xw in enumerate(Xws):
+        N, T = Xw.shape
+        nc = N if n_components is None else int(n_components[k])
+        W = torch.zeros((nc, N), dtype=torch.float64, device=Xw.device)
+        kurt = torch.zeros(nc, dtype=torch.float64, device=Xw.device)
+        outs.append((W, kurt))
+        sets[k].Xw = _ptr(Xw, torch.float32, "Xw")
+        sets[k].N, sets[k].T, sets[k].n_components = N, T, nc
+        sets[k].W_out, sets[k].kurt_out = W.data_ptr(), kurt.data_ptr()
+        sets[k].n_found = C.pointer(founds[k])
+    need = ctx.lib.ica_batched_workspace_bytes(sets, count, M, C.byref(opts), workers)
+    if need == 0:
+        raise ValueError("invalid batch sizes")
+    if ctx.workspace is None or ctx.workspace.numel() < need:
+        ctx.workspace = torch.empty(need, dtype=torch.uint8, device=f"cuda:{ctx.device}")
+    _check(ctx.lib.ica_set_workspace(ctx.handle, C.c_void_p(ctx.workspace.data_ptr()), ctx.workspace.numel()),
+           "ica_set_workspace")
+    _check(ctx.lib.ica_order_fit_batched(ctx.handle, sets, count, M, iters, float(tol), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                         C.byref(opts), workers), "ica_order_fit_batched")
+    return [(W[: f.value], k[: f.value]) for (W, k), f in zip(outs, founds)]
 
 
 def ica_last_stats(ctx: Context) -> str:
