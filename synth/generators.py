@@ -7,17 +7,18 @@ inputs from here: the FP64 CPU oracle (through the tests) and the CUDA path (thr
 and bench.py). Every draw comes from numpy's PCG64 keyed by an explicit seed and a stream tag,
 so a workload is reproducible bit for bit on x86 and Arm hosts.
 
-Workload shapes follow the paper's experiments and the build's five configurations:
+Workload shapes follow the paper's experiments:
 
-* ``c1``: N=8 sources {Laplace, uniform, Student-t nu=5, binary +-1, centred exponential,
+* ``small_mixture``: N=8 sources {Laplace, uniform, Student-t nu=5, binary +-1, centred exponential,
   Laplace^2, uniform, Gaussian}, T=10,000, A ~ N(0,1), M=64 restarts.
 * ``eeg_like``: EEG-shaped data (the paper's EEG experiment uses N=61 channels and about
   160,000-190,000 samples, Section 4.3; the recordings are not available here, so this
   generator stands in for them): 3/4 of the channels carry non-Gaussian sources, half of them
   super-Gaussian (Laplace, Student-t nu in {4, 6, 10}) and half sub-Gaussian (uniform, binary,
   sinusoid with random frequency and phase); the rest are Gaussian; sigma=0.05 sensor noise.
-  Used at N=64/T=2e5/M=1024, N=128/T=5e5/M=4096 and N=256/T=1e6/M=8192.
-* ``batch_of_datasets``: 32 independent C1-style datasets with N drawn from
+  Used at N=64/T=2e5/M=1024 (``eeg64``), N=128/T=5e5/M=4096 (``eeg128``) and
+  N=256/T=1e6/M=8192 (``eeg256``).
+* ``batch_of_datasets``: 32 independent small-mixture-style datasets with N drawn from
   {16, 32, 48, 64, 96, 128} and T log-uniform in [2e4, 4e5].
 * ``ggd_paper``: the artificial datasets of Section 4.2: generalised Gaussian sources with
   rho = 2 * 2^(i/4), i in {-10..-1, 1..10} (N=20), optionally plus 10 Gaussian sources (N=30).
@@ -37,17 +38,17 @@ __all__ = [
     "rng_for",
     "standardise",
     "make_source",
-    "c1",
+    "small_mixture",
     "eeg_like",
-    "c2",
-    "c3",
-    "c5",
+    "eeg64",
+    "eeg128",
+    "eeg256",
     "batch_of_datasets",
     "ggd_paper",
     "ggd_source",
     "restart_inits",
     "small_random",
-    "C1_SOURCES",
+    "SMALL_SOURCES",
 ]
 
 
@@ -101,7 +102,7 @@ def make_source(kind: str, rng: np.random.Generator, T: int) -> np.ndarray:
     raise ValueError(f"unknown source kind {kind!r}")
 
 
-C1_SOURCES = ["laplace", "uniform", "t5", "binary", "exp", "laplace2", "uniform", "gauss"]
+SMALL_SOURCES = ["laplace", "uniform", "t5", "binary", "exp", "laplace2", "uniform", "gauss"]
 
 
 @dataclass
@@ -145,9 +146,9 @@ def _mix(name, kinds, T, seed, M, iters, tol, noise=0.0, keep_sources=True, n_co
                     iters=iters, tol=tol, seed=seed)
 
 
-def c1(seed: int = 0, T: int = 10_000, M: int = 64, iters: int = 200, tol: float = 1e-10) -> Workload:
+def small_mixture(seed: int = 0, T: int = 10_000, M: int = 64, iters: int = 200, tol: float = 1e-10) -> Workload:
     """N=8 plain ordering-ICA workload: eight distinct sources, no noise."""
-    return _mix("c1", C1_SOURCES, T, seed, M, iters, tol)
+    return _mix("small_mixture_N8", SMALL_SOURCES, T, seed, M, iters, tol)
 
 
 def _eeg_kinds(N: int) -> list[str]:
@@ -167,17 +168,17 @@ def eeg_like(N: int, T: int, M: int, seed: int = 0, iters: int = 30, tol: float 
                 keep_sources=keep_sources, n_components=n_components)
 
 
-def c2(seed: int = 0, **kw) -> Workload:
+def eeg64(seed: int = 0, **kw) -> Workload:
     """EEG-like N=64 channels, T=200,000 samples, M=1024 restarts, all 64 components."""
     return eeg_like(64, 200_000, 1024, seed=seed, **kw)
 
 
-def c3(seed: int = 0, **kw) -> Workload:
+def eeg128(seed: int = 0, **kw) -> Workload:
     """Same generator at N=128, T=500,000, M=4096."""
     return eeg_like(128, 500_000, 4096, seed=seed, **kw)
 
 
-def c5(seed: int = 0, **kw) -> Workload:
+def eeg256(seed: int = 0, **kw) -> Workload:
     """Same generator at N=256, T=1,000,000, M=8192."""
     return eeg_like(256, 1_000_000, 8192, seed=seed, **kw)
 
@@ -185,13 +186,13 @@ def c5(seed: int = 0, **kw) -> Workload:
 def batch_of_datasets(count: int = 32, seed: int = 0, M: int = 512, iters: int = 30, tol: float = 1e-6,
                       Ns=(16, 32, 48, 64, 96, 128), T_lo: int = 20_000, T_hi: int = 400_000,
                       keep_sources: bool = False) -> list[Workload]:
-    """Independent C1-style datasets of uneven N and T (sources cycle through the C1 list)."""
+    """Independent datasets of uneven N and T (sources cycle through the small-mixture list)."""
     g = rng_for(seed, 7)
     out = []
     for k in range(count):
         N = int(g.choice(Ns))
         T = int(round(math.exp(g.uniform(math.log(T_lo), math.log(T_hi)))))
-        kinds = [C1_SOURCES[i % len(C1_SOURCES)] for i in range(N)]
+        kinds = [SMALL_SOURCES[i % len(SMALL_SOURCES)] for i in range(N)]
         out.append(_mix(f"batch{k}_N{N}_T{T}", kinds, T, seed * 1000 + 17 + k, M, iters, tol,
                         keep_sources=keep_sources))
     return out

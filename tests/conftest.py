@@ -16,12 +16,12 @@ def pytest_configure(config):
 
 
 @pytest.fixture(scope="session")
-def c1_oracle():
+def small_oracle():
     """Oracle fit (Algorithm 2, FP64) of the N=8 workload, seed 0, with explicit restarts."""
     import oracle
     import synth
 
-    w = synth.c1(0)
+    w = synth.small_mixture(0)
     B0 = synth.restart_inits(w.M, w.N, w.N, 1000)
     res, Xw, V, mean = oracle.order_fit(w.X, w.M, w.N, w.iters, w.tol, B0, record=True)
     return w, B0, res, Xw, V, mean

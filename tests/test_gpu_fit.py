@@ -55,7 +55,7 @@ def check_parity(W, kurt, ref, label):
 
 @pytest.fixture(scope="module")
 def c1_ref():
-    w = synth.c1(0)
+    w = synth.small_mixture(0)
     B0 = synth.restart_inits(w.M, w.N, w.N, 1000)
     ref, Xw, V, mean = oracle.order_fit(w.X, w.M, w.N, w.iters, w.tol, B0)
     return w, B0, ref
@@ -76,7 +76,7 @@ def test_c1_parity_seeded_restarts(ctx):
     ones from its own implementation of that generator."""
     from paper_2408_17118_gb300 import ica
 
-    w = synth.c1(1)
+    w = synth.small_mixture(1)
     seed = 0x1234_5678_9ABC
     B0 = oracle.seeded_B0(seed, w.M, w.N, w.N)
     ref, _, _, _ = oracle.order_fit(w.X, w.M, w.N, w.iters, w.tol, B0)
@@ -89,7 +89,7 @@ def test_c1_parity_seeded_restarts(ctx):
 def test_ragged_shapes(ctx, N, T, M, ncomp):
     from paper_2408_17118_gb300 import ica
 
-    kinds = [synth.C1_SOURCES[i % 8] for i in range(N)]
+    kinds = [synth.SMALL_SOURCES[i % 8] for i in range(N)]
     w = synth.generators._mix(f"r{N}", kinds, T, N + T, M, 100, 1e-8, n_components=ncomp)
     B0 = synth.restart_inits(M, N, ncomp, 7)
     ref, _, _, _ = oracle.order_fit(w.X, M, ncomp, 100, 1e-8, B0)
@@ -127,7 +127,7 @@ def test_full_size_eeg_like_sampled(ctx):
     y = w Xw; and no FP64 FastICA run from 16 fresh restarts on component 1 beating it."""
     from paper_2408_17118_gb300 import ica
 
-    w = synth.c2(0)
+    w = synth.eeg64(0)
     W, kurt, Xw, V = gpu_fit(ctx, w, ica.ICA_BF16, seed=11)
     assert W.shape == (64, 64)
     assert np.abs(W @ W.T - np.eye(64)).max() < 1e-12

@@ -102,7 +102,7 @@ def test_standardize_and_init(ica, ctx):
 def test_recorded_features_match_oracle(ica, ctx):
     # alpha at iteration 1 is the kurtosis of the initial restart on X~ (Eq. 2); labels mark the
     # restarts that ended at the picked direction (the picked restart itself included)
-    w = synth.c1(0)
+    w = synth.small_mixture(0)
     X = torch.from_numpy(w.X).cuda()
     Xw, V, mean = ica.ica_whiten(ctx, X)
     M = w.M

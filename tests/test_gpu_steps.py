@@ -99,12 +99,12 @@ def test_deflation_basis_identity(ctx):
 
 
 # ------------------------------------------------------------------------------ whitening
-@pytest.mark.parametrize("kind", ["c1", "eeg64", "n256"])
+@pytest.mark.parametrize("kind", ["small", "eeg64", "n256"])
 def test_whiten(ctx, kind):
     from paper_2408_17118_gb300 import ica
 
-    if kind == "c1":
-        X = synth.c1(0).X
+    if kind == "small":
+        X = synth.small_mixture(0).X
     elif kind == "eeg64":
         X = synth.eeg_like(64, 20_000, 8, seed=1).X
     else:
@@ -220,7 +220,7 @@ def test_fp_step_full_size_sampled(ctx):
     from paper_2408_17118_gb300 import ica
 
     M, n, T = 1024, 64, 200_000
-    w = synth.c2(0)
+    w = synth.eeg64(0)
     Xw, V, mean = ica.ica_whiten(ctx, torch.from_numpy(w.X).cuda())
     Xt32, Xt16 = ica.ica_reduce(ctx, torch.eye(n, dtype=torch.float64).cuda(), Xw)
     B = ica.ica_init_restarts(ctx, 5, 0, M, n, n)

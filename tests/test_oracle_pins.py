@@ -94,7 +94,7 @@ def test_gaussianity_threshold_formula_shape():
 
 # ------------------------------------------------------------------ whitening
 def test_whitening_invariants():
-    w = synth.c1(3, T=5000)
+    w = synth.small_mixture(3, T=5000)
     Xw, V, mean = oracle.whiten(w.X)
     T = w.T
     assert np.abs(Xw.mean(axis=1)).max() < 1e-12
@@ -152,16 +152,16 @@ def test_step_distance_sign_tolerant():
 
 
 # ------------------------------------------------------------------ end-to-end on the N=8 workload
-def test_orthonormal_output(c1_oracle):
-    w, B0, res, Xw, V, mean = c1_oracle
+def test_orthonormal_output(small_oracle):
+    w, B0, res, Xw, V, mean = small_oracle
     assert res.W.shape == (8, 8)
     assert np.abs(res.W @ res.W.T - np.eye(8)).max() < 1e-12
 
 
-def test_recovery_and_order(c1_oracle):
+def test_recovery_and_order(small_oracle):
     """Theorem 1: W V A is a signed permutation (Amari index) and the components come out in
     descending Upsilon of the sources' kurtosis (here the sample kurtosis of each true source)."""
-    w, B0, res, Xw, V, mean = c1_oracle
+    w, B0, res, Xw, V, mean = small_oracle
     P = res.W @ V @ w.A
     assert oracle.amari_index(P) < 3e-2  # T = 1e4: finite-sample error ~ T^-1/2
     src = np.argmax(np.abs(P), axis=1)
@@ -175,20 +175,20 @@ def test_recovery_and_order(c1_oracle):
 
 @pytest.mark.slow
 def test_recovery_large_T():
-    w = synth.c1(1, T=100_000)
+    w = synth.small_mixture(1, T=100_000)
     B0 = synth.restart_inits(w.M, w.N, w.N, 1001)
     res, Xw, V, mean = oracle.order_fit(w.X, w.M, w.N, w.iters, w.tol, B0)
     assert oracle.amari_index(res.W @ V @ w.A) < 1e-2
 
 
-def test_gaussian_component(c1_oracle):
-    w, B0, res, Xw, V, mean = c1_oracle
+def test_gaussian_component(small_oracle):
+    w, B0, res, Xw, V, mean = small_oracle
     assert abs(res.alpha[-1]) <= 3.0 * math.sqrt(24.0 / w.T)
 
 
-def test_fixed_point_residual(c1_oracle):
+def test_fixed_point_residual(small_oracle):
     """At convergence the update maps each found w to +-w (Algorithm 1 form, full space)."""
-    w, B0, res, Xw, V, mean = c1_oracle
+    w, B0, res, Xw, V, mean = small_oracle
     T = w.T
     for i in range(7):
         wi = res.W[i]
@@ -201,8 +201,8 @@ def test_fixed_point_residual(c1_oracle):
         assert min(np.linalg.norm(v - wi), np.linalg.norm(v + wi)) < tol, i
 
 
-def test_last_component_is_the_remaining_direction(c1_oracle):
-    w, B0, res, Xw, V, mean = c1_oracle
+def test_last_component_is_the_remaining_direction(small_oracle):
+    w, B0, res, Xw, V, mean = small_oracle
     _, _, vt = np.linalg.svd(res.W[:7])
     null = vt[-1]
     assert abs(abs(null @ res.W[7]) - 1.0) < 1e-12
@@ -212,7 +212,7 @@ def test_last_component_is_the_remaining_direction(c1_oracle):
 def test_algorithm1_equals_algorithm2():
     """Reduction of signals (Section 3.3) changes no trajectory: the batched reduced iteration
     with w = G^T b equals the per-initialisation projected iteration."""
-    w = synth.c1(2, T=4000, M=16)
+    w = synth.small_mixture(2, T=4000, M=16)
     B0 = synth.restart_inits(16, 8, 8, 77)
     Xw, V, mean = oracle.whiten(w.X)
     r2 = oracle.fast_ordering_ica(Xw, 16, 60, 1e-10, B0)
@@ -256,9 +256,9 @@ def test_two_dimensional_brute_force():
     assert abs(res.W[1] @ w1) < 1e-12
 
 
-def test_invariance_to_invertible_transform(c1_oracle):
+def test_invariance_to_invertible_transform(small_oracle):
     """Separated signals y = W V (X - mean) do not depend on an invertible transform of X."""
-    w, B0, res, Xw, V, mean = c1_oracle
+    w, B0, res, Xw, V, mean = small_oracle
     Q = np.random.default_rng(3).standard_normal((8, 8))
     X2 = (Q @ w.X.astype(np.float64))
     res2, Xw2, V2, mean2 = oracle.order_fit(X2, w.M, w.N, w.iters, w.tol, B0)
