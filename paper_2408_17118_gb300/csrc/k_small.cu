@@ -97,6 +97,61 @@ struct CompSum {  // s + c carries the exact running sum to about twice FP32 pre
     __device__ __forceinline__ float value() const { return s + c; }
 };
 
+// Warp 0 of a block (or the row's own warp) finishes row j from the summed update u*T (acc):
+// b' = acc / T - 3 b, normalisation, distance, flag, iteration count and trajectory.
+__device__ __forceinline__ void finish_row(const float (&accv)[8], int nq, int n, const int* __restrict__ act_idx,
+                                           int j, float* __restrict__ B32, int ldb, float inv_T, float tol,
+                                           int* __restrict__ flags, int* __restrict__ iters,
+                                           float* __restrict__ traj, int t_iter, bool want_traj, float e2sum,
+                                           float e4sum, int* status) {
+    const int lane = threadIdx.x & 31;
+    const int r = act_idx ? act_idx[j] : j;
+    float u[8], b[8];
+    float ss = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        u[q] = 0.f;
+        b[q] = 0.f;
+        if (q < nq && k < n) {
+            b[q] = B32[static_cast<int64_t>(r) * ldb + k];
+            u[q] = accv[q] * inv_T - 3.f * b[q];
+            ss = fmaf(u[q], u[q], ss);
+        }
+    }
+    ss = warp_sumf(ss);
+    const bool bad = !(ss > 0.f) || !isfinite(ss);
+    float dm = 0.f, dp = 0.f;
+    const float inv = bad ? 0.f : rsqrtf(ss);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        u[q] *= inv;
+        dm = fmaf(u[q] - b[q], u[q] - b[q], dm);
+        dp = fmaf(u[q] + b[q], u[q] + b[q], dp);
+    }
+    dm = warp_sumf(dm);
+    dp = warp_sumf(dp);
+    const float d = sqrtf(fminf(dm, dp));
+    if (!bad) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (q < nq && k < n) B32[static_cast<int64_t>(r) * ldb + k] = u[q];
+        }
+    }
+    if (lane == 0) {
+        flags[j] = (!bad && d > tol) ? 1 : 0;
+        iters[r] += 1;
+        if (bad) atomicOr(status, DEV_NONFINITE);
+        if (want_traj) {
+            const float e2 = e2sum * inv_T, e4 = e4sum * inv_T;
+            const float alpha = e2 > 0.f ? e4 / (e2 * e2) - 3.f : 0.f;
+            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 0] = alpha;
+            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 1] = d;
+        }
+    }
+}
+
 // One row j of the update: all NW warps sum the split partials, warp 0 finishes the row.
 template <int NW>
 __device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
@@ -144,14 +199,11 @@ __device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc,
     }
     __syncthreads();
     if (w != 0) return;
-    const int r = act_idx ? act_idx[j] : j;
-    float u[8], b[8];
-    float ss = 0.f;
+    float accv[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int k = lane + 32 * q;
-        u[q] = 0.f;
-        b[q] = 0.f;
+        accv[q] = 0.f;
         if (q < nq && k < n) {
             CompSum acc;
             float cs = 0.f;
@@ -159,80 +211,33 @@ __device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc,
                 acc.add(red_s[ww * n_pad + k]);
                 cs += red_c[ww * n_pad + k];
             }
-            b[q] = B32[static_cast<int64_t>(r) * ldb + k];
-            u[q] = (acc.value() + cs) * inv_T - 3.f * b[q];
-            ss = fmaf(u[q], u[q], ss);
+            accv[q] = acc.value() + cs;
         }
     }
-    ss = warp_sumf(ss);
-    const bool bad = !(ss > 0.f) || !isfinite(ss);
-    float dm = 0.f, dp = 0.f;
-    const float inv = bad ? 0.f : rsqrtf(ss);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        u[q] *= inv;
-        dm = fmaf(u[q] - b[q], u[q] - b[q], dm);
-        dp = fmaf(u[q] + b[q], u[q] + b[q], dp);
-    }
-    dm = warp_sumf(dm);
-    dp = warp_sumf(dp);
-    const float d = sqrtf(fminf(dm, dp));
-    if (!bad) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = lane + 32 * q;
-            if (q < nq && k < n) B32[static_cast<int64_t>(r) * ldb + k] = u[q];
+    CompSum m2, m4;
+    if (want_traj)
+        for (int ww = 0; ww < NW; ++ww) {
+            m2.add(redm[4 * ww + 0]);
+            m2.add(redm[4 * ww + 1]);
+            m4.add(redm[4 * ww + 2]);
+            m4.add(redm[4 * ww + 3]);
         }
-    }
-    if (lane == 0) {
-        flags[j] = (!bad && d > tol) ? 1 : 0;
-        iters[r] += 1;
-        if (bad) atomicOr(status, DEV_NONFINITE);
-        if (want_traj) {
-            CompSum m2, m4;
-            for (int ww = 0; ww < NW; ++ww) {
-                m2.add(redm[4 * ww + 0]);
-                m2.add(redm[4 * ww + 1]);
-                m4.add(redm[4 * ww + 2]);
-                m4.add(redm[4 * ww + 3]);
-            }
-            const float e2 = m2.value() * inv_T, e4 = m4.value() * inv_T;
-            const float alpha = e2 > 0.f ? e4 / (e2 * e2) - 3.f : 0.f;
-            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 0] = alpha;
-            traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 1] = d;
-        }
-    }
+    finish_row(accv, nq, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters, traj, t_iter, want_traj, m2.value(),
+               m4.value(), status);
 }
 
 
+// Compaction of the active list (Section 3.2: converged rows leave B) into act_out/count_out,
+// by the last block of the launch to finish: every block counts itself in after its flags are
+// visible device-wide. act_out and count_out must not alias the input list and count;
+// *done_ctr is zero on entry and is left zero. Called by every thread of every block.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
-                                                           const float* __restrict__ part_mom, int splits,
-                                                           int part_rows, int n_pad, int n,
-                                                           const int* __restrict__ act_idx,
-                                                           const int* __restrict__ count_dev, int M_act_host,
-                                                           float* __restrict__ B32, int ldb, float inv_T, float tol,
-                                                           int* __restrict__ flags, int* __restrict__ iters,
-                                                           float* __restrict__ traj, int t_iter, int* status,
-                                                           int* __restrict__ act_out, int* count_out,
-                                                           long long* rows_accum, unsigned int* done_ctr) {
-    extern __shared__ float fin_red[];  // [NW][n_pad] sums, [NW][n_pad] compensations, [NW][4] moments
+__device__ __forceinline__ void compact_tail(const int* __restrict__ flags, const int* __restrict__ act_idx,
+                                             int M_act, int* __restrict__ act_out, int* count_out,
+                                             long long* rows_accum, unsigned int* done_ctr) {
     __shared__ int is_last;
     __shared__ int warp_tot[NW];
-    float* red_s = fin_red;
-    float* red_c = fin_red + NW * n_pad;
-    float* redm = fin_red + 2 * NW * n_pad;
-    const int M_act = count_dev ? *count_dev : M_act_host;
-    const int j = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (j < M_act) {
-        finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
-                         traj, t_iter, status, red_s, red_c, redm);
-    }
-    // Compaction of the active list (Section 3.2: converged rows leave B) into act_out/count_out,
-    // by the last block to finish: every block counts itself in after its flag is visible
-    // device-wide. act_out and count_out must not alias act_idx and count_dev; *done_ctr is zero
-    // on entry and is left zero.
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -266,7 +271,34 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
     }
 }
 
-// Rows with many splits and few rows (the refinement) get 32 warps each, others 8.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
+                                                           const float* __restrict__ part_mom, int splits,
+                                                           int part_rows, int n_pad, int n,
+                                                           const int* __restrict__ act_idx,
+                                                           const int* __restrict__ count_dev, int M_act_host,
+                                                           float* __restrict__ B32, int ldb, float inv_T, float tol,
+                                                           int* __restrict__ flags, int* __restrict__ iters,
+                                                           float* __restrict__ traj, int t_iter, int* status,
+                                                           int* __restrict__ act_out, int* count_out,
+                                                           long long* rows_accum, unsigned int* done_ctr) {
+    extern __shared__ float fin_red[];  // [NW][n_pad] sums, [NW][n_pad] compensations, [NW][4] moments
+    float* red_s = fin_red;
+    float* red_c = fin_red + NW * n_pad;
+    float* redm = fin_red + 2 * NW * n_pad;
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    const int j = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j < M_act) {
+        finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
+                         traj, t_iter, status, red_s, red_c, redm);
+    }
+    compact_tail<NW>(flags, act_idx, M_act, act_out, count_out, rows_accum, done_ctr);
+}
+
+// Rows with many splits and few rows (the refinement) get 32 warps each, others 8. (Measured on
+// GB300: one warp per row, even with four loads in flight per lane, was slower - fewer warps
+// in flight to hide the L2 latency of the split partials.)
 cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
