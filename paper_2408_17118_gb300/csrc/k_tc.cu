@@ -31,15 +31,17 @@ namespace ica {
 // the next ones. TMEM holds D2 (n_pad columns) plus NB Z buffers of TC columns;
 // shared memory must keep at least NB + 1 X~ stages in flight (NB stages are pinned by chunks
 // waiting for their second product).
-// Chunks are as wide as TMEM allows (fixed costs per chunk - barrier round trips and commits -
-// dominate at small n): n_pad <= 64 uses 192 samples (accumulator 64 columns + 2 x 192).
+// Chunks are as wide as TMEM and shared memory allow (fixed costs per chunk - barrier round
+// trips and commits - dominate at small n): n_pad <= 64 uses 192 samples (accumulator 64
+// columns + 2 x 192), n_pad <= 128 uses 128 (128 + 2 x 128 columns; three 32 KB X~ stages),
+// larger n_pad 64.
 #ifndef ICA_TC_SMALL_CHUNK
 #define ICA_TC_SMALL_CHUNK 192
 #endif
 #ifndef ICA_TC_SMALL_NB
 #define ICA_TC_SMALL_NB 2
 #endif
-int tc_chunk(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_CHUNK : 64; }
+int tc_chunk(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_CHUNK : (n_pad <= 128 ? 128 : 64); }
 int tc_buffers(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_NB : 2; }
 // Optional K-major operand for the first product from a transposed copy of X~. Measured on GB300
 // the MN-major read of the X~ tile is as fast, so the copy is not used (saves its traffic).
@@ -454,6 +456,7 @@ cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, con
                        : launch_tc_impl<TCV, NBV, KTV, false, false>(ICA_TC_ARGS);                  \
     } while (0)
     if (n_pad <= 64) ICA_TC_DISPATCH(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB, false);
+    if (n_pad <= 128 && !KT) ICA_TC_DISPATCH(128, 2, false);
     if (KT) ICA_TC_DISPATCH(64, 2, true);
     ICA_TC_DISPATCH(64, 2, false);
 #undef ICA_TC_DISPATCH
