@@ -175,8 +175,12 @@ int map_device_status(int st) {
 }
 
 // Split of the sample range: about two waves of CTAs over the SMs, capped by kMaxCTAs.
-void choose_splits(int64_t total_chunks, int tiles, int waves_ctas, int max_splits, int* splits, int* cps) {
-    int s = (waves_ctas + tiles - 1) / tiles;
+void choose_splits(int64_t total_chunks, int tiles, int waves_ctas, int max_splits, int* splits, int* cps,
+                   bool one_wave = false) {
+    // one_wave: never more CTAs than the target (one CTA per SM): a partial second wave runs a
+    // few CTAs alone for a whole CTA's time (measured on GB300, n = 128, M = 4096, T = 1e6:
+    // 32 tiles x 5 splits = 160 CTAs 3.13 ms, 32 x 4 = 128 CTAs 1.91 ms)
+    int s = one_wave && tiles <= waves_ctas ? waves_ctas / tiles : (waves_ctas + tiles - 1) / tiles;
     const int cap = kMaxCTAs / tiles > 0 ? kMaxCTAs / tiles : 1;
     if (s > cap) s = cap;
     if (max_splits > 0 && s > max_splits) s = max_splits;
@@ -264,7 +268,7 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
         const int TC = tc_chunk(a.n_pad);
         const int64_t total = (a.T + TC - 1) / TC;
         const int tiles = (a.M_act + kTcRows - 1) / kTcRows;
-        choose_splits(total, tiles, 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps);  // one wave
+        choose_splits(total, tiles, 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps, true);  // one wave
         shape->part_rows = tiles * kTcRows;
         CUtensorMap map, map_t;
         int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
