@@ -296,9 +296,9 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
     compact_tail<NW>(flags, act_idx, M_act, act_out, count_out, rows_accum, done_ctr);
 }
 
-// Rows with many splits and few rows (the refinement) get 32 warps each, others 8. (Measured on
-// GB300: one warp per row, even with four loads in flight per lane, was slower - fewer warps
-// in flight to hide the L2 latency of the split partials.)
+// Rows with many splits and few rows (the refinement) get 32 warps each, others 4: with 8 warps
+// (58 registers) only four blocks fit an SM and 1024 rows took 1.7 waves (ncu); one warp per
+// row, even with four loads in flight per lane, was slower (too few warps to hide L2 latency).
 cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
@@ -313,8 +313,8 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                                                       count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
                                                       t_iter, status, act_out, count_out, rows_accum, done_ctr);
     } else {
-        const size_t smem = sizeof(float) * 8 * (2 * n_pad + 4);
-        finalize_kernel<8><<<M_act, 256, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
+        const size_t smem = sizeof(float) * 4 * (2 * n_pad + 4);
+        finalize_kernel<4><<<M_act, 128, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                                                     count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
                                                     t_iter, status, act_out, count_out, rows_accum, done_ctr);
     }
