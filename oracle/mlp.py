@@ -5,13 +5,15 @@ bench.py's CPU legs may use it.
 
 The pruner is a small multilayer perceptron that reads, for one restart of one component, the
 kurtosis alpha (Eq. 2) of the restart's row at the first five fixed-point iterations and the
-step distance min(||b - b_prev||, ||b + b_prev||) of those iterations, plus the reduced
-dimension n and log T, and returns the probability that the restart ends at the direction the
-component picks (Algorithm 2's global optimum). Layout of the parameter vector (float32 on the
-device, float64 here), shared with the library:
+step distance min(||b - b_prev||, ||b + b_prev||) of those iterations, the reduced dimension n,
+log T, and how far the restart's objective Upsilon (Eq. 1) at iteration 5 lies below the best
+one among the restarts still running then; it returns the probability that the restart ends
+at the direction the component picks (Algorithm 2's global optimum). Upsilon is evaluated with
+alpha clamped at -1.999 so that the gap stays finite for binary-like directions. Layout of the
+parameter vector (float32 on the device, float64 here), shared with the library:
 
-    mean[12], scale[12]            feature standardisation  x_hat = (x - mean) * scale
-    W1[64][12], b1[64]             h1 = relu(W1 x_hat + b1)
+    mean[13], scale[13]            feature standardisation  x_hat = (x - mean) * scale
+    W1[64][13], b1[64]             h1 = relu(W1 x_hat + b1)
     W2[64][64], b2[64]             h2 = relu(W2 h1 + b2)
     w3[64], b3                     logit = w3 . h2 + b3,  p = sigmoid(logit)
 
@@ -23,7 +25,8 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_HID = 12, 64
+N_IN, N_HID = 13, 64
+ALPHA_CLAMP = -1.999
 SIZES = [("mean", (N_IN,)), ("scale", (N_IN,)), ("W1", (N_HID, N_IN)), ("b1", (N_HID,)),
          ("W2", (N_HID, N_HID)), ("b2", (N_HID,)), ("w3", (N_HID,)), ("b3", (1,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SIZES)
@@ -43,12 +46,24 @@ def pack(blocks: dict) -> np.ndarray:
     return np.concatenate([np.asarray(blocks[name], dtype=np.float64).reshape(-1) for name, _ in SIZES])
 
 
-def features(alpha_traj: np.ndarray, step_traj: np.ndarray, n: int, T: int) -> np.ndarray:
-    """Rows of the 12 pruner inputs: alpha at iterations 1..5, step distance at 1..5, n, log T."""
+def upsilon_clamped(alpha) -> np.ndarray:
+    """Eq. 1 with alpha clamped at ALPHA_CLAMP (finite everywhere)."""
+    a = np.maximum(np.asarray(alpha, dtype=np.float64), ALPHA_CLAMP)
+    return a - 2.0 * np.log(a / 2.0 + 1.0)
+
+
+def features(alpha_traj: np.ndarray, step_traj: np.ndarray, n: int, T: int, active5=None) -> np.ndarray:
+    """Rows of the 13 pruner inputs: alpha at iterations 1..5, step distance at 1..5, n, log T,
+    and Upsilon(alpha_5) minus the largest Upsilon(alpha_5) among the rows marked active5 (the
+    restarts still running at iteration 5; all rows when None)."""
     a = np.asarray(alpha_traj, dtype=np.float64)
     d = np.asarray(step_traj, dtype=np.float64)
     rows = a.shape[0]
-    return np.concatenate([a, d, np.full((rows, 1), float(n)), np.full((rows, 1), np.log(float(T)))], axis=1)
+    u5 = upsilon_clamped(a[:, 4])
+    mask = np.ones(rows, dtype=bool) if active5 is None else np.asarray(active5, dtype=bool)
+    ref = u5[mask].max() if mask.any() else 0.0
+    return np.concatenate([a, d, np.full((rows, 1), float(n)), np.full((rows, 1), np.log(float(T))),
+                           (u5 - ref)[:, None]], axis=1)
 
 
 def standardisation(F: np.ndarray, eps: float = 1e-6):
@@ -103,7 +118,7 @@ def loss_grad(params: np.ndarray, F: np.ndarray, y: np.ndarray, pos_weight: floa
 
 def adam_step(params, m, v, grad, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba, 2015) of every parameter; returns new (params, m, v).
-    The standardisation block (first 24 entries) is left unchanged."""
+    The standardisation block (first 2 * N_IN entries) is left unchanged."""
     params = np.array(params, dtype=np.float64)
     m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * grad
     v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * grad * grad

@@ -14,7 +14,7 @@ def _rand_params(rng, scale=0.3):
 
 
 def test_layout_size():
-    assert mlp.N_PARAMS == 24 + 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1
+    assert mlp.N_PARAMS == 26 + 64 * 13 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 @pytest.mark.parametrize("pos_weight", [1.0, 4.0])
@@ -25,11 +25,11 @@ def test_backprop_matches_finite_differences(pos_weight):
     y = (rng.uniform(size=40) < 0.3).astype(np.float64)
     L, g = mlp.loss_grad(params, F, y, pos_weight)
     assert np.isclose(L, mlp.loss(params, F, y, pos_weight))
-    idx = list(range(24, mlp.N_PARAMS, 7)) + [mlp.N_PARAMS - 1]
+    idx = list(range(2 * mlp.N_IN, mlp.N_PARAMS, 7)) + [mlp.N_PARAMS - 1]
     gn = mlp.numeric_grad(params, F, y, pos_weight, h=1e-6, idx=idx)
     err = np.abs(g[idx] - gn[idx]).max() / np.abs(gn[idx]).max()
     assert err < 1e-6
-    assert np.all(g[:24] == 0.0)
+    assert np.all(g[:2 * mlp.N_IN] == 0.0)
 
 
 def test_zero_network_closed_form():
@@ -61,13 +61,14 @@ def test_first_adam_step_is_signed_learning_rate():
     lr = 0.01
     new, m, v = mlp.adam_step(params, np.zeros_like(g), np.zeros_like(g), g, 1, lr)
     upd = params - new
-    assert np.all(upd[:24] == 0)
-    assert np.allclose(upd[24:], lr * np.sign(g[24:]), rtol=1e-4)
+    k = 2 * mlp.N_IN
+    assert np.all(upd[:k] == 0)
+    assert np.allclose(upd[k:], lr * np.sign(g[k:]), rtol=1e-4)
 
 
 def test_standardisation():
     rng = np.random.default_rng(4)
-    F = rng.standard_normal((1000, mlp.N_IN)) * np.arange(1, 13) + np.arange(12)
+    F = rng.standard_normal((1000, mlp.N_IN)) * np.arange(1, 14) + np.arange(13)
     mean, scale = mlp.standardisation(F)
     Z = (F - mean) * scale
     assert np.allclose(Z.mean(axis=0), 0, atol=1e-12)
@@ -75,12 +76,17 @@ def test_standardisation():
 
 
 def test_features_layout():
-    a = np.arange(10.0).reshape(2, 5)
-    d = -np.arange(10.0).reshape(2, 5)
-    F = mlp.features(a, d, 17, 1000)
-    assert F.shape == (2, 12)
+    a = np.array([[0.1, 0.2, 0.3, 0.4, 0.5], [1.0, 1.5, 2.0, 2.5, 3.0], [-1.0, -2.5, -3.0, -2.0, -2.5]])
+    d = -np.arange(15.0).reshape(3, 5)
+    F = mlp.features(a, d, 17, 1000, active5=[True, True, False])
+    assert F.shape == (3, 13)
     assert np.all(F[:, :5] == a) and np.all(F[:, 5:10] == d)
     assert np.all(F[:, 10] == 17) and np.allclose(F[:, 11], np.log(1000))
+    # Upsilon gap at iteration 5 against the best active row (row 1: alpha 3 -> 3 - 2 log 2.5)
+    u = lambda x: x - 2 * np.log(x / 2 + 1)
+    assert F[1, 12] == 0.0 and np.isclose(F[0, 12], u(0.5) - u(3.0))
+    # alpha below -2 is clamped: finite gap
+    assert np.isclose(F[2, 12], u(mlp.ALPHA_CLAMP) - u(3.0))
 
 
 def test_training_reduces_loss_on_separable_data():
