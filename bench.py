@@ -366,7 +366,7 @@ def run_ours(args):
         train_sets = [ica.ica_whiten(ctx, torch.from_numpy(workload(args.config, args.seed + 101 + j).X).to(dev))[0]
                       for j in range(2)]
         F, y = pr.collect(ctx, train_sets, M, w.iters, w.tol, seed=4321)
-        params, tau, report = pr.train(ctx, F, y, steps=400)
+        params, tau, report = pr.train(ctx, F, y, steps=400, recall=0.99)
         report["collect_and_train_seconds"] = time.perf_counter() - t_tr
         del train_sets, F, y
         popts = ica.ica_default_opts(precision=ica.ICA_BF16)

@@ -82,7 +82,7 @@ typedef struct {
     float prune_tau;       /* keep-probability threshold (default 0.05) */
     float* record_features; /* optional (device): n_components x M x ICA_MLP_IN raw pruner inputs
                               of every restart (alpha at iterations 1..5, step distance at 1..5,
-                              n = N - i + 1, log T), for training the pruner */
+                              n = N - i + 1, log T, Upsilon gap at iteration 5), for training */
     float* record_labels;  /* optional (device, with record_features): n_components x M labels,
                               1 when the restart ended at the picked direction
                               (|b_r . b_p| >= 1 - 1e-3), else 0 */
@@ -243,20 +243,21 @@ int ica_order_fit_batched(ica_ctx* ctx, const ica_dataset* sets, int count, int 
                           uint64_t seed, const ica_opts* opts, int workers);
 
 /* ---------------------------------------------------------------------------------------
-   Learned restart pruner: a 12-64-64-1 perceptron (ReLU, sigmoid output) trained on the
+   Learned restart pruner: a 13-64-64-1 perceptron (ReLU, sigmoid output) trained on the
    trajectories the method itself records (record_features / record_labels above). Not part of
    the paper. Parameter vector layout (ICA_MLP_PARAMS FP32 values, device):
-     mean[12], scale[12]        input standardisation x_hat = (x - mean) * scale
-     W1[64][12], b1[64]         h1 = relu(W1 x_hat + b1)
+     mean[13], scale[13]        input standardisation x_hat = (x - mean) * scale
+     W1[64][13], b1[64]         h1 = relu(W1 x_hat + b1)
      W2[64][64], b2[64]         h2 = relu(W2 h1 + b2)
      w3[64], b3                 p = sigmoid(w3 . h2 + b3)
    Feature rows (ICA_MLP_IN FP32 values): alpha at iterations 1..5, step distance at 1..5, n,
-   log T. The kernels keep FP32 master weights; with fp16 = 1 weights and activations are
+   log T, and Upsilon(alpha_5) (Eq. 1, alpha clamped at -1.999) minus the largest such value among
+   the restarts still running at iteration 5. The kernels keep FP32 master weights; with fp16 = 1 weights and activations are
    rounded to FP16 (accumulation stays FP32), fp16 = 0 runs everything in FP32.
    --------------------------------------------------------------------------------------- */
-#define ICA_MLP_IN 12
+#define ICA_MLP_IN 13
 #define ICA_MLP_HIDDEN 64
-#define ICA_MLP_PARAMS 5081
+#define ICA_MLP_PARAMS 5147
 
 /* He-initialised weights (Philox4x32-10 keyed by seed), zero biases, mean 0, scale 1. */
 int ica_mlp_init(ica_ctx* ctx, uint64_t seed, float* params);

@@ -54,9 +54,9 @@ class ica_dataset(C.Structure):
 
 
 # learned restart pruner (include/ica.h)
-ICA_MLP_IN = 12
+ICA_MLP_IN = 13
 ICA_MLP_HIDDEN = 64
-ICA_MLP_PARAMS = 5081
+ICA_MLP_PARAMS = 5147
 
 
 vp, i32, i64, u64, f64, sz, f32 = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t, C.c_float

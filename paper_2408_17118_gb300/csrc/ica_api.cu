@@ -729,6 +729,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     std::vector<int> comp_iters, comp_refine, comp_pruned, comp_fallback;
     const bool prune_opt = o.prune_params != nullptr && o.precision != ICA_PLAIN_FP32;
     int* pruned = at<int>(c, L.pruned);
+    float* uref = reinterpret_cast<float*>(counts + 12);  // pruner feature reference (one float)
     std::vector<std::vector<int>> comp_hist;
     int found = 0;
     for (int i = 0; i < n_components; ++i) {
@@ -807,7 +808,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     int before = M_host;
                     rc = timed(K_PRUNE, 0.0, [&] {
                         KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, n,
-                                        std::log(static_cast<double>(T)), o.prune_tau, flags, pruned));
+                                        std::log(static_cast<double>(T)), o.prune_tau, uref, flags, pruned));
                         KL(launch_compact_keep(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1)));
                         return ICA_OK;
                     });
@@ -898,7 +899,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             KL(launch_argmax(s, ups, nullptr, cand_list, counts + 2, k, slots));
         }
         if (o.record_features && o.record_labels)
-            KL(launch_record(s, traj, B32, n_pad, n, M, slots, std::log(static_cast<double>(T)),
+            KL(launch_record(s, traj, itc, B32, n_pad, n, M, slots, std::log(static_cast<double>(T)), uref,
                              o.record_features + static_cast<int64_t>(i) * M * kMlpIn,
                              o.record_labels + static_cast<int64_t>(i) * M));
         // w_i = b_p G appended to W (Algorithm 2)

@@ -101,7 +101,7 @@ cudaError_t launch_fused_fp32_rows(cudaStream_t s, bool moments_only, const floa
                                    int part_rows);
 
 // ---- k_mlp.cu (learned restart pruner) ----
-constexpr int kMlpIn = 12, kMlpHid = 64;
+constexpr int kMlpIn = 13, kMlpHid = 64;
 constexpr int kMlpParams = 2 * kMlpIn + kMlpHid * kMlpIn + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid + 1;
 constexpr int kActRow = 272;  // floats of training activations per sample
 int mlp_slices(int rows);
@@ -113,9 +113,10 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
                                   const float* y, int rows, float lr, float pos_weight, bool fp16, float* scratch,
                                   float* loss_out, float* grad_out);
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
-                         const int* count_dev, int count_host, int n, double logT, float tau, int* keep, int* pruned);
-cudaError_t launch_record(cudaStream_t s, const float* traj, const float* B32, int ldb, int n, int M, const int* slot,
-                          double logT, float* F_out, float* y_out);
+                         const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
+                         int* pruned);
+cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, const float* B32, int ldb, int n, int M,
+                          const int* slot, double logT, float* ref, float* F_out, float* y_out);
 cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, int M, int* out);
 cudaError_t launch_compact_keep(cudaStream_t s, const int* keep, const int* act_in, const int* count_in_dev,
                                 int count_host, int* act_out, int* count_out_dev);

@@ -1,13 +1,14 @@
-// Learned restart pruner (not part of the paper's method): a 12-64-64-1 perceptron that reads
+// Learned restart pruner (not part of the paper's method): a 13-64-64-1 perceptron that reads
 // the first five iterations of a restart (kurtosis alpha of Eq. 2 and the step distance of the
-// convergence test) plus n and log T, and predicts whether the restart ends at the direction the
+// convergence test), n, log T and the gap of the restart's Upsilon (Eq. 1) at iteration 5 to the
+// best restart still running then, and predicts whether the restart ends at the direction the
 // component picks. Inference and training run here: FP16 weights and activations (the "fp16"
 // switch; 0 keeps everything FP32 for gradient checks), FP32 accumulation, FP32 master weights
 // and Adam moments.
 //
-// Parameter vector (FP32, kMlpParams floats): mean[12], scale[12], W1[64][12], b1[64],
+// Parameter vector (FP32, kMlpParams floats): mean[13], scale[13], W1[64][13], b1[64],
 // W2[64][64], b2[64], w3[64], b3. Training scratch: per sample a row of kActRow floats
-// (x_hat 12, h1 64, d1 64, h2 64, d2 64, dz 1), sample-major, so that the gradient kernel reads
+// (x_hat 13, h1 64, d1 64, h2 64, d2 64, dz 1), sample-major, so that the gradient kernel reads
 // the activations of one sample with coalesced loads.
 #include <cuda_fp16.h>
 
@@ -18,10 +19,10 @@ namespace ica {
 
 namespace {
 constexpr int IN = kMlpIn, HID = kMlpHid;
-constexpr int OFF_MEAN = 0, OFF_SCALE = 12, OFF_W1 = 24, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
+constexpr int OFF_MEAN = 0, OFF_SCALE = IN, OFF_W1 = 2 * IN, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
               OFF_B2 = OFF_W2 + HID * HID, OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID;
 static_assert(OFF_B3 + 1 == kMlpParams, "parameter layout");
-constexpr int A_X = 0, A_H1 = 12, A_D1 = A_H1 + HID, A_H2 = A_D1 + HID, A_D2 = A_H2 + HID, A_DZ = A_D2 + HID;
+constexpr int A_X = 0, A_H1 = IN, A_D1 = A_H1 + HID, A_H2 = A_D1 + HID, A_D2 = A_H2 + HID, A_DZ = A_D2 + HID;
 static_assert(A_DZ + 1 <= kActRow, "activation row");
 
 // Rounds to FP16 and back when the kernel runs in FP16 mode.
@@ -260,8 +261,16 @@ __global__ void mlp_standardize_kernel(const float* __restrict__ F, int rows, fl
     }
 }
 
-// Raw features of restart r: alpha and step distance of the first kTrajLen iterations, n, log T.
-__device__ __forceinline__ void restart_features(const float* __restrict__ traj, int r, float n, float logT, float* x) {
+// Eq. 1 with alpha clamped at -1.999 (finite for binary-like directions).
+__device__ __forceinline__ float upsilon_clamped(float a) {
+    a = fmaxf(a, -1.999f);
+    return a - 2.f * logf(0.5f * a + 1.f);
+}
+
+// Raw features of restart r: alpha and step distance of the first kTrajLen iterations, n, log T,
+// and Upsilon(alpha at iteration kTrajLen) minus ref (the best among the restarts running then).
+__device__ __forceinline__ void restart_features(const float* __restrict__ traj, int r, float n, float logT,
+                                                 float ref, float* x) {
 #pragma unroll
     for (int t = 0; t < kTrajLen; ++t) {
         x[t] = traj[(static_cast<int64_t>(r) * kTrajLen + t) * 2 + 0];
@@ -269,13 +278,37 @@ __device__ __forceinline__ void restart_features(const float* __restrict__ traj,
     }
     x[10] = n;
     x[11] = logT;
+    x[12] = upsilon_clamped(x[kTrajLen - 1]) - ref;
+}
+
+// ref = max Upsilon(alpha at iteration kTrajLen) over the restarts running then: the active list
+// (act_idx / count) inside a fit, or the restarts with iters[r] >= kTrajLen when recording.
+__global__ void upsilon_ref_kernel(const float* __restrict__ traj, const int* __restrict__ act_idx,
+                                   const int* __restrict__ count_dev, int count_host, const int* __restrict__ iters,
+                                   float* __restrict__ ref) {
+    __shared__ float red[256];
+    const int count = count_dev ? *count_dev : count_host;
+    float m = -INFINITY;
+    for (int j = threadIdx.x; j < count; j += blockDim.x) {
+        const int r = act_idx ? act_idx[j] : j;
+        if (iters && iters[r] < kTrajLen) continue;
+        m = fmaxf(m, upsilon_clamped(traj[(static_cast<int64_t>(r) * kTrajLen + kTrajLen - 1) * 2]));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ref = isfinite(red[0]) ? red[0] : 0.f;
 }
 
 // Inference on the active restarts inside a fit: keep flag (p >= tau) per active slot j, and
 // the pruned mark of every restart it drops.
 __global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ params, const float* __restrict__ traj,
                                                     const int* __restrict__ act_idx, const int* __restrict__ count_dev,
-                                                    int count_host, float n, float logT, float tau,
+                                                    int count_host, float n, float logT,
+                                                    const float* __restrict__ ref, float tau,
                                                     int* __restrict__ keep, int* __restrict__ pruned) {
     __shared__ SmemNet s;
     load_net<true>(params, s);
@@ -284,7 +317,7 @@ __global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ pa
     if (j >= count) return;
     const int r = act_idx ? act_idx[j] : j;
     float x[IN];
-    restart_features(traj, r, n, logT, x);
+    restart_features(traj, r, n, logT, *ref, x);
     const float p = sigmoidf(forward_one<true>(s, x, nullptr, nullptr));
     const int k = p >= tau ? 1 : 0;
     keep[j] = k;
@@ -294,12 +327,12 @@ __global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ pa
 // Training record of one component: raw features of every restart and whether the restart
 // ended at the picked direction (|b_r . b_p| >= 1 - 1e-3 on normalised rows).
 __global__ void record_kernel(const float* __restrict__ traj, const float* __restrict__ B32, int ldb, int n_dim, int M,
-                              const int* __restrict__ slot, float n, float logT, float* __restrict__ F_out,
-                              float* __restrict__ y_out) {
+                              const int* __restrict__ slot, float n, float logT, const float* __restrict__ ref,
+                              float* __restrict__ F_out, float* __restrict__ y_out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
     float x[IN];
-    restart_features(traj, r, n, logT, x);
+    restart_features(traj, r, n, logT, *ref, x);
 #pragma unroll
     for (int i = 0; i < IN; ++i) F_out[static_cast<int64_t>(r) * IN + i] = x[i];
     const int p = *slot;
@@ -394,17 +427,24 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 }
 
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
-                         const int* count_dev, int count_host, int n, double logT, float tau, int* keep, int* pruned) {
+                         const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
+                         int* pruned) {
+    upsilon_ref_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, nullptr, ref);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     prune_kernel<<<(count_host + 127) / 128, 128, 0, s>>>(params, traj, act_idx, count_dev, count_host,
-                                                          static_cast<float>(n), static_cast<float>(logT), tau, keep,
-                                                          pruned);
+                                                          static_cast<float>(n), static_cast<float>(logT), ref, tau,
+                                                          keep, pruned);
     return cudaGetLastError();
 }
 
-cudaError_t launch_record(cudaStream_t s, const float* traj, const float* B32, int ldb, int n, int M, const int* slot,
-                          double logT, float* F_out, float* y_out) {
+cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, const float* B32, int ldb, int n, int M,
+                          const int* slot, double logT, float* ref, float* F_out, float* y_out) {
+    upsilon_ref_kernel<<<1, 256, 0, s>>>(traj, nullptr, nullptr, M, iters, ref);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     record_kernel<<<(M + 127) / 128, 128, 0, s>>>(traj, B32, ldb, n, M, slot, static_cast<float>(n),
-                                                  static_cast<float>(logT), F_out, y_out);
+                                                  static_cast<float>(logT), ref, F_out, y_out);
     return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ def test_gradient_parity(ica, ctx, pos_weight):
         gg = grad.cpu().numpy().astype(np.float64)
         assert abs(float(loss.item()) - L) <= tol_l * abs(L)
         assert np.linalg.norm(gg - g) <= tol_g * np.linalg.norm(g)
-        assert np.all(gg[:24] == 0)
+        assert np.all(gg[:2 * mlp.N_IN] == 0)
     # parameters unchanged with lr = 0
     assert np.array_equal(P.cpu().numpy(), params.astype(np.float32))
 
@@ -85,15 +85,16 @@ def test_adam_step_parity(ica, ctx):
 
 def test_standardize_and_init(ica, ctx):
     rng = np.random.default_rng(7)
-    F = (rng.standard_normal((5000, mlp.N_IN)) * np.arange(1, 13) + np.arange(12)).astype(np.float32)
+    F = (rng.standard_normal((5000, mlp.N_IN)) * np.arange(1, mlp.N_IN + 1) + np.arange(mlp.N_IN)).astype(np.float32)
     P = ica.ica_mlp_init(ctx, 11)
     P2 = ica.ica_mlp_init(ctx, 11)
     assert torch.equal(P, P2)
     ica.ica_mlp_standardize(ctx, _dev(F), P)
     mean, scale = mlp.standardisation(F.astype(np.float64))
     p = P.cpu().numpy()
-    assert np.allclose(p[:12], mean, rtol=1e-5, atol=1e-5)
-    assert np.allclose(p[12:24], scale, rtol=1e-5)
+    k = mlp.N_IN
+    assert np.allclose(p[:k], mean, rtol=1e-5, atol=1e-5)
+    assert np.allclose(p[k:2 * k], scale, rtol=1e-5)
     blocks = mlp.unpack(p.astype(np.float64))
     assert abs(blocks["W1"].std() - np.sqrt(2 / 12)) < 0.05 and abs(blocks["W2"].std() - np.sqrt(2 / 64)) < 0.02
     assert np.all(blocks["b1"] == 0) and np.all(blocks["b2"] == 0) and blocks["b3"][0] == 0
@@ -121,6 +122,13 @@ def test_recorded_features_match_oracle(ica, ctx):
         assert y[i, comp["winner"]] == 1.0
         assert np.all(F[i, :, 10] == 8 - i)
         assert np.allclose(F[i, :, 11], np.log(w.X.shape[1]))
+        # Upsilon gap at iteration 5 to the best restart still running then (rows that stopped
+        # earlier keep alpha_5 = 0 and are not part of the reference)
+        ran5 = F[i, :, 4] != 0.0
+        if ran5.any():
+            ref = mlp.features(F[i, :, :5], F[i, :, 5:10], 8 - i, w.X.shape[1], active5=ran5)[:, 12]
+            assert np.abs(F[i, :, 12] - ref).max() < 1e-4
+            assert F[i, ran5, 12].max() == 0.0
     assert np.all((y == 0) | (y == 1))
 
 
