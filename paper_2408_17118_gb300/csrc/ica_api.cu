@@ -257,6 +257,7 @@ struct FusedArgs {
     int tcols = 0;
     int64_t ldx = 0;
     int max_splits = 0;
+    int* shape_dev = nullptr;  // BF16 update: shape the launch on the device, write {splits, part_rows} here
 };
 
 int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape) {
@@ -268,6 +269,17 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
         const int TC = tc_chunk(a.n_pad);
         const int64_t total = (a.T + TC - 1) / TC;
         const int tiles = (a.M_act + kTcRows - 1) / kTcRows;
+        if (a.shape_dev && a.count_dev && !a.moments_only && a.max_splits == 0 && !(a.Xt16t && tc_transposed(a.n_pad))) {
+            CUtensorMap map;
+            int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
+            if (rc) return rc;
+            KL(launch_fused_tc_shaped(s, a.moments, map, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.n_pad, a.T,
+                                      152 / c->cta_div, static_cast<int>(total), pacc, pmom, status, a.shape_dev));
+            shape->splits = -1;  // on the device (a.shape_dev)
+            shape->cps = -1;
+            shape->part_rows = -1;
+            return ICA_OK;
+        }
         choose_splits(total, tiles, 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps, true);  // one wave
         shape->part_rows = tiles * kTcRows;
         CUtensorMap map, map_t;
@@ -330,6 +342,9 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
 // first, when most restarts leave, then every second, then every fourth. Between reads the
 // launches are sized for the last count read, an upper bound (counts only fall).
 bool sync_due(int t) { return t <= 4 || (t <= 12 && t % 2 == 0) || t % 4 == 0; }
+// The BF16 stage shapes its launches on the device, so the host reads the count only to stop
+// early when every restart converged.
+bool sync_due_shaped(int t) { return t % 4 == 0; }
 
 int check_ws(ica_ctx* c, const Layout& L) {
     if (!c->ws || c->ws_bytes < L.total) return ICA_ERR_WORKSPACE;
@@ -779,6 +794,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             // fixed-point iterations with removal of converged rows (Algorithm 2, Section 3.2)
             int cur = 0, M_host = M;
             t = 0;
+            fa.shape_dev = bf16 ? counts + 14 : nullptr;  // {splits, part_rows} of each BF16 update
             while (t < iters && M_host > 0) {
                 StepShape sh;
                 fa.act = act[cur];
@@ -792,13 +808,13 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
                                        n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
                                        o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
-                                       counts + (cur ^ 1), crows + 2 * i, done_ctr));
+                                       counts + (cur ^ 1), crows + 2 * i, done_ctr, fa.shape_dev));
                     return ICA_OK;
                 });
                 if (rc) return rc;
                 cur ^= 1;
                 ++t;
-                if (sync_due(t)) {
+                if (fa.shape_dev ? sync_due_shaped(t) : sync_due(t)) {
                     rc = read_count(counts + cur, &M_host);
                     if (rc) return rc;
                     hist.push_back(M_host);
@@ -824,6 +840,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     dropped_all = before > 0 && M_host == 0;
                 }
             }
+            fa.shape_dev = nullptr;
             // kurtosis of every candidate: converged rows plus rows still running after `iters`
             {
                 StepShape sh;

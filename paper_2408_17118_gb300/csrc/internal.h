@@ -43,7 +43,7 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr);
+                            unsigned int* done_ctr, const int* shape_dev = nullptr);
 cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                            int part_rows, int n_pad, int M, const float* B, double inv_T, float* Bnew,
                            float* moments);
@@ -121,6 +121,20 @@ cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pru
 cudaError_t launch_compact_keep(cudaStream_t s, const int* keep, const int* act_in, const int* count_in_dev,
                                 int count_host, int* act_out, int* count_out_dev);
 
+// Launch shape of a fused tcgen05 update from the device count of active rows (also evaluated
+// by the finalize): tiles of 128 rows, splits of the sample range so that tiles x splits <= ctas
+// (one wave), chunks per split.
+__host__ __device__ inline void tc_device_shape(int M_act, int ctas, int total_chunks, int* tiles, int* splits,
+                                                int* cps) {
+    const int t = (M_act + kTcRows - 1) / kTcRows;
+    int s = t < 1 ? 1 : (t <= ctas ? ctas / t : 1);
+    if (s > total_chunks) s = total_chunks;
+    if (s < 1) s = 1;
+    const int c = (total_chunks + s - 1) / s;
+    *tiles = t;
+    *cps = c;
+    *splits = (total_chunks + c - 1) / c;
+}
 // ---- k_tc.cu ----
 int tc_chunk(int n_pad);
 bool tc_transposed(int n_pad);
@@ -128,6 +142,9 @@ size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out);
 // xmap: X~ (n_pad x T, samples contiguous), box {64, n_pad}. xmap_t (optional, n_pad <= 128):
 // X~^T (T x round_up64cols(n_pad), reduced index contiguous), box {64, tc_chunk(n_pad)}; when
 // given, the first product reads it as a K-major operand.
+cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
+                                   const int* act_idx, const int* count_dev, int M_ub, int n_pad, int64_t T, int ctas,
+                                   int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out);
 cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
                             const CUtensorMap* xmap_t, const float* B32, int ldb, const int* act_idx,
                             const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,

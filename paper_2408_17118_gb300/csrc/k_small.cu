@@ -281,8 +281,13 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
                                                            int* __restrict__ flags, int* __restrict__ iters,
                                                            float* __restrict__ traj, int t_iter, int* status,
                                                            int* __restrict__ act_out, int* count_out,
-                                                           long long* rows_accum, unsigned int* done_ctr) {
+                                                           long long* rows_accum, unsigned int* done_ctr,
+                                                           const int* __restrict__ shape_dev) {
     extern __shared__ float fin_red[];  // [NW][n_pad] sums, [NW][n_pad] compensations, [NW][4] moments
+    if (shape_dev) {  // split count and partial-row stride chosen on the device by the fused launch
+        splits = shape_dev[0];
+        part_rows = shape_dev[1];
+    }
     float* red_s = fin_red;
     float* red_c = fin_red + NW * n_pad;
     float* redm = fin_red + 2 * NW * n_pad;
@@ -303,7 +308,7 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr) {
+                            unsigned int* done_ctr, const int* shape_dev) {
     const float fT = static_cast<float>(inv_T), ftol = static_cast<float>(tol);
     if (M_act <= 64 && splits > 16) {
         const size_t smem = sizeof(float) * 32 * (2 * n_pad + 4);
@@ -311,12 +316,12 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
         if (e != cudaSuccess) return e;
         finalize_kernel<32><<<M_act, 1024, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                                                       count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
-                                                      t_iter, status, act_out, count_out, rows_accum, done_ctr);
+                                                      t_iter, status, act_out, count_out, rows_accum, done_ctr, shape_dev);
     } else {
         const size_t smem = sizeof(float) * 4 * (2 * n_pad + 4);
         finalize_kernel<4><<<M_act, 128, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                                                     count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
-                                                    t_iter, status, act_out, count_out, rows_accum, done_ctr);
+                                                    t_iter, status, act_out, count_out, rows_accum, done_ctr, shape_dev);
     }
     return cudaGetLastError();
 }

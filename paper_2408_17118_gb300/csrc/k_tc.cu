@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int total_chunks, int stages, uint32_t a_bytes, uint32_t xsub_bytes, uint32_t xstage_bytes,
                     uint32_t off_x,
                     uint32_t off_p, uint32_t off_bar, float* __restrict__ part_acc, float* __restrict__ part_mom,
-                    int part_rows, int* status) {
+                    int part_rows, int* status, int shape_ctas, int* shape_out) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_u32 = smem_u32(smem_raw);
     const uint32_t base_u32 = (raw_u32 + 1023u) & ~1023u;
@@ -134,12 +134,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* mom_sm = reinterpret_cast<float*>(bars + kBars + 2);  // [3][128][4]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int split = blockIdx.x, tile = blockIdx.y;
-    const int m0 = tile * kTcRows;
     const int M_act = count_dev ? *count_dev : M_act_host;
+    int split = blockIdx.x, tile = blockIdx.y, cps = chunks_per_split;
+    if (shape_ctas > 0) {
+        // launch shape from the device count (the host knows only an upper bound): tiles of 128
+        // active rows x splits of the sample range, at most one wave (tc_device_shape)
+        int tiles, sp;
+        tc_device_shape(M_act, shape_ctas, total_chunks, &tiles, &sp, &cps);
+        const int b = blockIdx.x;
+        if (b == 0 && threadIdx.x == 0 && shape_out) {
+            shape_out[0] = sp;
+            shape_out[1] = tiles * kTcRows;
+        }
+        if (b >= tiles * sp) return;
+        tile = b / sp;
+        split = b % sp;
+        part_rows = tiles * kTcRows;
+    }
+    const int m0 = tile * kTcRows;
     if (m0 >= M_act) return;  // grid sized for an upper bound of the active count
-    const int c_begin = split * chunks_per_split;
-    const int c_end = min(total_chunks, c_begin + chunks_per_split);
+    const int c_begin = split * cps;
+    const int c_end = min(total_chunks, c_begin + cps);
     const int nch = c_end - c_begin;
 
     if (threadIdx.x == 0) {
@@ -427,18 +442,39 @@ static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const
                                   const float* B32, int ldb,
                                   const int* act_idx, const int* count_dev, int M_act, int n_pad, int64_t T,
                                   int splits, int chunks_per_split, int total_chunks, float* part_acc,
-                                  float* part_mom, int part_rows, int* status) {
+                                  float* part_mom, int part_rows, int* status, int shape_ctas = 0,
+                                  int* shape_out = nullptr) {
     const TcLayout L = tc_layout(n_pad, MO, TC, NB, KT);
     if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
     if (KT && !xmap_t) return cudaErrorInvalidValue;
     cudaError_t e = allow_max_dyn_smem(fused_tc_kernel<TC, NB, KT, MO, MOM>);
     if (e != cudaSuccess) return e;
-    const dim3 grid(splits, (M_act + kTcRows - 1) / kTcRows);
+    const int tiles_ub = (M_act + kTcRows - 1) / kTcRows;
+    const dim3 grid = shape_ctas > 0 ? dim3(tiles_ub > shape_ctas ? tiles_ub : shape_ctas, 1)
+                                     : dim3(splits, tiles_ub);
     fused_tc_kernel<TC, NB, KT, MO, MOM><<<grid, kThreads, L.total, s>>>(
         xmap, KT ? *xmap_t : xmap, B32, ldb, act_idx, count_dev, M_act, n_pad, T, chunks_per_split, total_chunks,
         static_cast<int>(L.stages), L.a_bytes, L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p, L.off_bar, part_acc,
-        part_mom, part_rows, status);
+        part_mom, part_rows, status, shape_ctas, shape_out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
+                                   const int* act_idx, const int* count_dev, int M_ub, int n_pad, int64_t T, int ctas,
+                                   int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out) {
+    const int TC = tc_chunk(n_pad);
+#define ICA_TC_SHAPED(TCV, NBV)                                                                                     \
+    return moments ? launch_tc_impl<TCV, NBV, false, false, true>(s, xmap, nullptr, B32, ldb, act_idx, count_dev,   \
+                                                                  M_ub, n_pad, T, 0, 0, total_chunks, part_acc,      \
+                                                                  part_mom, 0, status, ctas, shape_out)              \
+                   : launch_tc_impl<TCV, NBV, false, false, false>(s, xmap, nullptr, B32, ldb, act_idx, count_dev,  \
+                                                                   M_ub, n_pad, T, 0, 0, total_chunks, part_acc,     \
+                                                                   part_mom, 0, status, ctas, shape_out)
+    if (n_pad <= 64) ICA_TC_SHAPED(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB);
+    if (n_pad <= 128) ICA_TC_SHAPED(128, 2);
+    ICA_TC_SHAPED(64, 2);
+#undef ICA_TC_SHAPED
+    (void)TC;
 }
 
 cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
