@@ -46,6 +46,14 @@ int tc_buffers(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_NB : 2; }
 // Optional K-major operand for the first product from a transposed copy of X~. Measured on GB300
 // the MN-major read of the X~ tile is as fast, so the copy is not used (saves its traffic).
 bool tc_transposed(int n_pad) { return false; }
+// Restart rows as two BF16 terms (hi = bf16(b), lo = bf16(b - hi)) in the first product, for the
+// 192-sample chunks (n_pad <= 64): Z = B_hi X~ + B_lo X~ carries b to about 16 bits instead of 8,
+// so that the BF16 stage's step distance can fall below its tolerance instead of stalling at the
+// rounding noise of b. Costs one more MMA per K step of the first product.
+#ifndef ICA_TC_SPLIT_B
+#define ICA_TC_SPLIT_B 1
+#endif
+__host__ __device__ constexpr bool tc_split_b(int TC) { return ICA_TC_SPLIT_B && TC == 192; }
 
 namespace {
 constexpr int kBars = 40;
@@ -63,7 +71,7 @@ struct TcLayout {
 };
 TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, bool KT) {
     TcLayout L{};
-    L.a_bytes = static_cast<uint32_t>((n_pad + 63) / 64) * 16384u;
+    L.a_bytes = static_cast<uint32_t>((n_pad + 63) / 64) * 16384u * (tc_split_b(TC) ? 2u : 1u);
     L.xsub_bytes = static_cast<uint32_t>(n_pad) * 128u;
     L.xn_bytes = static_cast<uint32_t>(TC / 64) * L.xsub_bytes;  // X~ tile: n_pad rows x TC samples
     // + X~^T tile: ceil(n_pad / 64) K-blocks of TC rows x 128 bytes
@@ -195,9 +203,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 v1 = src[1];
             }
             const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pack_bf16x2(v0.x, v0.y)),
-                         "r"(pack_bf16x2(v0.z, v0.w)), "r"(pack_bf16x2(v1.x, v1.y)), "r"(pack_bf16x2(v1.z, v1.w))
+            const uint32_t h0 = pack_bf16x2(v0.x, v0.y), h1 = pack_bf16x2(v0.z, v0.w), h2 = pack_bf16x2(v1.x, v1.y),
+                           h3 = pack_bf16x2(v1.z, v1.w);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(h0), "r"(h1), "r"(h2), "r"(h3)
                          : "memory");
+            if constexpr (tc_split_b(TC)) {  // residuals b - float(bf16(b)) in the second half
+                auto lo = [](uint32_t hp, float x, float y) {
+                    return pack_bf16x2(x - __uint_as_float(hp << 16), y - __uint_as_float(hp & 0xFFFF0000u));
+                };
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + (a_bytes >> 1)),
+                             "r"(lo(h0, v0.x, v0.y)), "r"(lo(h1, v0.z, v0.w)), "r"(lo(h2, v1.x, v1.y)),
+                             "r"(lo(h3, v1.z, v1.w))
+                             : "memory");
+            }
         }
         fence_proxy_async_smem();
     }
@@ -264,6 +282,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
                                               : (static_cast<uint32_t>(ks) * 2048u) >> 4;
                     umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
+                }
+                if constexpr (tc_split_b(TC)) {
+                    const uint64_t a1_lo = a1_desc + static_cast<uint64_t>((a_bytes >> 1) >> 4);
+#pragma unroll
+                    for (int ks = 0; ks < 16; ++ks) {
+                        if (ks >= ksteps1) break;
+                        const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                        const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                        umma_bf16_acc(d1, a1_lo + a_off, b1s + b_off, id1);
+                    }
                 }
                 umma_commit(&d1_full[b]);
                 if (MOMENTS_ONLY) umma_commit(&empty[s]);  // no second product reads the stage

@@ -144,8 +144,19 @@ STEP_SHAPES = [(1, 1, 64), (63, 5, 1000), (64, 16, 4097), (65, 17, 12345), (129,
                (300, 100, 5000), (128, 128, 8192), (130, 129, 3000), (257, 200, 6000), (100, 256, 10_000)]
 
 
-def oracle_update(B, Xt, T, bf16_inputs):
-    Bq = bf16(B) if bf16_inputs else B.astype(np.float64)
+def b_operand(B, n_pad):
+    """The restart rows as the BF16 kernel feeds them to the tensor cores: for n_pad <= 64 (192-sample
+    chunks) as two BF16 terms hi = bf16(b), lo = bf16(b - hi); otherwise one BF16 value."""
+    B = np.asarray(B, dtype=np.float32)
+    hi = bf16(B).astype(np.float32)
+    if n_pad > 64:
+        return hi.astype(np.float64)
+    lo = bf16((B - hi).astype(np.float32)).astype(np.float32)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def oracle_update(B, Xt, T, bf16_inputs, n_pad=None):
+    Bq = b_operand(B, n_pad) if bf16_inputs else B.astype(np.float64)
     Xq = bf16(Xt) if bf16_inputs else Xt.astype(np.float64)
     Bq = Bq.astype(np.float64)
     Xq = Xq.astype(np.float64)
@@ -168,7 +179,7 @@ def test_fp_step(ctx, prec, M, n, T):
     Bnew, mom = ica.ica_fp_step(ctx, p, torch.from_numpy(B).cuda(), n, xt, T)
     Bnew = Bnew.cpu().numpy()
     mom = mom.cpu().numpy()
-    U, S, Z = oracle_update(B[:, :n], Xt, T, prec == "bf16")
+    U, S, Z = oracle_update(B[:, :n], Xt, T, prec == "bf16", n_pad)
     tol = (1e-4 if prec == "fp32" else 2.0 ** -8) * S + 1e-6
     err = np.abs(Bnew[:, :n] - U)
     assert np.all(err <= tol), (err.max(), (err / tol).max())
@@ -201,7 +212,7 @@ def test_kurtosis(ctx, prec, M, n, T):
     a, u = ica.ica_kurtosis(ctx, p, torch.from_numpy(B).cuda(), n, xt, T)
     a = a.cpu().numpy()
     u = u.cpu().numpy()
-    Bq = bf16(B[:, :n]).astype(np.float64) if prec == "bf16" else B[:, :n].astype(np.float64)
+    Bq = b_operand(B[:, :n], n_pad) if prec == "bf16" else B[:, :n].astype(np.float64)
     Xq = bf16(Xt).astype(np.float64) if prec == "bf16" else Xt.astype(np.float64)
     Z = Bq @ Xq
     m2 = np.mean(Z ** 2, axis=1)
@@ -228,7 +239,7 @@ def test_fp_step_full_size_sampled(ctx):
     rows = np.random.default_rng(0).choice(M, 16, replace=False)
     Xq = Xt16[:n, :T].float().cpu().numpy().astype(np.float64)
     Bs = B.cpu().numpy()[rows]
-    Zs = bf16(Bs).astype(np.float64) @ Xq
+    Zs = b_operand(Bs, 64) @ Xq
     U = (Zs ** 3) @ Xq.T / T - 3.0 * Bs
     S = (np.abs(Zs) ** 3) @ np.abs(Xq).T / T
     err = np.abs(Bnew.cpu().numpy()[rows] - U)
