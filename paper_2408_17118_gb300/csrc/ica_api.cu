@@ -441,7 +441,7 @@ void ica_default_opts(ica_opts* o) {
     o->precision = ICA_BF16;
     o->gauss_test = 0;
     o->refine_topk = 4;
-    o->refine_iters = 100;
+    o->refine_iters = 10;
     o->stage_tol = 1e-4;
     o->refine_tol = 1e-6;
     o->fp32_tol_floor = 1e-6;

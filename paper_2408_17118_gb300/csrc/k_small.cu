@@ -186,11 +186,13 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
     const int M_act = count_dev ? *count_dev : M_act_host;
     const int j = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (j < M_act) {
-        finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
-                         traj, t_iter, status, red_s, red_c, redm);
+    if (j >= M_act) {  // the grid covers an upper bound of the active count
+        if (j == 0 && threadIdx.x == 0) *count_out = 0;  // nothing active: empty list
+        return;
     }
-    compact_tail<NW>(flags, act_idx, M_act, act_out, count_out, rows_accum, done_ctr);
+    finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
+                     traj, t_iter, status, red_s, red_c, redm);
+    compact_tail<NW>(flags, act_idx, M_act, act_out, count_out, rows_accum, done_ctr, M_act);
 }
 
 // Rows with many splits and few rows (the refinement) get 32 warps each, others 4: with 8 warps

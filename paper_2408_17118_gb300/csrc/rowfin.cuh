@@ -104,18 +104,18 @@ __device__ __forceinline__ void compact_block(const int* __restrict__ flags, con
     }
 }
 
-// The last block of a launch to finish (every block counts itself in after its flags are
-// visible device-wide) compacts the active list into act_out/count_out; *done_ctr is zero on
+// The last of the `blocks` participating blocks to finish (each counts itself in after its flags
+// are visible device-wide) compacts the active list into act_out/count_out; *done_ctr is zero on
 // entry and is left zero. act_out and count_out must not alias the input list and count.
 template <int NW>
 __device__ __forceinline__ void compact_tail(const int* __restrict__ flags, const int* __restrict__ act_idx,
                                              int M_act, int* __restrict__ act_out, int* count_out,
-                                             long long* rows_accum, unsigned int* done_ctr) {
+                                             long long* rows_accum, unsigned int* done_ctr, int blocks) {
     __shared__ int is_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        is_last = atomicAdd(done_ctr, 1u) == gridDim.x - 1;
+        is_last = atomicAdd(done_ctr, 1u) == static_cast<unsigned>(blocks - 1);
     }
     __syncthreads();
     if (!is_last) return;
