@@ -121,10 +121,23 @@ cudaError_t launch_covariance(cudaStream_t s, const float* X, const double* mean
 // Two-sided cyclic Jacobi (Golub & Van Loan, Matrix Computations, Sec. 8.5) with the
 // round-robin (circle) ordering: every round applies m/2 disjoint rotations at once, so a
 // round updates each 2x2 block (pair a, pair b) of A independently: A <- J^T A J, V <- V J.
-// A (m x m, ld m) is overwritten; on exit lam[i] = A[i][i] and the columns of V are the
-// eigenvectors. Stops when the off-diagonal mass is below (1e-15)^2 of the total, or after
-// max_sweeps sweeps (then DEV_ILLCOND is raised). The matrices live in shared memory when
-// they fit, else in global memory (L2 resident).
+// Only the blocks with a <= b are computed; block (b, a) is written as the transpose, which
+// keeps A exactly symmetric and halves the arithmetic on A.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate, and one CTA does all of the work, so the
+// eigensolver is FP64-bound. For m <= kJacMixedMax it runs in two phases:
+//   1. FP32 sweeps on A scaled by a power of two, until the off-diagonal mass is below 1e-11
+//      of the total (or 12 sweeps): V32 holds the eigenvectors to ~1e-6;
+//   2. FP64 polish: two Newton-Schulz steps V <- V (3I - V^T V) / 2 make V orthogonal to
+//      rounding, A' = V^T A V is then diagonal up to ~1e-6, and FP64 sweeps started from
+//      (A', V) converge quadratically (two sweeps in practice) to the same stopping rule as the
+//      plain FP64 solver.
+// The result is an FP64 eigendecomposition (backward stable: V orthogonal to rounding, A = V
+// diag(lam) V^T to rounding) at about a third of the FP64 work of FP64 sweeps from the start.
+// Larger m runs FP64 sweeps only (matrices in shared memory when they fit, else in global
+// memory, L2 resident).
+constexpr int kJacMixedMin = 12, kJacMixedMax = 80;
+
 __device__ __forceinline__ void rr_pair(int r, int a, int me, int& p, int& q) {
     const int mm = me - 1;
     if (a == 0) {
@@ -141,26 +154,90 @@ __device__ __forceinline__ void rr_pair(int r, int a, int me, int& p, int& q) {
     }
 }
 
-__global__ void __launch_bounds__(1024) jacobi_kernel(double* Ag, double* Vg, double* lam, int m, int* status,
-                                                      int max_sweeps, int use_smem) {
-    extern __shared__ double jsm[];
-    __shared__ double rc[kMaxN / 2], rs[kMaxN / 2];
-    __shared__ double red[32];
-    __shared__ int stop;
-    const int me = m + (m & 1);
-    const int np = me / 2;
-    double* A = use_smem ? jsm : Ag;
-    double* V = use_smem ? jsm + m * m : Vg;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < m * m; i += nth) {
-        if (use_smem) A[i] = Ag[i];
-        V[i] = (i / m == i % m) ? 1.0 : 0.0;
+// Rotation (c, s) that zeroes A[p][q] for each pair of round r (one thread per pair).
+template <typename T>
+__device__ __forceinline__ void jac_params(const T* A, int m, int me, int np, int r, T* rc, T* rs) {
+    const int tid = threadIdx.x;
+    if (tid < np) {
+        int p, q;
+        rr_pair(r, tid, me, p, q);
+        T c = T(1), sn = T(0);
+        if (q < m) {
+            const T apq = A[p * m + q];
+            if (apq != T(0)) {
+                const T app = A[p * m + p], aqq = A[q * m + q];
+                const T tau = (aqq - app) / (T(2) * apq);
+                const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                c = T(1) / sqrt(T(1) + t * t);
+                sn = t * c;
+            }
+        }
+        rc[tid] = c;
+        rs[tid] = sn;
     }
-    __syncthreads();
+}
+
+// A <- J^T A J (upper blocks, mirrored) and V <- V J for the rotations of round r.
+template <typename T>
+__device__ __forceinline__ void jac_apply(T* A, T* V, int m, int me, int np, int r, const T* rc, const T* rs) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int e = tid; e < np * np; e += nth) {
+        const int a = e / np, b = e % np;
+        if (a > b) continue;
+        int pa, qa, pb, qb;
+        rr_pair(r, a, me, pa, qa);
+        rr_pair(r, b, me, pb, qb);
+        const T ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
+        const bool qa_ok = qa < m, qb_ok = qb < m;
+        const T x00 = A[pa * m + pb];
+        const T x01 = qb_ok ? A[pa * m + qb] : T(0);
+        const T x10 = qa_ok ? A[qa * m + pb] : T(0);
+        const T x11 = (qa_ok && qb_ok) ? A[qa * m + qb] : T(0);
+        // rows: (p) c x_p - s x_q, (q) s x_p + c x_q
+        const T y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+        const T y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+        // columns: (p) c y_p - s y_q, (q) s y_p + c y_q
+        T z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
+        T z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
+        if (a == b) {  // the rotated pair's own block: its off-diagonal is zero by construction
+            z01 = T(0);
+            z10 = T(0);
+        }
+        A[pa * m + pb] = z00;
+        if (qb_ok) A[pa * m + qb] = z01;
+        if (qa_ok) A[qa * m + pb] = z10;
+        if (qa_ok && qb_ok) A[qa * m + qb] = z11;
+        if (a != b) {  // block (b, a) = block (a, b)^T
+            A[pb * m + pa] = z00;
+            if (qb_ok) A[qb * m + pa] = z01;
+            if (qa_ok) A[pb * m + qa] = z10;
+            if (qa_ok && qb_ok) A[qb * m + qa] = z11;
+        }
+    }
+    for (int e = tid; e < m * np; e += nth) {
+        const int i = e / np, b = e % np;
+        int pb, qb;
+        rr_pair(r, b, me, pb, qb);
+        if (qb >= m) continue;
+        const T cb = rc[b], sb = rs[b];
+        const T vp = V[i * m + pb], vq = V[i * m + qb];
+        V[i * m + pb] = cb * vp - sb * vq;
+        V[i * m + qb] = sb * vp + cb * vq;
+    }
+}
+
+// Sweeps until off-diagonal mass <= rel_tol * total mass. Returns 1 when converged, 2 when
+// max_sweeps sweeps ran without converging, 3 when A holds a non-finite value. Called by
+// every thread of the block; the return value is uniform. red holds 64 doubles.
+template <typename T>
+__device__ int jac_sweeps(T* A, T* V, int m, double rel_tol, int max_sweeps, double* red, int* stop_sh, T* rc,
+                          T* rs) {
+    const int me = m + (m & 1), np = me / 2;
+    const int tid = threadIdx.x, nth = blockDim.x;
     for (int sweep = 0;; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int i = tid; i < m * m; i += nth) {
-            const double v = A[i];
+            const double v = static_cast<double>(A[i]);
             tot += v * v;
             if (i / m != i % m) off += v * v;
         }
@@ -168,89 +245,60 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* Ag, double* Vg, do
         tot = warp_sum(tot);
         if ((tid & 31) == 0) {
             red[tid >> 5] = off;
+            red[32 + (tid >> 5)] = tot;
         }
         __syncthreads();
         if (tid == 0) {
-            double o = 0.0;
-            for (int i = 0; i < nth / 32; ++i) o += red[i];
-            red[31] = o;
-        }
-        __syncthreads();
-        const double off_all = red[31];
-        __syncthreads();
-        if ((tid & 31) == 0) red[tid >> 5] = tot;
-        __syncthreads();
-        if (tid == 0) {
-            double o = 0.0;
-            for (int i = 0; i < nth / 32; ++i) o += red[i];
-            stop = (off_all <= 1e-30 * o) || (off_all == 0.0);
-            if (!stop && sweep >= max_sweeps) {
-                atomicOr(status, DEV_ILLCOND);
-                stop = 1;
+            double o = 0.0, t = 0.0;
+            for (int i = 0; i < nth / 32; ++i) {
+                o += red[i];
+                t += red[32 + i];
             }
+            int st = 0;
+            if (!isfinite(t))
+                st = 3;
+            else if (o <= rel_tol * t || o == 0.0)
+                st = 1;
+            else if (sweep >= max_sweeps)
+                st = 2;
+            *stop_sh = st;
         }
         __syncthreads();
-        if (stop) break;
+        const int st = *stop_sh;
+        __syncthreads();  // red and stop_sh are rewritten by the next sweep
+        if (st) return st;
         for (int r = 0; r < me - 1; ++r) {
-            if (tid < np) {
-                int p, q;
-                rr_pair(r, tid, me, p, q);
-                double c = 1.0, sn = 0.0;
-                if (q < m) {
-                    const double apq = A[p * m + q];
-                    if (apq != 0.0) {
-                        const double app = A[p * m + p], aqq = A[q * m + q];
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        sn = t * c;
-                    }
-                }
-                rc[tid] = c;
-                rs[tid] = sn;
-            }
+            jac_params(A, m, me, np, r, rc, rs);
             __syncthreads();
-            // A <- J^T A J on every 2x2 block (pair a rows, pair b columns)
-            for (int e = tid; e < np * np; e += nth) {
-                const int a = e / np, b = e % np;
-                int pa, qa, pb, qb;
-                rr_pair(r, a, me, pa, qa);
-                rr_pair(r, b, me, pb, qb);
-                const double ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
-                const bool qa_ok = qa < m, qb_ok = qb < m;
-                const double x00 = A[pa * m + pb];
-                const double x01 = qb_ok ? A[pa * m + qb] : 0.0;
-                const double x10 = qa_ok ? A[qa * m + pb] : 0.0;
-                const double x11 = (qa_ok && qb_ok) ? A[qa * m + qb] : 0.0;
-                // rows: (p) c x_p - s x_q, (q) s x_p + c x_q
-                const double y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
-                const double y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
-                // columns: (p) c y_p - s y_q, (q) s y_p + c y_q
-                double z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
-                double z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
-                if (a == b) {  // the rotated pair's own block: its off-diagonal is zero by construction
-                    z01 = 0.0;
-                    z10 = 0.0;
-                }
-                A[pa * m + pb] = z00;
-                if (qb_ok) A[pa * m + qb] = z01;
-                if (qa_ok) A[qa * m + pb] = z10;
-                if (qa_ok && qb_ok) A[qa * m + qb] = z11;
-            }
-            // V <- V J
-            for (int e = tid; e < m * np; e += nth) {
-                const int i = e / np, b = e % np;
-                int pb, qb;
-                rr_pair(r, b, me, pb, qb);
-                if (qb >= m) continue;
-                const double cb = rc[b], sb = rs[b];
-                const double vp = V[i * m + pb], vq = V[i * m + qb];
-                V[i * m + pb] = cb * vp - sb * vq;
-                V[i * m + qb] = sb * vp + cb * vq;
-            }
+            jac_apply(A, V, m, me, np, r, rc, rs);
             __syncthreads();
         }
     }
+}
+
+// FP64 sweeps from (A, V = I): the solver for m > kJacMixedMax (and tiny m). Stops when the
+// off-diagonal mass is below (1e-15)^2 of the total, or after max_sweeps sweeps (then
+// DEV_ILLCOND is raised). A is read from its upper triangle.
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* Ag, double* Vg, double* lam, int m, int* status,
+                                                      int max_sweeps, int use_smem) {
+    extern __shared__ double jsm[];
+    __shared__ double rc[kMaxN / 2], rs[kMaxN / 2];
+    __shared__ double red[64];
+    __shared__ int stop;
+    double* A = use_smem ? jsm : Ag;
+    double* V = use_smem ? jsm + m * m : Vg;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < m * m; i += nth) {
+        const int r = i / m, c = i % m;
+        if (use_smem)
+            A[i] = r <= c ? Ag[i] : Ag[c * m + r];
+        else if (r > c)
+            A[i] = Ag[c * m + r];  // lower entries only written, upper only read
+        V[i] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int st = jac_sweeps<double>(A, V, m, 1e-30, max_sweeps, red, &stop, rc, rs);
+    if (st >= 2 && tid == 0) atomicOr(status, DEV_ILLCOND);
     for (int i = tid; i < m; i += nth) lam[i] = A[i * m + i];
     if (use_smem)
         for (int i = tid; i < m * m; i += nth) {
@@ -259,15 +307,117 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* Ag, double* Vg, do
         }
 }
 
+// Symmetric product C = X^T Y of m x m shared-memory matrices when X^T Y is known to be
+// symmetric (upper triangle computed, mirrored), or general C = X Y (sym = false, transA =
+// false). Called by every thread; ends with a barrier.
+__device__ __forceinline__ void jac_gemm(const double* X, const double* Y, double* C, int m, bool transA, bool sym) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int e = tid; e < m * m; e += nth) {
+        const int r = e / m, c = e % m;
+        if (sym && r > c) continue;
+        double acc = 0.0;
+        if (transA)
+            for (int k = 0; k < m; ++k) acc = fma(X[k * m + r], Y[k * m + c], acc);
+        else
+            for (int k = 0; k < m; ++k) acc = fma(X[r * m + k], Y[k * m + c], acc);
+        C[e] = acc;
+        if (sym && r != c) C[c * m + r] = acc;
+    }
+    __syncthreads();
+}
+
+// Mixed-precision solver for kJacMixedMin <= m <= kJacMixedMax (see above). Shared memory:
+// four m x m FP64 buffers P0..P3; the FP32 phase keeps its A and V in P2 and P3.
+__global__ void __launch_bounds__(1024) jacobi_mixed_kernel(double* Ag, double* Vg, double* lam, int m, int* status,
+                                                            int max_sweeps) {
+    extern __shared__ double jsm[];
+    __shared__ double rcd[kJacMixedMax / 2], rsd[kJacMixedMax / 2];
+    __shared__ float rcf[kJacMixedMax / 2], rsf[kJacMixedMax / 2];
+    __shared__ double red[64];
+    __shared__ int stop;
+    const int mm = m * m;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    double* P0 = jsm;  // A (FP64, kept)
+    double* P1 = jsm + mm;
+    double* P2 = jsm + 2 * mm;
+    double* P3 = jsm + 3 * mm;
+    float* A32 = reinterpret_cast<float*>(P2);
+    float* V32 = reinterpret_cast<float*>(P3);
+    double amax = 0.0;
+    for (int i = tid; i < mm; i += nth) {
+        const int r = i / m, c = i % m;
+        const double v = r <= c ? Ag[i] : Ag[c * m + r];
+        P0[i] = v;
+        amax = fmax(amax, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((tid & 31) == 0) red[tid >> 5] = amax;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int i = 0; i < nth / 32; ++i) a = fmax(a, red[i]);
+        red[40] = a;
+    }
+    __syncthreads();
+    amax = red[40];
+    // power-of-two scale (exact) so that the FP32 phase sees entries of order one
+    const double scale = (amax > 0.0 && isfinite(amax)) ? ldexp(1.0, -ilogb(amax)) : 1.0;
+    __syncthreads();
+    for (int i = tid; i < mm; i += nth) {
+        A32[i] = static_cast<float>(P0[i] * scale);
+        V32[i] = (i / m == i % m) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    int st = jac_sweeps<float>(A32, V32, m, 1e-11, 12, red, &stop, rcf, rsf);
+    if (st == 3) {  // non-finite input: report it, return A's diagonal and V = I
+        if (tid == 0) atomicOr(status, DEV_ILLCOND);
+        for (int i = tid; i < m; i += nth) lam[i] = P0[i * m + i];
+        for (int i = tid; i < mm; i += nth) Vg[i] = (i / m == i % m) ? 1.0 : 0.0;
+        return;
+    }
+    for (int i = tid; i < mm; i += nth) P1[i] = static_cast<double>(V32[i]);
+    __syncthreads();
+    // two Newton-Schulz steps toward the orthogonal polar factor of V
+    for (int it = 0; it < 2; ++it) {
+        jac_gemm(P1, P1, P2, m, true, true);  // S = V^T V
+        for (int e = tid; e < mm; e += nth) {  // V (3I - S) / 2
+            const int r = e / m, c = e % m;
+            double acc = 0.0;
+            for (int k = 0; k < m; ++k) acc = fma(P1[r * m + k], (k == c ? 3.0 : 0.0) - P2[k * m + c], acc);
+            P3[e] = 0.5 * acc;
+        }
+        __syncthreads();
+        double* t = P1;
+        P1 = P3;
+        P3 = t;
+    }
+    jac_gemm(P0, P1, P2, m, false, false);  // A V
+    jac_gemm(P1, P2, P3, m, true, true);    // A' = V^T A V
+    st = jac_sweeps<double>(P3, P1, m, 1e-30, max_sweeps, red, &stop, rcd, rsd);
+    if (st >= 2 && tid == 0) atomicOr(status, DEV_ILLCOND);
+    for (int i = tid; i < m; i += nth) lam[i] = P3[i * m + i];
+    for (int i = tid; i < mm; i += nth) {
+        Ag[i] = P3[i];
+        Vg[i] = P1[i];
+    }
+}
+
 cudaError_t launch_jacobi(cudaStream_t s, double* A, double* V, double* lam, int m, int* status, int max_sweeps) {
+    int threads = m * m / 2;
+    threads = threads < 128 ? 128 : (threads > 1024 ? 1024 : round_up(threads, 32));
+    if (m >= kJacMixedMin && m <= kJacMixedMax) {
+        const size_t smem = 4ull * m * m * sizeof(double);
+        cudaError_t e = allow_max_dyn_smem(jacobi_mixed_kernel);
+        if (e != cudaSuccess) return e;
+        jacobi_mixed_kernel<<<1, threads, smem, s>>>(A, V, lam, m, status, max_sweeps);
+        return cudaGetLastError();
+    }
     const size_t smem = 2ull * m * m * sizeof(double);
     const int use_smem = smem <= 160 * 1024;
     if (use_smem) {
         cudaError_t e = allow_max_dyn_smem(jacobi_kernel);
         if (e != cudaSuccess) return e;
     }
-    int threads = m * m / 2;
-    threads = threads < 128 ? 128 : (threads > 1024 ? 1024 : round_up(threads, 32));
     jacobi_kernel<<<1, threads, use_smem ? smem : 0, s>>>(A, V, lam, m, status, max_sweeps, use_smem);
     return cudaGetLastError();
 }
