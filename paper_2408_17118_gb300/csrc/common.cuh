@@ -40,6 +40,15 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
+// ------------------------------------------------------------------------- dependent launch
+// Programmatic dependent launch (griddepcontrol, sm_90+). pdl_wait blocks until the grid that
+// precedes this one in the stream has completed and its memory is visible (a no-op when the
+// grid was launched without the programmatic-serialization attribute); a kernel launched with
+// the attribute calls it before touching global memory. pdl_trigger lets the next grid in the
+// stream be scheduled once every CTA of this grid has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

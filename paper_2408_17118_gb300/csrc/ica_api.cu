@@ -808,7 +808,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
                                        n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
                                        o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
-                                       counts + (cur ^ 1), crows + 2 * i, done_ctr, fa.shape_dev));
+                                       counts + (cur ^ 1), crows + 2 * i, done_ctr, fa.shape_dev,
+                                       fa.shape_dev != nullptr));
                     return ICA_OK;
                 });
                 if (rc) return rc;

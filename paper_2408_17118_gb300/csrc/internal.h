@@ -43,7 +43,7 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr, const int* shape_dev = nullptr);
+                            unsigned int* done_ctr, const int* shape_dev = nullptr, bool pdl = false);
 cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                            int part_rows, int n_pad, int M, const float* B, double inv_T, float* Bnew,
                            float* moments);

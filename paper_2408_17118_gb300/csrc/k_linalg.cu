@@ -138,20 +138,62 @@ cudaError_t launch_covariance(cudaStream_t s, const float* X, const double* mean
 // memory, L2 resident).
 constexpr int kJacMixedMin = 12, kJacMixedMax = 80;
 
+// Pair a of round r in the circle ordering of me = m + (m odd) indices (p < q; q = m is the
+// dummy index of odd m). r, a < me - 1 and a <= (me - 1) / 2, so no modulo is needed.
 __device__ __forceinline__ void rr_pair(int r, int a, int me, int& p, int& q) {
     const int mm = me - 1;
     if (a == 0) {
         p = r;
         q = mm;
     } else {
-        p = (r + a) % mm;
-        q = (r - a + mm) % mm;
+        p = r + a;
+        if (p >= mm) p -= mm;
+        q = r - a;
+        if (q < 0) q += mm;
     }
     if (p > q) {
         const int t = p;
         p = q;
         q = t;
     }
+}
+
+// Jacobi rotation (c, s) zeroing a_pq (Golub & Van Loan, Algorithm 8.5.1): t is the root of
+// smaller magnitude of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq), c = (1+t^2)^-1/2.
+__device__ __forceinline__ void rot_params(float apq, float app, float aqq, float& c, float& s) {
+    const float tau = (aqq - app) / (2.f * apq);
+    const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+    c = 1.f / sqrtf(1.f + t * t);
+    s = t * c;
+}
+// FP64: the FP32 tangent, refined by two Newton steps on f(t) = a_pq t^2 + (a_qq - a_pp) t - a_pq
+// (same roots) with an FP32 reciprocal of f'(t) (each step multiplies the relative error by
+// about 1e-7), then c by two Newton steps for (1 + t^2)^-1/2 from an FP32 start. Only FP64
+// multiply-adds: FP64 division and square root would run on the block's one parameter warp at
+// the low FP64 rate of this GPU. Requires entries of order one (the callers scale A).
+__device__ __forceinline__ void rot_params(double apq, double app, double aqq, double& c, double& s) {
+    const double d = aqq - app;
+    const float a32 = static_cast<float>(apq);
+    if (a32 == 0.f) {  // |a_pq| < 1e-45 against entries of order one: below rounding
+        c = 1.0;
+        s = 0.0;
+        return;
+    }
+    float c32, s32;
+    rot_params(a32, static_cast<float>(app), static_cast<float>(aqq), c32, s32);
+    double t = static_cast<double>(s32 / c32);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double f = fma(fma(apq, t, d), t, -apq);
+        const double r = static_cast<double>(1.f / static_cast<float>(fma(2.0 * apq, t, d)));
+        t = fma(-f, r, t);
+    }
+    const double u = fma(t, t, 1.0);
+    double y = static_cast<double>(rsqrtf(static_cast<float>(u)));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) y = y * fma(-0.5 * u, y * y, 1.5);
+    c = y;
+    s = t * y;
 }
 
 // Rotation (c, s) that zeroes A[p][q] for each pair of round r (one thread per pair).
@@ -164,65 +206,87 @@ __device__ __forceinline__ void jac_params(const T* A, int m, int me, int np, in
         T c = T(1), sn = T(0);
         if (q < m) {
             const T apq = A[p * m + q];
-            if (apq != T(0)) {
-                const T app = A[p * m + p], aqq = A[q * m + q];
-                const T tau = (aqq - app) / (T(2) * apq);
-                const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-                c = T(1) / sqrt(T(1) + t * t);
-                sn = t * c;
-            }
+            if (apq != T(0)) rot_params(apq, A[p * m + p], A[q * m + q], c, sn);
         }
         rc[tid] = c;
         rs[tid] = sn;
     }
 }
 
+// Per-thread walk over the np x np block indices e = tid, tid + nth, ... as (e / np, e % np),
+// advanced without division.
+struct BlockWalk {
+    int a0, b0, da, db;
+    __device__ __forceinline__ BlockWalk(int np) {
+        a0 = static_cast<int>(threadIdx.x) / np;
+        b0 = static_cast<int>(threadIdx.x) % np;
+        da = static_cast<int>(blockDim.x) / np;
+        db = static_cast<int>(blockDim.x) % np;
+    }
+};
+
 // A <- J^T A J (upper blocks, mirrored) and V <- V J for the rotations of round r.
 template <typename T>
-__device__ __forceinline__ void jac_apply(T* A, T* V, int m, int me, int np, int r, const T* rc, const T* rs) {
+__device__ __forceinline__ void jac_apply(T* A, T* V, int m, int me, int np, int r, const T* rc, const T* rs,
+                                          const BlockWalk& w) {
     const int tid = threadIdx.x, nth = blockDim.x;
+    int a = w.a0, b = w.b0;
     for (int e = tid; e < np * np; e += nth) {
-        const int a = e / np, b = e % np;
-        if (a > b) continue;
-        int pa, qa, pb, qb;
-        rr_pair(r, a, me, pa, qa);
-        rr_pair(r, b, me, pb, qb);
-        const T ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
-        const bool qa_ok = qa < m, qb_ok = qb < m;
-        const T x00 = A[pa * m + pb];
-        const T x01 = qb_ok ? A[pa * m + qb] : T(0);
-        const T x10 = qa_ok ? A[qa * m + pb] : T(0);
-        const T x11 = (qa_ok && qb_ok) ? A[qa * m + qb] : T(0);
-        // rows: (p) c x_p - s x_q, (q) s x_p + c x_q
-        const T y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
-        const T y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
-        // columns: (p) c y_p - s y_q, (q) s y_p + c y_q
-        T z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
-        T z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
-        if (a == b) {  // the rotated pair's own block: its off-diagonal is zero by construction
-            z01 = T(0);
-            z10 = T(0);
+        if (a <= b) {
+            int pa, qa, pb, qb;
+            rr_pair(r, a, me, pa, qa);
+            rr_pair(r, b, me, pb, qb);
+            const T ca = rc[a], sa = rs[a], cb = rc[b], sb = rs[b];
+            const bool qa_ok = qa < m, qb_ok = qb < m;
+            const T x00 = A[pa * m + pb];
+            const T x01 = qb_ok ? A[pa * m + qb] : T(0);
+            const T x10 = qa_ok ? A[qa * m + pb] : T(0);
+            const T x11 = (qa_ok && qb_ok) ? A[qa * m + qb] : T(0);
+            // rows: (p) c x_p - s x_q, (q) s x_p + c x_q
+            const T y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+            const T y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+            // columns: (p) c y_p - s y_q, (q) s y_p + c y_q
+            T z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
+            T z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
+            if (a == b) {  // the rotated pair's own block: its off-diagonal is zero by construction
+                z01 = T(0);
+                z10 = T(0);
+            }
+            A[pa * m + pb] = z00;
+            if (qb_ok) A[pa * m + qb] = z01;
+            if (qa_ok) A[qa * m + pb] = z10;
+            if (qa_ok && qb_ok) A[qa * m + qb] = z11;
+            if (a != b) {  // block (b, a) = block (a, b)^T
+                A[pb * m + pa] = z00;
+                if (qb_ok) A[qb * m + pa] = z01;
+                if (qa_ok) A[pb * m + qa] = z10;
+                if (qa_ok && qb_ok) A[qb * m + qa] = z11;
+            }
         }
-        A[pa * m + pb] = z00;
-        if (qb_ok) A[pa * m + qb] = z01;
-        if (qa_ok) A[qa * m + pb] = z10;
-        if (qa_ok && qb_ok) A[qa * m + qb] = z11;
-        if (a != b) {  // block (b, a) = block (a, b)^T
-            A[pb * m + pa] = z00;
-            if (qb_ok) A[qb * m + pa] = z01;
-            if (qa_ok) A[pb * m + qa] = z10;
-            if (qa_ok && qb_ok) A[qb * m + qa] = z11;
+        a += w.da;
+        b += w.db;
+        if (b >= np) {
+            b -= np;
+            ++a;
         }
     }
+    int i = w.a0;
+    b = w.b0;
     for (int e = tid; e < m * np; e += nth) {
-        const int i = e / np, b = e % np;
         int pb, qb;
         rr_pair(r, b, me, pb, qb);
-        if (qb >= m) continue;
-        const T cb = rc[b], sb = rs[b];
-        const T vp = V[i * m + pb], vq = V[i * m + qb];
-        V[i * m + pb] = cb * vp - sb * vq;
-        V[i * m + qb] = sb * vp + cb * vq;
+        if (qb < m) {
+            const T cb = rc[b], sb = rs[b];
+            const T vp = V[i * m + pb], vq = V[i * m + qb];
+            V[i * m + pb] = cb * vp - sb * vq;
+            V[i * m + qb] = sb * vp + cb * vq;
+        }
+        i += w.da;
+        b += w.db;
+        if (b >= np) {
+            b -= np;
+            ++i;
+        }
     }
 }
 
@@ -234,6 +298,7 @@ __device__ int jac_sweeps(T* A, T* V, int m, double rel_tol, int max_sweeps, dou
                           T* rs) {
     const int me = m + (m & 1), np = me / 2;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const BlockWalk walk(np);
     for (int sweep = 0;; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int i = tid; i < m * m; i += nth) {
@@ -270,10 +335,33 @@ __device__ int jac_sweeps(T* A, T* V, int m, double rel_tol, int max_sweeps, dou
         for (int r = 0; r < me - 1; ++r) {
             jac_params(A, m, me, np, r, rc, rs);
             __syncthreads();
-            jac_apply(A, V, m, me, np, r, rc, rs);
+            jac_apply(A, V, m, me, np, r, rc, rs, walk);
             __syncthreads();
         }
     }
+}
+
+// Exact power-of-two scale 2^-floor(log2 max|A_ij|) that brings the largest entry into [1, 2)
+// (1 for a zero matrix); the rotation parameters assume entries of order one. Called by every
+// thread; red holds 64 doubles.
+__device__ double jac_scale(const double* Ag, int mm, double* red) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    double amax = 0.0;
+    for (int i = tid; i < mm; i += nth) amax = fmax(amax, fabs(Ag[i]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((tid & 31) == 0) red[tid >> 5] = amax;
+    __syncthreads();
+    if (tid == 0) {
+        double x = 0.0;
+        for (int i = 0; i < nth / 32; ++i) x = fmax(x, red[i]);
+        red[40] = x;
+    }
+    __syncthreads();
+    amax = red[40];
+    __syncthreads();
+    if (!(amax > 0.0) || !isfinite(amax)) return 1.0;
+    const int e = ilogb(amax);
+    return ldexp(1.0, -(e < -1000 ? -1000 : (e > 1000 ? 1000 : e)));
 }
 
 // FP64 sweeps from (A, V = I): the solver for m > kJacMixedMax (and tiny m). Stops when the
@@ -288,23 +376,26 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* Ag, double* Vg, do
     double* A = use_smem ? jsm : Ag;
     double* V = use_smem ? jsm + m * m : Vg;
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < m * m; i += nth) {
+    const double scale = jac_scale(Ag, m * m, red), unscale = 1.0 / scale;  // powers of two: exact
+    for (int i = tid; i < m * m; i += nth) {  // upper triangle scaled (each entry by its own thread)
         const int r = i / m, c = i % m;
-        if (use_smem)
-            A[i] = r <= c ? Ag[i] : Ag[c * m + r];
-        else if (r > c)
-            A[i] = Ag[c * m + r];  // lower entries only written, upper only read
+        if (r <= c) A[i] = Ag[i] * scale;
         V[i] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int i = tid; i < m * m; i += nth) {  // mirrored into the lower triangle
+        const int r = i / m, c = i % m;
+        if (r > c) A[i] = A[c * m + r];
     }
     __syncthreads();
     const int st = jac_sweeps<double>(A, V, m, 1e-30, max_sweeps, red, &stop, rc, rs);
     if (st >= 2 && tid == 0) atomicOr(status, DEV_ILLCOND);
-    for (int i = tid; i < m; i += nth) lam[i] = A[i * m + i];
-    if (use_smem)
-        for (int i = tid; i < m * m; i += nth) {
-            Ag[i] = A[i];
-            Vg[i] = V[i];
-        }
+    for (int i = tid; i < m; i += nth) lam[i] = A[i * m + i] * unscale;
+    __syncthreads();  // A may be Ag itself: unscale in place only after the diagonal was read
+    for (int i = tid; i < m * m; i += nth) {
+        Ag[i] = A[i] * unscale;
+        if (use_smem) Vg[i] = V[i];
+    }
 }
 
 // Symmetric product C = X^T Y of m x m shared-memory matrices when X^T Y is known to be
@@ -343,35 +434,19 @@ __global__ void __launch_bounds__(1024) jacobi_mixed_kernel(double* Ag, double* 
     double* P3 = jsm + 3 * mm;
     float* A32 = reinterpret_cast<float*>(P2);
     float* V32 = reinterpret_cast<float*>(P3);
-    double amax = 0.0;
+    const double scale = jac_scale(Ag, mm, red), unscale = 1.0 / scale;  // powers of two: exact
     for (int i = tid; i < mm; i += nth) {
         const int r = i / m, c = i % m;
-        const double v = r <= c ? Ag[i] : Ag[c * m + r];
+        const double v = (r <= c ? Ag[i] : Ag[c * m + r]) * scale;
         P0[i] = v;
-        amax = fmax(amax, fabs(v));
-    }
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((tid & 31) == 0) red[tid >> 5] = amax;
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0;
-        for (int i = 0; i < nth / 32; ++i) a = fmax(a, red[i]);
-        red[40] = a;
-    }
-    __syncthreads();
-    amax = red[40];
-    // power-of-two scale (exact) so that the FP32 phase sees entries of order one
-    const double scale = (amax > 0.0 && isfinite(amax)) ? ldexp(1.0, -ilogb(amax)) : 1.0;
-    __syncthreads();
-    for (int i = tid; i < mm; i += nth) {
-        A32[i] = static_cast<float>(P0[i] * scale);
-        V32[i] = (i / m == i % m) ? 1.f : 0.f;
+        A32[i] = static_cast<float>(v);
+        V32[i] = (r == c) ? 1.f : 0.f;
     }
     __syncthreads();
     int st = jac_sweeps<float>(A32, V32, m, 1e-11, 12, red, &stop, rcf, rsf);
     if (st == 3) {  // non-finite input: report it, return A's diagonal and V = I
         if (tid == 0) atomicOr(status, DEV_ILLCOND);
-        for (int i = tid; i < m; i += nth) lam[i] = P0[i * m + i];
+        for (int i = tid; i < m; i += nth) lam[i] = P0[i * m + i] * unscale;
         for (int i = tid; i < mm; i += nth) Vg[i] = (i / m == i % m) ? 1.0 : 0.0;
         return;
     }
@@ -395,9 +470,9 @@ __global__ void __launch_bounds__(1024) jacobi_mixed_kernel(double* Ag, double* 
     jac_gemm(P1, P2, P3, m, true, true);    // A' = V^T A V
     st = jac_sweeps<double>(P3, P1, m, 1e-30, max_sweeps, red, &stop, rcd, rsd);
     if (st >= 2 && tid == 0) atomicOr(status, DEV_ILLCOND);
-    for (int i = tid; i < m; i += nth) lam[i] = P3[i * m + i];
+    for (int i = tid; i < m; i += nth) lam[i] = P3[i * m + i] * unscale;
     for (int i = tid; i < mm; i += nth) {
-        Ag[i] = P3[i];
+        Ag[i] = P3[i] * unscale;
         Vg[i] = P1[i];
     }
 }

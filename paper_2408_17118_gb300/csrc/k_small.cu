@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
                                                            long long* rows_accum, unsigned int* done_ctr,
                                                            const int* __restrict__ shape_dev) {
     extern __shared__ float fin_red[];  // [NW][n_pad] sums, [NW][n_pad] compensations, [NW][4] moments
+    pdl_wait();  // the update grid wrote the partials and the shape
+    pdl_trigger();
     if (shape_dev) {  // split count and partial-row stride chosen on the device by the fused launch
         splits = shape_dev[0];
         part_rows = shape_dev[1];
@@ -202,22 +204,30 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr, const int* shape_dev) {
+                            unsigned int* done_ctr, const int* shape_dev, bool pdl) {
     const float fT = static_cast<float>(inv_T), ftol = static_cast<float>(tol);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(M_act, 1, 1);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
     if (M_act <= 64 && splits > 16) {
-        const size_t smem = sizeof(float) * 32 * (2 * n_pad + 4);
         cudaError_t e = allow_max_dyn_smem(finalize_kernel<32>);
         if (e != cudaSuccess) return e;
-        finalize_kernel<32><<<M_act, 1024, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
-                                                      count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
-                                                      t_iter, status, act_out, count_out, rows_accum, done_ctr, shape_dev);
-    } else {
-        const size_t smem = sizeof(float) * 4 * (2 * n_pad + 4);
-        finalize_kernel<4><<<M_act, 128, smem, s>>>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
-                                                    count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj,
-                                                    t_iter, status, act_out, count_out, rows_accum, done_ctr, shape_dev);
+        cfg.blockDim = dim3(1024, 1, 1);
+        cfg.dynamicSmemBytes = sizeof(float) * 32 * (2 * n_pad + 4);
+        return cudaLaunchKernelEx(&cfg, finalize_kernel<32>, part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
+                                  count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj, t_iter, status, act_out,
+                                  count_out, rows_accum, done_ctr, shape_dev);
     }
-    return cudaGetLastError();
+    cfg.blockDim = dim3(128, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(float) * 4 * (2 * n_pad + 4);
+    return cudaLaunchKernelEx(&cfg, finalize_kernel<4>, part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
+                              count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj, t_iter, status, act_out,
+                              count_out, rows_accum, done_ctr, shape_dev);
 }
 
 // Un-normalised update (step entry point): Bnew = acc / T - 3 B and moments / T.

@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* mom_sm = reinterpret_cast<float*>(bars + kBars + 2);  // [3][128][4]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_wait();  // the previous grid (finalize of the last update) wrote B, the list and the count
+    pdl_trigger();
     const int M_act = count_dev ? *count_dev : M_act_host;
     int split = blockIdx.x, tile = blockIdx.y, cps = chunks_per_split;
     if (shape_ctas > 0) {
@@ -480,11 +482,21 @@ static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const
     const int tiles_ub = (M_act + kTcRows - 1) / kTcRows;
     const dim3 grid = shape_ctas > 0 ? dim3(tiles_ub > shape_ctas ? tiles_ub : shape_ctas, 1)
                                      : dim3(splits, tiles_ub);
-    fused_tc_kernel<TC, NB, KT, MO, MOM><<<grid, kThreads, L.total, s>>>(
-        xmap, KT ? *xmap_t : xmap, B32, ldb, act_idx, count_dev, M_act, n_pad, T, chunks_per_split, total_chunks,
-        static_cast<int>(L.stages), L.a_bytes, L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p, L.off_bar, part_acc,
-        part_mom, part_rows, status, shape_ctas, shape_out);
-    return cudaGetLastError();
+    // device-shaped launches (the fit's update loop) overlap their launch with the previous grid
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = shape_ctas > 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fused_tc_kernel<TC, NB, KT, MO, MOM>, xmap, KT ? *xmap_t : xmap, B32, ldb,
+                              act_idx, count_dev, M_act, n_pad, T, chunks_per_split, total_chunks,
+                              static_cast<int>(L.stages), L.a_bytes, L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p,
+                              L.off_bar, part_acc, part_mom, part_rows, status, shape_ctas, shape_out);
 }
 
 cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
