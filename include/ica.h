@@ -89,6 +89,13 @@ typedef struct {
     float* record_labels;  /* optional (device, with record_features): n_components x M labels,
                               1 when the restart ended at the picked direction
                               (|b_r . b_p| >= 1 - 1e-3), else 0 */
+    int stage_persistent;  /* BF16: 1 (default) runs each component's BF16 iterations as one
+                              persistent cooperative launch (one CTA per SM, grid barriers
+                              between the update, the row completion and the removal of
+                              converged rows) when the fit has the GPU to itself (not inside a
+                              multi-worker ica_order_fit_batched) and M <= 152 * 128; 0 launches
+                              the update and the row completion per iteration. Both give the
+                              same results. */
 } ica_opts;
 
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,

@@ -38,6 +38,7 @@ class ica_opts(C.Structure):
         ("prune_tau", C.c_float),
         ("record_features", C.c_void_p),
         ("record_labels", C.c_void_p),
+        ("stage_persistent", C.c_int),
     ]
 
 

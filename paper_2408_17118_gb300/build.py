@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libica.so")
 
 SOURCES = ["ica_api.cu", "k_small.cu", "k_linalg.cu", "k_reduce.cu", "k_fp32.cu", "k_tc.cu", "k_plain.cu",
-           "k_mlp.cu", "noalloc.cu"]
+           "k_mlp.cu", "k_stage.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]

@@ -62,6 +62,11 @@ struct ica_ctx {
     // share of the GPU (CTAs per launch, as a fraction of one wave) that fused launches aim
     // for: 1 when the fit owns the GPU, smaller when several fits run concurrently
     int cta_div = 1;
+    // the BF16 stage may run as one persistent cooperative launch per component (k_stage.cu):
+    // only when this context's fits do not share the GPU with other fits, and until such a
+    // launch was refused for lack of resident CTAs
+    bool persist_ok = true;
+    std::string persist_note;  // why the persistent stage was not used, when it was refused
     // concurrent fits of ica_order_fit_batched: worker contexts with their own streams, and the
     // autotuned CTA share per (workers, shape) key
     std::vector<ica_ctx*> workers;
@@ -125,7 +130,7 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     };
     const size_t nN = static_cast<size_t>(N) * N;
     L.status = take(16 * sizeof(int));
-    L.counts = take(16 * sizeof(int));
+    L.counts = take(32 * sizeof(int));
     L.Xt32 = take(sizeof(float) * L.n_pad_max * static_cast<size_t>(L.ldx));
     L.Xt16 = take(precision == ICA_BF16 ? sizeof(uint16_t) * L.n_pad_max * static_cast<size_t>(L.ldx) : 0);
     L.tcols = round_up64cols(L.n_pad_max < 128 ? L.n_pad_max : 128);
@@ -451,6 +456,7 @@ void ica_default_opts(ica_opts* o) {
     o->prune_tau = 0.05f;
     o->record_features = nullptr;
     o->record_labels = nullptr;
+    o->stage_persistent = 1;
 }
 
 const char* ica_status_string(int st) {
@@ -674,6 +680,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     int* status = at<int>(c, L.status);
     int* counts = at<int>(c, L.counts);  // [0], [1]: active counts (double-buffered); [2]: candidates
     unsigned int* done_ctr = reinterpret_cast<unsigned int*>(counts + 8);  // finalize's block counter
+    unsigned int* stage_bar = reinterpret_cast<unsigned int*>(counts + 16);  // persistent stage's grid barrier
+    int* stage_ctl = counts + 20;  // persistent stage's {iteration reached, active count, list index}
     float* B32 = at<float>(c, L.B32);
     float* Xt32 = at<float>(c, L.Xt32);
     uint16_t* Xt16 = at<uint16_t>(c, L.Xt16);
@@ -746,6 +754,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     int* pruned = at<int>(c, L.pruned);
     float* uref = reinterpret_cast<float*>(counts + 12);  // pruner feature reference (one float)
     std::vector<std::vector<int>> comp_hist;
+    long long persist_launches = 0;  // persistent BF16 stage launches of this fit
     int found = 0;
     for (int i = 0; i < n_components; ++i) {
         const int n = N - i;
@@ -764,6 +773,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         // look at least as good as the kept ones (prune_check), the component is fitted again
         // without pruning from the same initial restarts (attempt 1).
         int t = 0, rt = 0, n_pruned = 0, fell_back = 0;
+        long long stage_rows_seen = 0;  // last value read of this component's stage row counter
         std::vector<int> hist;
         bool pruned_now = false, dropped_all = false;
         FusedArgs fa;
@@ -795,30 +805,107 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             int cur = 0, M_host = M;
             t = 0;
             fa.shape_dev = bf16 ? counts + 14 : nullptr;  // {splits, part_rows} of each BF16 update
+            // The BF16 stage runs as one persistent cooperative launch per segment of iterations
+            // (k_stage.cu; same arithmetic as the per-launch path below) when the fit owns the GPU.
+            bool persist = bf16 && o.stage_persistent && o.max_splits == 0 && c->persist_ok && c->cta_div == 1 &&
+                           !want_t && M <= 152 * kTcRows;
             while (t < iters && M_host > 0) {
-                StepShape sh;
-                fa.act = act[cur];
-                fa.count_dev = counts + cur;
-                fa.M_act = M_host;
-                fa.moments_only = false;
-                fa.moments = t < kTrajLen;
-                rc = timed(K_ITER, 4.0 * n * M_host * dT, [&] { return run_fused(c, L, fa, &sh); });
-                if (rc) return rc;
-                rc = timed(K_FINALIZE, 0.0, [&] {
-                    KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
-                                       n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
-                                       o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
-                                       counts + (cur ^ 1), crows + 2 * i, done_ctr, fa.shape_dev,
-                                       fa.shape_dev != nullptr));
-                    return ICA_OK;
-                });
-                if (rc) return rc;
-                cur ^= 1;
-                ++t;
-                if (fa.shape_dev ? sync_due_shaped(t) : sync_due(t)) {
-                    rc = read_count(counts + cur, &M_host);
+                if (persist) {
+                    const int t_end = (prune_this && t < kTrajLen) ? std::min(iters, kTrajLen) : iters;
+                    CUtensorMap map;
+                    rc = encode_xmap(c, &map, Xt16, n_pad, T, ldx);
                     if (rc) return rc;
+                    StageLaunch sl{};
+                    sl.B32 = B32;
+                    sl.ldb = n_pad;
+                    sl.act0 = act[0];
+                    sl.act1 = act[1];
+                    sl.count0 = counts + 0;
+                    sl.count1 = counts + 1;
+                    sl.cur0 = cur;
+                    sl.n_pad = n_pad;
+                    sl.n = n;
+                    sl.T = T;
+                    sl.ctas = 152;
+                    sl.part_acc = at<float>(c, L.part_acc);
+                    sl.part_mom = at<float>(c, L.part_mom);
+                    sl.flags = flags;
+                    sl.iters = itc;
+                    sl.traj = traj;
+                    sl.status = status;
+                    sl.rows_accum = crows + 2 * i;
+                    sl.bar_ctr = stage_bar;
+                    sl.ctl = stage_ctl;
+                    sl.t_begin = t;
+                    sl.t_end = t_end;
+                    sl.inv_T = inv_T;
+                    sl.tol = tol_iter;
+                    CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
+                    cudaError_t le = cudaSuccess;
+                    int resident = 0;
+                    const size_t rec0 = c->recs.size();
+                    rc = timed(K_ITER, 0.0, [&] {
+                        le = launch_stage_tc(s, map, sl, &resident);
+                        return ICA_OK;
+                    });
+                    if (rc) return rc;
+                    if (le == cudaErrorCooperativeLaunchTooLarge) {  // not all CTAs can be resident
+                        cudaGetLastError();
+                        c->persist_ok = false;
+                        c->persist_note = "cooperative launch too large: " + std::to_string(resident) +
+                                          " resident CTAs at n_pad " + std::to_string(n_pad);
+                        persist = false;
+                        if (c->recs.size() > rec0) c->recs.pop_back();
+                        continue;
+                    }
+                    if (le != cudaSuccess) {
+                        note_cuda_error(le, "launch_stage_tc", __LINE__);
+                        return ICA_ERR_CUDA;
+                    }
+                    ++c->launches;
+                    ++c->launches_total;
+                    ++persist_launches;
+                    long long* rows_h = reinterpret_cast<long long*>(c->host_i + 100);
+                    CK(cudaMemcpyAsync(c->host_i + 96, stage_ctl, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+                    CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+                    CK(cudaMemcpyAsync(rows_h, crows + 2 * i, sizeof(long long), cudaMemcpyDeviceToHost, s));
+                    const long long rows_before = stage_rows_seen;
+                    CK(cudaStreamSynchronize(s));
+                    rc = map_device_status(c->host_i[1]);
+                    if (rc) return rc;
+                    t = c->host_i[96];
+                    M_host = c->host_i[97];
+                    cur = c->host_i[98];
+                    stage_rows_seen = *rows_h;
+                    if (c->recs.size() > rec0)  // exact FLOPs of the segment: rows updated x 4 n T
+                        c->recs.back().flops = 4.0 * n * static_cast<double>(*rows_h - rows_before) * dT;
                     hist.push_back(M_host);
+                }
+                if (!persist) {
+                    StepShape sh;
+                    fa.act = act[cur];
+                    fa.count_dev = counts + cur;
+                    fa.M_act = M_host;
+                    fa.moments_only = false;
+                    fa.moments = t < kTrajLen;
+                    rc = timed(K_ITER, 4.0 * n * M_host * dT, [&] { return run_fused(c, L, fa, &sh); });
+                    if (rc) return rc;
+                    rc = timed(K_FINALIZE, 0.0, [&] {
+                        KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
+                                           n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
+                                           o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
+                                           counts + (cur ^ 1), crows + 2 * i, done_ctr, fa.shape_dev,
+                                           fa.shape_dev != nullptr, fa.shape_dev ? 152 / c->cta_div : 0));
+                        return ICA_OK;
+                    });
+                    if (rc) return rc;
+                    cur ^= 1;
+                    ++t;
+                    if (fa.shape_dev ? sync_due_shaped(t) : sync_due(t)) {
+                        rc = read_count(counts + cur, &M_host);
+                        if (rc) return rc;
+                        hist.push_back(M_host);
+                    }
                 }
                 if (prune_this && t == kTrajLen && t < iters) {
                     // learned pruner on the first kTrajLen iterations' trajectories
@@ -996,6 +1083,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     json_kv(js, "fit_ms", fit_ms);
     json_kv(js, "launches", static_cast<double>(c->launches));
     json_kv(js, "launches_total", static_cast<double>(c->launches_total));
+    json_kv(js, "stage_persistent_launches", static_cast<double>(persist_launches));
+    js += "\"stage_persistent_note\": \"" + c->persist_note + "\", ";
     js += "\"fused\": {";
     for (int k = 0; k < 4; ++k) {
         char buf[200];
@@ -1233,6 +1322,7 @@ int ica_order_fit_batched(ica_ctx* c, const ica_dataset* sets, int count, int M,
     CK(cudaEventRecord(start, c->stream));
     for (int w = 0; w < nw; ++w) {
         c->workers[w]->cta_div = nw == 1 ? 1 : div;
+        if (nw > 1) c->workers[w]->persist_ok = false;
         if (cudaStreamWaitEvent(c->workers[w]->stream, start, 0) != cudaSuccess) {
             cudaEventDestroy(start);
             return ICA_ERR_CUDA;

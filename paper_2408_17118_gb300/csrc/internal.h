@@ -43,7 +43,17 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr, const int* shape_dev = nullptr, bool pdl = false);
+                            unsigned int* done_ctr, const int* shape_dev = nullptr, bool pdl = false,
+                            int vw_ctas = 0);
+// Order of the compensated sums over split partials in the BF16 stage's row completion: the
+// number of virtual warps V per row (split s goes to virtual warp s mod V; the V sums are added
+// in order). More virtual warps when few rows share the GPU, so that the persistent stage kernel
+// finishes every row in one round of its CTAs' 16 warps (ctas = CTAs of the update). The
+// per-launch finalize follows the same order when given vw_ctas, so both paths agree bit for bit.
+constexpr int kFinMaxVWarps = 16;
+__host__ __device__ inline int fin_vwarps(int M_act, int ctas) {
+    return M_act <= ctas ? 16 : (M_act <= 4 * ctas ? 4 : 2);
+}
 cudaError_t launch_combine(cudaStream_t s, const float* part_acc, const float* part_mom, int splits,
                            int part_rows, int n_pad, int M, const float* B, double inv_T, float* Bnew,
                            float* moments);
@@ -137,6 +147,7 @@ __host__ __device__ inline void tc_device_shape(int M_act, int ctas, int total_c
 }
 // ---- k_tc.cu ----
 int tc_chunk(int n_pad);
+int tc_buffers(int n_pad);
 bool tc_transposed(int n_pad);
 size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out);
 // xmap: X~ (n_pad x T, samples contiguous), box {64, n_pad}. xmap_t (optional, n_pad <= 128):
@@ -149,6 +160,35 @@ cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, con
                             const CUtensorMap* xmap_t, const float* B32, int ldb, const int* act_idx,
                             const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
                             int total_chunks, float* part_acc, float* part_mom, int part_rows, int* status);
+
+// ---- k_stage.cu ----
+// Persistent BF16 stage: iterations [t_begin, t_end) of the update loop of one component in one
+// cooperative launch of `ctas` CTAs (one per SM). The active list act_{cur0} / count_{cur0} is
+// the input; ctl receives {iteration index reached, final active count, final list index}, and
+// the final count is also stored in count_{ctl[2]}. bar_ctr must be zero. Returns
+// cudaErrorCooperativeLaunchTooLarge, launching nothing, when the CTAs cannot all be resident.
+struct StageLaunch {
+    float* B32;
+    int ldb;
+    int *act0, *act1, *count0, *count1;
+    int cur0;
+    int n_pad, n;
+    int64_t T;
+    int ctas;
+    float* part_acc;
+    float* part_mom;
+    int* flags;
+    int* iters;
+    float* traj;
+    int* status;
+    long long* rows_accum;
+    unsigned int* bar_ctr;
+    int* ctl;
+    int t_begin, t_end;
+    double inv_T, tol;
+};
+// resident (optional) receives the number of CTAs of the kernel that fit the GPU at once.
+cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident = nullptr);
 
 // ---- k_plain.cu ----
 cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx,

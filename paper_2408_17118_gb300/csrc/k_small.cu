@@ -95,74 +95,24 @@ __device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc,
                                              const int* __restrict__ act_idx, int j, float* __restrict__ B32,
                                              int ldb, float inv_T, float tol, int* __restrict__ flags,
                                              int* __restrict__ iters, float* __restrict__ traj, int t_iter,
-                                             int* status, float* red_s, float* red_c, float* redm) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                                             int* status, int V, float* red) {
+    const int w = threadIdx.x >> 5;
     const bool want_traj = traj && t_iter < kTrajLen;
-    const int nq = (n_pad + 31) >> 5;  // columns per lane
-    {
-
-        CompSum acc[8];
-        CompSum m2, m4;
-#pragma unroll 4
-        for (int sp = w; sp < splits; sp += NW) {
-            const float* p = part_acc + (static_cast<int64_t>(sp) * part_rows + j) * n_pad;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q >= nq) break;
-                const int k = lane + 32 * q;
-                if (k < n_pad) acc[q].add(p[k]);
-            }
-            if (want_traj && lane == 0) {
-                m2.add(part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 0]);
-                m4.add(part_mom[(static_cast<int64_t>(sp) * part_rows + j) * 4 + 1]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q >= nq) break;
-            const int k = lane + 32 * q;
-            if (k < n_pad) {
-                red_s[w * n_pad + k] = acc[q].s;
-                red_c[w * n_pad + k] = acc[q].c;
-            }
-        }
-        if (lane == 0) {
-            redm[4 * w + 0] = m2.s;
-            redm[4 * w + 1] = m2.c;
-            redm[4 * w + 2] = m4.s;
-            redm[4 * w + 3] = m4.c;
-        }
+    const int nq = (n_pad + 31) >> 5;
+    int r = 0;
+    float b[8];
+    if (w == 0) {  // the restart row, loaded while the split sums run
+        r = act_idx ? __ldcg(act_idx + j) : j;
+        load_row(B32, ldb, r, nq, n, b);
     }
+    row_partials(part_acc, part_mom, splits, part_rows, n_pad, j, want_traj, V, NW, w, red);
     __syncthreads();
     if (w != 0) return;
-    float accv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int k = lane + 32 * q;
-        accv[q] = 0.f;
-        if (q < nq && k < n) {
-            CompSum acc;
-            float cs = 0.f;
-            for (int ww = 0; ww < NW; ++ww) {
-                acc.add(red_s[ww * n_pad + k]);
-                cs += red_c[ww * n_pad + k];
-            }
-            accv[q] = acc.value() + cs;
-        }
-    }
-    CompSum m2, m4;
-    if (want_traj)
-        for (int ww = 0; ww < NW; ++ww) {
-            m2.add(redm[4 * ww + 0]);
-            m2.add(redm[4 * ww + 1]);
-            m4.add(redm[4 * ww + 2]);
-            m4.add(redm[4 * ww + 3]);
-        }
-    finish_row(accv, nq, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters, traj, t_iter, want_traj, m2.value(),
-               m4.value(), status);
+    float accv[8], e2, e4;
+    row_combine(red, V, n_pad, n, want_traj, accv, &e2, &e4);
+    finish_row_loaded(accv, b, nq, n, r, j, B32, ldb, inv_T, tol, flags, iters, traj, t_iter, want_traj, e2, e4,
+                      status);
 }
-
-
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
                                                            const float* __restrict__ part_mom, int splits,
@@ -174,26 +124,25 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
                                                            float* __restrict__ traj, int t_iter, int* status,
                                                            int* __restrict__ act_out, int* count_out,
                                                            long long* rows_accum, unsigned int* done_ctr,
-                                                           const int* __restrict__ shape_dev) {
-    extern __shared__ float fin_red[];  // [NW][n_pad] sums, [NW][n_pad] compensations, [NW][4] moments
+                                                           const int* __restrict__ shape_dev, int vw_ctas) {
+    extern __shared__ float fin_red[];  // [V][n_pad] sums, [V][n_pad] compensations, [V][4] moments
     pdl_wait();  // the update grid wrote the partials and the shape
     pdl_trigger();
     if (shape_dev) {  // split count and partial-row stride chosen on the device by the fused launch
         splits = shape_dev[0];
         part_rows = shape_dev[1];
     }
-    float* red_s = fin_red;
-    float* red_c = fin_red + NW * n_pad;
-    float* redm = fin_red + 2 * NW * n_pad;
     const int M_act = count_dev ? *count_dev : M_act_host;
     const int j = blockIdx.x;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (j >= M_act) {  // the grid covers an upper bound of the active count
         if (j == 0 && threadIdx.x == 0) *count_out = 0;  // nothing active: empty list
         return;
     }
+    // summation order: NW virtual warps, or (update loop of the BF16 stage) the persistent stage
+    // kernel's order for this active count, so that both give identical rows
+    const int V = vw_ctas > 0 ? fin_vwarps(M_act, vw_ctas) : NW;
     finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
-                     traj, t_iter, status, red_s, red_c, redm);
+                     traj, t_iter, status, V, fin_red);
     compact_tail<NW>(flags, act_idx, M_act, act_out, count_out, rows_accum, done_ctr, M_act);
 }
 
@@ -204,7 +153,7 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr, const int* shape_dev, bool pdl) {
+                            unsigned int* done_ctr, const int* shape_dev, bool pdl, int vw_ctas) {
     const float fT = static_cast<float>(inv_T), ftol = static_cast<float>(tol);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -221,13 +170,13 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
         cfg.dynamicSmemBytes = sizeof(float) * 32 * (2 * n_pad + 4);
         return cudaLaunchKernelEx(&cfg, finalize_kernel<32>, part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                                   count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj, t_iter, status, act_out,
-                                  count_out, rows_accum, done_ctr, shape_dev);
+                                  count_out, rows_accum, done_ctr, shape_dev, 0);
     }
     cfg.blockDim = dim3(128, 1, 1);
-    cfg.dynamicSmemBytes = sizeof(float) * 4 * (2 * n_pad + 4);
+    cfg.dynamicSmemBytes = sizeof(float) * (vw_ctas > 0 ? kFinMaxVWarps : 4) * (2 * n_pad + 4);
     return cudaLaunchKernelEx(&cfg, finalize_kernel<4>, part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                               count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj, t_iter, status, act_out,
-                              count_out, rows_accum, done_ctr, shape_dev);
+                              count_out, rows_accum, done_ctr, shape_dev, vw_ctas);
 }
 
 // Un-normalised update (step entry point): Bnew = acc / T - 3 B and moments / T.

@@ -1,0 +1,538 @@
+// Persistent BF16 stage of Algorithm 2: every fixed-point update of the restarts of one
+// component, from the first iteration to the last, in one cooperative launch (one CTA per SM,
+// all CTAs co-resident). Per iteration t:
+//
+//   1. update:   each CTA takes the (restart tile, sample split) that the active count gives it
+//                (tc_device_shape, the same one-wave shape as the per-launch update kernel) and
+//                runs the fused GEMM-cube-GEMM of Section 3.1 on the tensor cores over its
+//                chunks of X~, writing its FP32 partial of (Z o Z o Z) X~^T;
+//   2. grid barrier; finish: groups of 16, 4 or 2 warps (fewer rows, larger groups) finish the
+//                active rows (compensated sum of the split partials in a fixed order, b' =
+//                acc / T - 3 b, normalisation, step distance, convergence flag);
+//   3. grid barrier; removal of converged rows (Section 3.2): every CTA compacts the active list
+//                from the flags (all CTAs compute the same list), and the loop ends when no row
+//                is active or the iteration limit is reached.
+//
+// The arithmetic of every step is that of the per-launch path (fused_tc_kernel + finalize_kernel),
+// so both give identical results; the persistent form removes two launches per iteration, the
+// TMEM allocation and barrier set-up of each update, and the host's reads of the active count.
+//
+// Data written by other CTAs inside the launch (restart rows, partials, flags, the active list)
+// is read with cache-global loads (L1 is not coherent across SMs). Every wait is bounded
+// (ICA_WAIT_NS): on timeout the CTA raises the device status word, stops arriving at the grid
+// barriers (the other CTAs then time out as well), drains its copies and MMAs, frees TMEM and
+// returns.
+#include "rowfin.cuh"
+#include "tc_common.cuh"
+
+namespace ica {
+
+namespace {
+
+struct StageArgs {
+    float* B32;
+    int ldb;
+    int* act[2];       // the two active lists; act[cur0] holds the list on entry
+    int* count[2];     // their counts
+    int cur0;
+    int n_pad, n;
+    int64_t T;
+    int total_chunks, shape_ctas;
+    float* part_acc;
+    float* part_mom;
+    int* flags;
+    int* iters;
+    float* traj;  // [M][kTrajLen][2] (alpha, step distance) or null
+    int* status;
+    long long* rows_accum;
+    unsigned int* bar_ctr;  // grid barrier counter, zero on entry
+    int* ctl;               // out: iteration index reached, final active count, final list index
+    int t_begin, t_end;
+    float inv_T, tol;
+    int stages;
+    uint32_t a_bytes, xsub_bytes, xstage_bytes, off_x, off_p, off_bar;
+};
+
+// Grid-wide barrier over the CTAs of a cooperative launch: arrival counter with release (fence +
+// atomic) and a bounded acquire spin by one thread. `target` is the number of arrivals of all
+// barriers so far. Returns false (and raises the abort flag) on timeout.
+__device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int target, volatile int* abort_flag,
+                                             int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!*abort_flag) {
+            __threadfence();
+            atomicAdd(ctr, 1u);
+            const uint64_t t0 = global_ns();
+            for (uint32_t it = 0;; ++it) {
+                if (*reinterpret_cast<volatile unsigned int*>(ctr) >= target) break;
+                if ((it & 15u) == 15u && global_ns() - t0 > ICA_WAIT_NS) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    *abort_flag = 1;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return !*abort_flag;
+}
+
+// One active row j finished by a group of R warps (warp gw of the group, named barrier bar_id):
+// the split partials summed in the virtual-warp order of row_partials with V = R, the row
+// completed by the group's first warp (which loads the restart row while the sums run).
+// red: the group's scratch, [R][n_pad] sums, [R][n_pad] compensations, [R][4].
+__device__ __forceinline__ void group_finish_row(const StageArgs& a, const int* act, int j, int splits, int part_rows,
+                                                 int t, float* red, int R, int gw, int bar_id) {
+    const bool want_traj = a.traj && t < kTrajLen;
+    const int nq = (a.n_pad + 31) >> 5;
+    int r = 0;
+    float b[8];
+    if (gw == 0) {
+        r = __ldcg(act + j);
+        load_row(a.B32, a.ldb, r, nq, a.n, b);
+    }
+    row_partials(a.part_acc, a.part_mom, splits, part_rows, a.n_pad, j, want_traj, R, R, gw, red);
+    named_bar_sync(bar_id, 32 * R);
+    if (gw == 0) {
+        float accv[8], e2, e4;
+        row_combine(red, R, a.n_pad, a.n, want_traj, accv, &e2, &e4);
+        finish_row_loaded(accv, b, nq, a.n, r, j, a.B32, a.ldb, a.inv_T, a.tol, a.flags, a.iters, a.traj, t,
+                          want_traj, e2, e4, a.status);
+    }
+    named_bar_sync(bar_id, 32 * R);  // the scratch is reused by the group's next row
+}
+
+}  // namespace
+
+template <int TC, int NB>
+__global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_constant__ CUtensorMap xmap, const StageArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_raw);
+    const uint32_t base_u32 = (raw_u32 + 1023u) & ~1023u;
+    uint8_t* base = smem_raw + (base_u32 - raw_u32);
+    constexpr uint32_t p_bytes = static_cast<uint32_t>(TC / 64) * 16384u;
+    const uint32_t stages = static_cast<uint32_t>(a.stages);
+    const uint32_t sA = base_u32, sX = base_u32 + a.off_x, sP = base_u32 + a.off_p;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + a.off_bar);
+    uint64_t* full = bars;          // [8]  X~ stage loaded
+    uint64_t* empty = bars + 8;     // [8]  X~ stage released by the second product that read it
+    uint64_t* d1_full = bars + 16;  // [NB] Z chunk ready in TMEM
+    uint64_t* d1_empty = bars + 19; // [NB] Z chunk read out by the epilogue warps
+    uint64_t* p_full = bars + 22;   // [NB] P chunk written to SMEM by the epilogue warps
+    uint64_t* d2_full = bars + 28;  //      accumulator complete (once per update of this CTA)
+    uint64_t* mma_done = bars + 29; //      every MMA of this CTA retired (teardown)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kBars);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* mom_sm = reinterpret_cast<float*>(bars + kBars + 2);  // [3][128][4]
+    int* new_count = reinterpret_cast<int*>(base + a.off_bar + 6656u);
+    float* fin_scratch = reinterpret_cast<float*>(base);  // restart tile region, free while rows finish
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = static_cast<int>(gridDim.x), bid = static_cast<int>(blockIdx.x);
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&d1_full[b], 1);
+            mbar_init(&d1_empty[b], kEpiWarps);
+            mbar_init(&p_full[b], kEpiWarps);
+        }
+        mbar_init(d2_full, 1);
+        mbar_init(mma_done, 2);  // one commit per MMA-issuing thread
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) tma_prefetch_desc(&xmap);
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t kD1Col = TC == 192 ? 64u : (TC == 128 ? 128u : 256u);  // Z buffers after D2
+    static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
+    static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
+
+    // running counts of each role (mbarrier phases continue across the updates)
+    uint32_t pc = 0;   // producer: chunks issued
+    uint32_t g1c = 0;  // first-product issuer: chunks consumed
+    uint32_t g2c = 0;  // second-product issuer: chunks consumed
+    uint32_t ec = 0;   // epilogue: chunks consumed
+    uint32_t d2n = 0;  // updates this CTA took part in
+    unsigned int bar_target = 0;
+    int cur = a.cur0;
+    int M_act = __ldcg(cur ? a.count[1] : a.count[0]);
+    int t = a.t_begin;
+    for (; t < a.t_end && M_act > 0; ++t) {
+        const int* act = cur ? a.act[1] : a.act[0];
+        int tiles, sp, cps;
+        tc_device_shape(M_act, a.shape_ctas, a.total_chunks, &tiles, &sp, &cps);
+        const bool active = bid < tiles * sp;
+        const int tile = bid / sp, split = bid % sp;
+        const int m0 = tile * kTcRows;
+        const int c_begin = split * cps;
+        const int nch = active ? min(a.total_chunks, c_begin + cps) - c_begin : 0;
+        const int part_rows = tiles * kTcRows;
+        const bool mom = t < kTrajLen;
+
+        if (active && warp >= 2 && warp < 2 + kEpiWarps) {
+            // restart tile -> BF16, K-major, 128-byte swizzle (as the per-launch update kernel)
+            const int et = threadIdx.x - 64;
+            const int cpr = a.n_pad / 8;
+            for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
+                const int row = idx / cpr, ch = idx % cpr;
+                const int gm = m0 + row;
+                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                if (gm < M_act) {
+                    const int r = __ldcg(act + gm);
+                    const float4* src =
+                        reinterpret_cast<const float4*>(a.B32 + static_cast<int64_t>(r) * a.ldb + ch * 8);
+                    v0 = __ldcg(src);
+                    v1 = __ldcg(src + 1);
+                }
+                const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
+                const uint32_t h0 = pack_bf16x2(v0.x, v0.y), h1 = pack_bf16x2(v0.z, v0.w),
+                               h2 = pack_bf16x2(v1.x, v1.y), h3 = pack_bf16x2(v1.z, v1.w);
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(h0), "r"(h1), "r"(h2),
+                             "r"(h3)
+                             : "memory");
+                if constexpr (tc_split_b(TC)) {  // residuals b - float(bf16(b)) in the second half
+                    auto lo = [](uint32_t hp, float x, float y) {
+                        return pack_bf16x2(x - __uint_as_float(hp << 16), y - __uint_as_float(hp & 0xFFFF0000u));
+                    };
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + (a.a_bytes >> 1)),
+                                 "r"(lo(h0, v0.x, v0.y)), "r"(lo(h1, v0.z, v0.w)), "r"(lo(h2, v1.x, v1.y)),
+                                 "r"(lo(h3, v1.z, v1.w))
+                                 : "memory");
+                }
+            }
+            fence_proxy_async_smem();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+
+        if (active) {
+            if (warp == 0) {
+                // -------------------------------------------------------------- TMA producer
+                if (lane == 0) {
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t s = pc % stages;
+                        if (pc >= stages &&
+                            !mbar_wait(&empty[s], ((pc / stages) - 1u) & 1u, abort_flag, a.status))
+                            break;
+                        mbar_arrive_expect_tx(&full[s], a.xstage_bytes);
+                        const int tg = (c_begin + c) * TC;
+                        const uint32_t stage = sX + s * a.xstage_bytes;
+#pragma unroll
+                        for (int sub = 0; sub < TC / 64; ++sub)
+                            tma_load_2d(stage + static_cast<uint32_t>(sub) * a.xsub_bytes, &xmap, &full[s],
+                                        tg + sub * 64, 0);
+                        ++pc;
+                    }
+                }
+            } else if (warp == 1) {
+                // -------------------------------------------------------------- first products
+                if (lane == 0) {
+                    constexpr uint32_t id1 = idesc_bf16(128, TC, 1u);  // B: X~ MN-major
+                    const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
+                    const uint64_t b1_desc = sw128_desc(sX, a.xsub_bytes, 1024u);
+                    const uint32_t stage16 = a.xstage_bytes >> 4;
+                    const int ksteps1 = a.n_pad / 16;
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t s = g1c % stages, b = g1c % NB;
+                        bool ok = mbar_wait(&full[s], (g1c / stages) & 1u, abort_flag, a.status);
+                        if (ok && g1c >= static_cast<uint32_t>(NB))
+                            ok = mbar_wait(&d1_empty[b], ((g1c - NB) / NB) & 1u, abort_flag, a.status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t d1 = tmem + kD1Col + b * TC;
+                        const uint64_t b1s = b1_desc + static_cast<uint64_t>(s * stage16);
+#pragma unroll
+                        for (int ks = 0; ks < 16; ++ks) {
+                            if (ks >= ksteps1) break;
+                            const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                            const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                            umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
+                        }
+                        if constexpr (tc_split_b(TC)) {
+                            const uint64_t a1_lo = a1_desc + static_cast<uint64_t>((a.a_bytes >> 1) >> 4);
+#pragma unroll
+                            for (int ks = 0; ks < 16; ++ks) {
+                                if (ks >= ksteps1) break;
+                                const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                                const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                                umma_bf16_acc(d1, a1_lo + a_off, b1s + b_off, id1);
+                            }
+                        }
+                        umma_commit(&d1_full[b]);
+                        ++g1c;
+                    }
+                }
+            } else if (warp == kG2Warp) {
+                // -------------------------------------------------------------- second products
+                if (lane == 0) {
+                    const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(a.n_pad), 0);
+                    constexpr int KS2 = TC / 16;
+                    uint64_t pd[KS2], xd[KS2];
+#pragma unroll
+                    for (int j = 0; j < KS2; ++j) {
+                        const uint32_t ks = static_cast<uint32_t>(j);
+                        pd[j] = sw128_desc(sP + (ks >> 2) * 16384u + (ks & 3u) * 32u, 16u, 1024u);
+                        xd[j] = sw128_desc(sX + (ks >> 2) * a.xsub_bytes + (ks & 3u) * 32u, 16u, 1024u);
+                    }
+                    const uint32_t stage16 = a.xstage_bytes >> 4;
+                    bool ok = true;
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t b = g2c % NB, s = g2c % stages;
+                        ok = mbar_wait(&p_full[b], (g2c / NB) & 1u, abort_flag, a.status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint64_t po = static_cast<uint64_t>((b * p_bytes) >> 4);
+                        const uint64_t xo = static_cast<uint64_t>(s * stage16);
+                        umma_bf16(tmem, pd[0] + po, xd[0] + xo, id2, c > 0 ? 1u : 0u);
+#pragma unroll
+                        for (int j = 1; j < KS2; ++j) umma_bf16_acc(tmem, pd[j] + po, xd[j] + xo, id2);
+                        umma_commit(&empty[s]);  // releases the X~ stage and the P buffer
+                        ++g2c;
+                    }
+                    if (ok) umma_commit(d2_full);
+                }
+            } else {
+                // -------------------------------------------------------------- epilogue warps
+                const int q = warp & 3;
+                const int h = (warp - 2) >> 2;  // column group 0..kGroups-1
+                const int row = q * 32 + lane;
+                const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+                constexpr int CW = TC / kGroups;
+                float2 s2 = make_float2(0.f, 0.f), s4 = make_float2(0.f, 0.f);
+                bool ok = true;
+                for (int c = 0; c < nch; ++c) {
+                    const uint32_t b = ec % NB;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], (ec / NB) & 1u, abort_flag, a.status));
+                    if (!ok) break;
+                    tc_fence_after();
+                    float v[CW];
+                    const uint32_t d1 = tmem + kD1Col + b * TC + lane_off + static_cast<uint32_t>(h * CW);
+                    constexpr int N64 = CW / 64, N32 = (CW % 64) / 32, N16 = (CW % 32) / 16;
+                    static_assert(CW % 16 == 0, "column group must be a multiple of 16");
+#pragma unroll
+                    for (int i = 0; i < N64; ++i)
+                        tmem_ld64(d1 + static_cast<uint32_t>(64 * i), *reinterpret_cast<float(*)[64]>(&v[64 * i]));
+                    if constexpr (N32 == 1)
+                        tmem_ld32(d1 + static_cast<uint32_t>(64 * N64), *reinterpret_cast<float(*)[32]>(&v[64 * N64]));
+                    if constexpr (N16 == 1)
+                        tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
+                    tmem_ld_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&d1_empty[b]);
+                    uint32_t pk[CW / 2];
+                    if (mom) {
+#pragma unroll
+                        for (int i = 0; i < CW; i += 2) {
+                            const float2 z = make_float2(v[i], v[i + 1]);
+                            const float2 z2 = mul2(z, z);
+                            s2 = add2(s2, z2);
+                            s4 = fma2(z2, z2, s4);
+                            const float2 z3 = mul2(z2, z);
+                            pk[i / 2] = pack_bf16x2(z3.x, z3.y);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < CW; i += 2) {
+                            const float2 z = make_float2(v[i], v[i + 1]);
+                            const float2 z3 = mul2(mul2(z, z), z);
+                            pk[i / 2] = pack_bf16x2(z3.x, z3.y);
+                        }
+                    }
+                    if (ec >= static_cast<uint32_t>(NB)) {
+                        // P[b] is free once the second product of chunk ec - NB retired
+                        const uint32_t cr = ec - NB;
+                        ok = __all_sync(0xffffffffu,
+                                        mbar_wait(&empty[cr % stages], (cr / stages) & 1u, abort_flag, a.status));
+                        if (!ok) break;
+                    }
+                    const uint32_t pbase = sP + b * p_bytes;
+#pragma unroll
+                    for (int g = 0; g < CW / 8; ++g) {
+                        const int col = h * CW + g * 8;  // sample within the chunk
+                        const uint32_t addr = pbase + static_cast<uint32_t>(col >> 6) * 16384u +
+                                              sw128_off(static_cast<uint32_t>(row),
+                                                        static_cast<uint32_t>((col & 63) >> 3));
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pk[g * 4 + 0]),
+                                     "r"(pk[g * 4 + 1]), "r"(pk[g * 4 + 2]), "r"(pk[g * 4 + 3])
+                                     : "memory");
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&p_full[b]);
+                    ++ec;
+                }
+                const int grow = m0 + row;
+                const int64_t prow = static_cast<int64_t>(split) * part_rows + grow;
+                if (ok && h < 2) {  // accumulator read-out: two warps per lane quarter
+                    ok = __all_sync(0xffffffffu, mbar_wait(d2_full, d2n & 1u, abort_flag, a.status));
+                    if (ok) {
+                        tc_fence_after();
+                        const int half = a.n_pad / 2;
+                        for (int g = 0; g < half / 8; ++g) {
+                            const int col = h * half + g * 8;
+                            float v8[8];
+                            tmem_ld8(tmem + lane_off + static_cast<uint32_t>(col), v8);
+                            tmem_ld_wait();
+                            if (grow < M_act) {
+                                float4* dst = reinterpret_cast<float4*>(a.part_acc + prow * a.n_pad + col);
+                                dst[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);
+                                dst[1] = make_float4(v8[4], v8[5], v8[6], v8[7]);
+                            }
+                        }
+                    }
+                }
+                ++d2n;
+                if (h > 0) {
+                    float* dst = mom_sm + ((h - 1) * kTcRows + row) * 4;
+                    dst[0] = s2.x + s2.y;
+                    dst[1] = s4.x + s4.y;
+                    dst[2] = 0.f;
+                }
+                named_bar_sync(1, 32 * kEpiWarps);
+                if (h == 0 && grow < M_act) {
+                    float m2 = s2.x + s2.y, m4 = s4.x + s4.y, mq = 0.f;
+#pragma unroll
+                    for (int hh = 0; hh < kGroups - 1; ++hh) {  // fixed order: groups 1, 2, ...
+                        const float* src = mom_sm + (hh * kTcRows + row) * 4;
+                        m2 += src[0];
+                        m4 += src[1];
+                        mq += src[2];
+                    }
+                    a.part_mom[prow * 4 + 0] = m2;
+                    a.part_mom[prow * 4 + 1] = m4;
+                    a.part_mom[prow * 4 + 2] = mq;
+                    a.part_mom[prow * 4 + 3] = 0.f;
+                }
+            }
+        }
+        // ---------------------------------------------------------------- finish the rows
+        tc_fence_before();
+        bar_target += static_cast<unsigned int>(G);
+        if (!grid_barrier(a.bar_ctr, bar_target, abort_flag, a.status)) break;
+        tc_fence_after();
+        if (warp < 16) {  // groups of R warps, one row per group and round (fin_vwarps)
+            const int R = fin_vwarps(M_act, G), ngrp = 16 / R;
+            const int grp = warp / R, gw = warp % R;
+            float* red = fin_scratch + grp * R * (2 * a.n_pad + 4);
+            for (int j = bid * ngrp + grp; j < M_act; j += G * ngrp)
+                group_finish_row(a, act, j, sp, part_rows, t, red, R, gw, 2 + grp);
+        }
+        bar_target += static_cast<unsigned int>(G);
+        if (!grid_barrier(a.bar_ctr, bar_target, abort_flag, a.status)) break;
+        // ---------------------------------------------------------------- remove converged rows
+        compact_block(a.flags, act, M_act, cur ? a.act[0] : a.act[1], new_count, bid == 0 ? a.rows_accum : nullptr, kThreads);
+        __syncthreads();
+        const int M_new = *reinterpret_cast<volatile int*>(new_count);
+        __syncthreads();  // new_count is rewritten by the next compaction
+        cur ^= 1;
+        M_act = M_new;
+    }
+    // ------------------------------------------------------------------ teardown
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && lane == 0) {  // every issued load must land before the CTA exits
+        for (uint32_t s = 0; s < stages && s < pc; ++s) {
+            const uint32_t c_last = s + ((pc - 1u - s) / stages) * stages;
+            mbar_drain(&full[s], (c_last / stages) & 1u, a.status);
+        }
+    }
+    if ((warp == 1 || warp == kG2Warp) && lane == 0) {
+        umma_commit(mma_done);
+        mbar_drain(mma_done, 0u, a.status);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (bid == 0 && threadIdx.x == 0 && !*abort_flag) {
+        a.ctl[0] = t;
+        a.ctl[1] = M_act;
+        a.ctl[2] = cur;
+        *(cur ? a.count[1] : a.count[0]) = M_act;
+    }
+}
+
+template <int TC, int NB>
+static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p,
+                                     int* resident) {
+    const TcLayout L = tc_layout(p.n_pad, false, TC, NB, false, 1024u);  // + the compaction's static scratch
+    if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
+    cudaError_t e = allow_max_dyn_smem(stage_tc_kernel<TC, NB>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_tc_kernel<TC, NB>, kThreads, L.total)) !=
+        cudaSuccess)
+        return e;
+    if (resident) *resident = per_sm * sms;
+    if (per_sm * sms < p.ctas) return cudaErrorCooperativeLaunchTooLarge;  // nothing launched
+    StageArgs a{};
+    a.B32 = p.B32;
+    a.ldb = p.ldb;
+    a.act[0] = p.act0;
+    a.act[1] = p.act1;
+    a.count[0] = p.count0;
+    a.count[1] = p.count1;
+    a.cur0 = p.cur0;
+    a.n_pad = p.n_pad;
+    a.n = p.n;
+    a.T = p.T;
+    a.total_chunks = static_cast<int>((p.T + TC - 1) / TC);
+    a.shape_ctas = p.ctas;
+    a.part_acc = p.part_acc;
+    a.part_mom = p.part_mom;
+    a.flags = p.flags;
+    a.iters = p.iters;
+    a.traj = p.traj;
+    a.status = p.status;
+    a.rows_accum = p.rows_accum;
+    a.bar_ctr = p.bar_ctr;
+    a.ctl = p.ctl;
+    a.t_begin = p.t_begin;
+    a.t_end = p.t_end;
+    a.inv_T = static_cast<float>(p.inv_T);
+    a.tol = static_cast<float>(p.tol);
+    a.stages = static_cast<int>(L.stages);
+    a.a_bytes = L.a_bytes;
+    a.xsub_bytes = L.xsub_bytes;
+    a.xstage_bytes = L.xstage_bytes;
+    a.off_x = L.off_x;
+    a.off_p = L.off_p;
+    a.off_bar = L.off_bar;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(p.ctas), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stage_tc_kernel<TC, NB>, xmap, a);
+}
+
+cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident) {
+    if (p.n_pad <= 64) return launch_stage_impl<ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB>(s, xmap, p, resident);
+    if (p.n_pad <= 128) return launch_stage_impl<128, 2>(s, xmap, p, resident);
+    return launch_stage_impl<64, 2>(s, xmap, p, resident);
+}
+
+}  // namespace ica

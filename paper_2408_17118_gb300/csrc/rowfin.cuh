@@ -17,24 +17,33 @@ struct CompSum {  // s + c carries the exact running sum to about twice FP32 pre
     __device__ __forceinline__ float value() const { return s + c; }
 };
 
-// Warp 0 of a block (or the row's own warp) finishes row j from the summed update u*T (acc):
-// b' = acc / T - 3 b, normalisation, distance, flag, iteration count and trajectory.
-__device__ __forceinline__ void finish_row(const float (&accv)[8], int nq, int n, const int* __restrict__ act_idx,
-                                           int j, float* __restrict__ B32, int ldb, float inv_T, float tol,
-                                           int* __restrict__ flags, int* __restrict__ iters,
-                                           float* __restrict__ traj, int t_iter, bool want_traj, float e2sum,
-                                           float e4sum, int* status) {
+// Restart row r's current entries (lane's columns k = lane + 32 q), loaded ahead of the split
+// sums so that their latency overlaps them. Cache-global loads: in the persistent stage kernel
+// other CTAs wrote these rows earlier in the same launch.
+__device__ __forceinline__ void load_row(const float* __restrict__ B32, int ldb, int r, int nq, int n, float (&b)[8]) {
     const int lane = threadIdx.x & 31;
-    const int r = act_idx ? act_idx[j] : j;
-    float u[8], b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        b[q] = (q < nq && k < n) ? __ldcg(B32 + static_cast<int64_t>(r) * ldb + k) : 0.f;
+    }
+}
+
+// One warp finishes active row j (restart r, current entries b) from the summed update u*T
+// (acc): b' = acc / T - 3 b, normalisation, distance, flag, iteration count and trajectory.
+__device__ __forceinline__ void finish_row_loaded(const float (&accv)[8], const float (&b)[8], int nq, int n, int r,
+                                                  int j, float* __restrict__ B32, int ldb, float inv_T, float tol,
+                                                  int* __restrict__ flags, int* __restrict__ iters,
+                                                  float* __restrict__ traj, int t_iter, bool want_traj, float e2sum,
+                                                  float e4sum, int* status) {
+    const int lane = threadIdx.x & 31;
+    float u[8];
     float ss = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int k = lane + 32 * q;
         u[q] = 0.f;
-        b[q] = 0.f;
         if (q < nq && k < n) {
-            b[q] = B32[static_cast<int64_t>(r) * ldb + k];
             u[q] = accv[q] * inv_T - 3.f * b[q];
             ss = fmaf(u[q], u[q], ss);
         }
@@ -61,7 +70,7 @@ __device__ __forceinline__ void finish_row(const float (&accv)[8], int nq, int n
     }
     if (lane == 0) {
         flags[j] = (!bad && d > tol) ? 1 : 0;
-        iters[r] += 1;
+        iters[r] = __ldcg(iters + r) + 1;
         if (bad) atomicOr(status, DEV_NONFINITE);
         if (want_traj) {
             const float e2 = e2sum * inv_T, e4 = e4sum * inv_T;
@@ -70,6 +79,88 @@ __device__ __forceinline__ void finish_row(const float (&accv)[8], int nq, int n
             traj[(static_cast<int64_t>(r) * kTrajLen + t_iter) * 2 + 1] = d;
         }
     }
+}
+
+// Compensated sums of active row j's split partials in the virtual-warp order: virtual warp v
+// of V adds splits v, v + V, v + 2V, ... in increasing order (and, with moments, their sum z^2
+// and sum z^4); the V partial sums are then combined in the order v = 0, 1, ..., V - 1
+// (row_combine). A group of R real warps (warp w of the group) computes virtual warps w,
+// w + R, ... into red: [V][n_pad] sums, [V][n_pad] compensations, [V][4] moment sums.
+__device__ __forceinline__ void row_partials(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
+                                             int splits, int part_rows, int n_pad, int j, bool want_mom, int V,
+                                             int R, int w, float* red) {
+    const int lane = threadIdx.x & 31;
+    const int nq = (n_pad + 31) >> 5;
+    float* red_s = red;
+    float* red_c = red + V * n_pad;
+    float* redm = red + 2 * V * n_pad;
+    for (int v = w; v < V; v += R) {
+        CompSum acc[8];
+        CompSum m2, m4;
+#pragma unroll 4
+        for (int sp = v; sp < splits; sp += V) {
+            const float* p = part_acc + (static_cast<int64_t>(sp) * part_rows + j) * n_pad;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nq) break;
+                const int k = lane + 32 * q;
+                if (k < n_pad) acc[q].add(__ldcg(p + k));
+            }
+            if (want_mom && lane == 0) {
+                m2.add(__ldcg(part_mom + (static_cast<int64_t>(sp) * part_rows + j) * 4 + 0));
+                m4.add(__ldcg(part_mom + (static_cast<int64_t>(sp) * part_rows + j) * 4 + 1));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q >= nq) break;
+            const int k = lane + 32 * q;
+            if (k < n_pad) {
+                red_s[v * n_pad + k] = acc[q].s;
+                red_c[v * n_pad + k] = acc[q].c;
+            }
+        }
+        if (lane == 0) {
+            redm[4 * v + 0] = m2.s;
+            redm[4 * v + 1] = m2.c;
+            redm[4 * v + 2] = m4.s;
+            redm[4 * v + 3] = m4.c;
+        }
+    }
+}
+
+// One warp combines the V virtual-warp sums of row_partials (after a barrier of the group).
+__device__ __forceinline__ void row_combine(const float* red, int V, int n_pad, int n, bool want_mom, float (&accv)[8],
+                                            float* e2sum, float* e4sum) {
+    const int lane = threadIdx.x & 31;
+    const int nq = (n_pad + 31) >> 5;
+    const float* red_s = red;
+    const float* red_c = red + V * n_pad;
+    const float* redm = red + 2 * V * n_pad;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        accv[q] = 0.f;
+        if (q < nq && k < n) {
+            CompSum acc;
+            float cs = 0.f;
+            for (int ww = 0; ww < V; ++ww) {
+                acc.add(red_s[ww * n_pad + k]);
+                cs += red_c[ww * n_pad + k];
+            }
+            accv[q] = acc.value() + cs;
+        }
+    }
+    CompSum m2, m4;
+    if (want_mom)
+        for (int ww = 0; ww < V; ++ww) {
+            m2.add(redm[4 * ww + 0]);
+            m2.add(redm[4 * ww + 1]);
+            m4.add(redm[4 * ww + 2]);
+            m4.add(redm[4 * ww + 3]);
+        }
+    *e2sum = m2.value();
+    *e4sum = m4.value();
 }
 
 // Stable compaction of the active list (Section 3.2: converged rows leave B) by one block of
@@ -97,7 +188,7 @@ __device__ __forceinline__ void compact_block(const int* __restrict__ flags, con
     for (int ww = 0; ww < w; ++ww) before += warp_tot[ww];
     int pos = before + incl - local;
     for (int i = b0; i < e0; ++i)
-        if (__ldcg(flags + i)) act_out[pos++] = act_idx ? act_idx[i] : i;
+        if (__ldcg(flags + i)) act_out[pos++] = act_idx ? __ldcg(act_idx + i) : i;
     if (threadIdx.x == nthr - 1) {
         *count_out = before + incl;
         if (rows_accum) *rows_accum += M_act;  // rows this iteration updated

@@ -43,6 +43,7 @@ def test_default_opts_and_status_strings(lib):
     o = _lib.ica_opts()
     lib.ica_default_opts(C.byref(o))
     assert o.precision == _lib.ICA_BF16 and o.refine_topk == 4 and o.refine_iters == 10
+    assert o.stage_persistent == 1
     assert o.stage_tol == 1e-4 and o.refine_tol == 1e-6 and o.fp32_tol_floor == 1e-6 and not o.B0
     for st in range(8):
         assert lib.ica_status_string(st) not in (None, b"unknown status")

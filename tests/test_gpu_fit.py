@@ -150,3 +150,33 @@ def test_full_size_eeg_like_sampled(ctx):
         w0 = rng.standard_normal(64)
         wl, yl, _, _ = oracle.fastica_run(w0, Xw, np.zeros((64, 64)), 30, 1e-6)
         assert oracle.upsilon(oracle.kurtosis_alpha(yl)) <= ups0 + 1e-6, l
+
+
+@pytest.mark.parametrize("case", ["small", "eeg32", "ragged"])
+def test_persistent_stage_equals_per_launch(ctx, case):
+    """The persistent cooperative BF16 stage (one launch per component: update, grid barrier,
+    row completion, grid barrier, removal of converged rows) runs the same arithmetic as the
+    per-launch update + finalize path: identical W, kurtoses and restart updates. The persistent
+    stage reports the exact iteration count; the per-launch loop learns the active count only
+    every fourth iteration and counts the empty launches before that read."""
+    import json
+
+    from paper_2408_17118_gb300 import ica
+
+    if case == "small":
+        w = synth.small_mixture(0)
+    elif case == "eeg32":
+        w = synth.eeg_like(32, 50_000, 512, seed=4)
+    else:
+        w = synth.eeg_like(21, 9_999, 300, seed=5)  # ragged n, T and M
+    out = []
+    for persistent in (1, 0):
+        W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, seed=7, stage_persistent=persistent)
+        st = json.loads(ica.ica_last_stats(ctx))
+        out.append((W, kurt, st))
+    (W0, k0, s0), (W1, k1, s1) = out
+    assert s0["stage_persistent_launches"] >= 1 and s1["stage_persistent_launches"] == 0
+    assert np.array_equal(W0, W1) and np.array_equal(k0, k1)
+    for c0, c1 in zip(s0["components"], s1["components"]):
+        assert c0["rows_updated"] == c1["rows_updated"] and c0["refine_rows"] == c1["refine_rows"]
+        assert c0["iterations"] <= c1["iterations"] < c0["iterations"] + 4
