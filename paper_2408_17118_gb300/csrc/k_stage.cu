@@ -134,15 +134,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], tc_g2_issuers(TC));  // a commit of every second-product issuer
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(&d1_full[b], 1);
-            mbar_init(&d1_empty[b], kEpiWarps);
-            mbar_init(&p_full[b], kEpiWarps);
+            mbar_init(&d1_empty[b], kEpiWarps / 2);  // one epilogue team per buffer
+            mbar_init(&p_full[b], kEpiWarps / 2);
         }
-        mbar_init(d2_full, 1);
-        mbar_init(mma_done, 2);  // one commit per MMA-issuing thread
+        mbar_init(d2_full, tc_g2_issuers(TC));
+        mbar_init(mma_done, 1 + tc_g2_issuers(TC));  // one commit per MMA-issuing thread
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t kD1Col = TC == 192 ? 64u : (TC == 128 ? 128u : 256u);  // Z buffers after D2
+    constexpr int G2S = tc_g2_issuers(TC);
+    constexpr uint32_t kD2Cols = tc_d2_cols(TC);
+    constexpr uint32_t kD1Col = G2S * kD2Cols;  // Z buffers after the G2S accumulators
     static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
     static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
 
@@ -275,15 +277,18 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                         ++g1c;
                     }
                 }
-            } else if (warp == kG2Warp) {
+            } else if (warp == kG2Warp || warp == kG2bWarp) {
                 // -------------------------------------------------------------- second products
-                if (lane == 0) {
+                // issuer gi of G2S: K steps j = gi mod G2S into accumulator gi
+                const int gi = warp - kG2Warp;
+                if (lane == 0 && gi < G2S) {
                     const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(a.n_pad), 0);
-                    constexpr int KS2 = TC / 16;
-                    uint64_t pd[KS2], xd[KS2];
+                    const uint32_t dacc = tmem + static_cast<uint32_t>(gi) * kD2Cols;
+                    constexpr int KSI = TC / 16 / G2S;  // K steps of this issuer: gi, gi + G2S, ...
+                    uint64_t pd[KSI], xd[KSI];
 #pragma unroll
-                    for (int j = 0; j < KS2; ++j) {
-                        const uint32_t ks = static_cast<uint32_t>(j);
+                    for (int j = 0; j < KSI; ++j) {
+                        const uint32_t ks = static_cast<uint32_t>(gi + j * G2S);
                         pd[j] = sw128_desc(sP + (ks >> 2) * 16384u + (ks & 3u) * 32u, 16u, 1024u);
                         xd[j] = sw128_desc(sX + (ks >> 2) * a.xsub_bytes + (ks & 3u) * 32u, 16u, 1024u);
                     }
@@ -296,85 +301,101 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                         tc_fence_after();
                         const uint64_t po = static_cast<uint64_t>((b * p_bytes) >> 4);
                         const uint64_t xo = static_cast<uint64_t>(s * stage16);
-                        umma_bf16(tmem, pd[0] + po, xd[0] + xo, id2, c > 0 ? 1u : 0u);
+                        umma_bf16(dacc, pd[0] + po, xd[0] + xo, id2, c > 0 ? 1u : 0u);
 #pragma unroll
-                        for (int j = 1; j < KS2; ++j) umma_bf16_acc(tmem, pd[j] + po, xd[j] + xo, id2);
-                        umma_commit(&empty[s]);  // releases the X~ stage and the P buffer
+                        for (int j = 1; j < KSI; ++j) umma_bf16_acc(dacc, pd[j] + po, xd[j] + xo, id2);
+                        umma_commit(&empty[s]);  // with the other issuers' commits: releases the stage and P
                         ++g2c;
                     }
                     if (ok) umma_commit(d2_full);
                 }
             } else {
                 // -------------------------------------------------------------- epilogue warps
+                // Two teams of 8 warps take alternate chunks (team k: chunks g = k mod 2, Z / P
+                // buffer k), so that one team's TMEM-load and barrier latency overlaps the other
+                // team's cube conversion. In a team, warp (lane quarter q, half hh) converts rows
+                // 32q.. of columns [hh TC/2, (hh+1) TC/2) in two passes of TC/4 columns.
+                static_assert(NB == 2, "one Z / P buffer per epilogue team");
                 const int q = warp & 3;
-                const int h = (warp - 2) >> 2;  // column group 0..kGroups-1
+                const int h = (warp - 2) >> 2;  // moment group 0..3 = 2 team + hh
+                const int team = h >> 1, hh = h & 1;
                 const int row = q * 32 + lane;
                 const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-                constexpr int CW = TC / kGroups;
+                constexpr int CW = TC / 4;  // columns per pass
                 float2 s2 = make_float2(0.f, 0.f), s4 = make_float2(0.f, 0.f);
                 bool ok = true;
-                for (int c = 0; c < nch; ++c) {
-                    const uint32_t b = ec % NB;
-                    ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], (ec / NB) & 1u, abort_flag, a.status));
+                for (int c = 0; c < nch && ok; ++c) {
+                    const uint32_t g = ec + static_cast<uint32_t>(c);
+                    if (static_cast<int>(g & 1u) != team) continue;
+                    const uint32_t b = g % NB;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], (g / NB) & 1u, abort_flag, a.status));
                     if (!ok) break;
                     tc_fence_after();
-                    float v[CW];
-                    const uint32_t d1 = tmem + kD1Col + b * TC + lane_off + static_cast<uint32_t>(h * CW);
-                    constexpr int N64 = CW / 64, N32 = (CW % 64) / 32, N16 = (CW % 32) / 16;
-                    static_assert(CW % 16 == 0, "column group must be a multiple of 16");
-#pragma unroll
-                    for (int i = 0; i < N64; ++i)
-                        tmem_ld64(d1 + static_cast<uint32_t>(64 * i), *reinterpret_cast<float(*)[64]>(&v[64 * i]));
-                    if constexpr (N32 == 1)
-                        tmem_ld32(d1 + static_cast<uint32_t>(64 * N64), *reinterpret_cast<float(*)[32]>(&v[64 * N64]));
-                    if constexpr (N16 == 1)
-                        tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
-                    tmem_ld_wait();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&d1_empty[b]);
-                    uint32_t pk[CW / 2];
-                    if (mom) {
-#pragma unroll
-                        for (int i = 0; i < CW; i += 2) {
-                            const float2 z = make_float2(v[i], v[i + 1]);
-                            const float2 z2 = mul2(z, z);
-                            s2 = add2(s2, z2);
-                            s4 = fma2(z2, z2, s4);
-                            const float2 z3 = mul2(z2, z);
-                            pk[i / 2] = pack_bf16x2(z3.x, z3.y);
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < CW; i += 2) {
-                            const float2 z = make_float2(v[i], v[i + 1]);
-                            const float2 z3 = mul2(mul2(z, z), z);
-                            pk[i / 2] = pack_bf16x2(z3.x, z3.y);
-                        }
-                    }
-                    if (ec >= static_cast<uint32_t>(NB)) {
-                        // P[b] is free once the second product of chunk ec - NB retired
-                        const uint32_t cr = ec - NB;
-                        ok = __all_sync(0xffffffffu,
-                                        mbar_wait(&empty[cr % stages], (cr / stages) & 1u, abort_flag, a.status));
-                        if (!ok) break;
-                    }
                     const uint32_t pbase = sP + b * p_bytes;
+#pragma unroll 1
+                    for (int pass = 0; pass < 2; ++pass) {
+                        const int col0 = hh * (TC / 2) + pass * CW;  // first sample of this pass
+                        float v[CW];
+                        const uint32_t d1 = tmem + kD1Col + b * TC + lane_off + static_cast<uint32_t>(col0);
+                        constexpr int N64 = CW / 64, N32 = (CW % 64) / 32, N16 = (CW % 32) / 16;
+                        static_assert(CW % 16 == 0, "column group must be a multiple of 16");
 #pragma unroll
-                    for (int g = 0; g < CW / 8; ++g) {
-                        const int col = h * CW + g * 8;  // sample within the chunk
-                        const uint32_t addr = pbase + static_cast<uint32_t>(col >> 6) * 16384u +
-                                              sw128_off(static_cast<uint32_t>(row),
-                                                        static_cast<uint32_t>((col & 63) >> 3));
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pk[g * 4 + 0]),
-                                     "r"(pk[g * 4 + 1]), "r"(pk[g * 4 + 2]), "r"(pk[g * 4 + 3])
-                                     : "memory");
+                        for (int i = 0; i < N64; ++i)
+                            tmem_ld64(d1 + static_cast<uint32_t>(64 * i), *reinterpret_cast<float(*)[64]>(&v[64 * i]));
+                        if constexpr (N32 == 1)
+                            tmem_ld32(d1 + static_cast<uint32_t>(64 * N64),
+                                      *reinterpret_cast<float(*)[32]>(&v[64 * N64]));
+                        if constexpr (N16 == 1)
+                            tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
+                        tmem_ld_wait();
+                        if (pass == 1) {  // the team has read all of Z(g)
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&d1_empty[b]);
+                        }
+                        uint32_t pk[CW / 2];
+                        if (mom) {
+#pragma unroll
+                            for (int i = 0; i < CW; i += 2) {
+                                const float2 z = make_float2(v[i], v[i + 1]);
+                                const float2 z2 = mul2(z, z);
+                                s2 = add2(s2, z2);
+                                s4 = fma2(z2, z2, s4);
+                                const float2 z3 = mul2(z2, z);
+                                pk[i / 2] = pack_bf16x2(z3.x, z3.y);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < CW; i += 2) {
+                                const float2 z = make_float2(v[i], v[i + 1]);
+                                const float2 z3 = mul2(mul2(z, z), z);
+                                pk[i / 2] = pack_bf16x2(z3.x, z3.y);
+                            }
+                        }
+                        if (pass == 0 && g >= static_cast<uint32_t>(NB)) {
+                            // P[b] is free once the second product of chunk g - NB retired
+                            const uint32_t cr = g - NB;
+                            ok = __all_sync(0xffffffffu,
+                                            mbar_wait(&empty[cr % stages], (cr / stages) & 1u, abort_flag, a.status));
+                            if (!ok) break;
+                        }
+#pragma unroll
+                        for (int j = 0; j < CW / 8; ++j) {
+                            const int col = col0 + j * 8;  // sample within the chunk
+                            const uint32_t addr = pbase + static_cast<uint32_t>(col >> 6) * 16384u +
+                                                  sw128_off(static_cast<uint32_t>(row),
+                                                            static_cast<uint32_t>((col & 63) >> 3));
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pk[j * 4 + 0]),
+                                         "r"(pk[j * 4 + 1]), "r"(pk[j * 4 + 2]), "r"(pk[j * 4 + 3])
+                                         : "memory");
+                        }
                     }
+                    if (!ok) break;
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&p_full[b]);
-                    ++ec;
                 }
+                ec += static_cast<uint32_t>(nch);
                 const int grow = m0 + row;
                 const int64_t prow = static_cast<int64_t>(split) * part_rows + grow;
                 if (ok && h < 2) {  // accumulator read-out: two warps per lane quarter
@@ -386,7 +407,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             const int col = h * half + g * 8;
                             float v8[8];
                             tmem_ld8(tmem + lane_off + static_cast<uint32_t>(col), v8);
-                            tmem_ld_wait();
+                            if constexpr (G2S == 2) {  // the odd K steps' accumulator
+                                float w8[8];
+                                tmem_ld8(tmem + kD2Cols + lane_off + static_cast<uint32_t>(col), w8);
+                                tmem_ld_wait();
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) v8[i] += w8[i];
+                            } else {
+                                tmem_ld_wait();
+                            }
                             if (grow < M_act) {
                                 float4* dst = reinterpret_cast<float4*>(a.part_acc + prow * a.n_pad + col);
                                 dst[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);
@@ -450,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             mbar_drain(&full[s], (c_last / stages) & 1u, a.status);
         }
     }
-    if ((warp == 1 || warp == kG2Warp) && lane == 0) {
+    if ((warp == 1 || warp == kG2Warp || (warp == kG2bWarp && tc_g2_issuers(TC) == 2)) && lane == 0) {
         umma_commit(mma_done);
         mbar_drain(mma_done, 0u, a.status);
     }

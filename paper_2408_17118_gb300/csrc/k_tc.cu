@@ -93,15 +93,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], MOMENTS_ONLY ? 1 : tc_g2_issuers(TC));  // every second-product issuer
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(&d1_full[b], 1);
             mbar_init(&d1_empty[b], kEpiWarps);
             mbar_init(&p_full[b], kEpiWarps);
         }
-        mbar_init(d2_full, 1);
-        mbar_init(mma_done, MOMENTS_ONLY ? 1 : 2);  // one commit per MMA-issuing thread
+        mbar_init(d2_full, tc_g2_issuers(TC));
+        mbar_init(mma_done, MOMENTS_ONLY ? 1 : 1 + tc_g2_issuers(TC));  // one commit per MMA-issuing thread
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tD2 = tmem;
-    constexpr uint32_t kD1Col = TC == 192 ? 64u : (TC == 128 ? 128u : 256u);  // Z buffers after D2
+    constexpr int G2S = tc_g2_issuers(TC);
+    constexpr uint32_t kD2Cols = tc_d2_cols(TC);
+    constexpr uint32_t kD1Col = G2S * kD2Cols;  // Z buffers after the G2S accumulators
     static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
     static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
 
@@ -224,22 +226,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma_commit(mma_done);
             mbar_drain(mma_done, 0u, status);
         }
-    } else if (warp == kG2Warp) {
-        // ------------------------------------------------------------------ second-product issuer
-        // A thread of its own (on another scheduler than the first-product issuer), so that the
-        // two instruction streams overlap; the products write different TMEM columns and every
+    } else if (warp == kG2Warp || warp == kG2bWarp) {
+        // ------------------------------------------------------------------ second-product issuers
+        // Threads of their own (on other schedulers than the first-product issuer), so that the
+        // instruction streams overlap; the products write different TMEM columns and every
         // shared operand they share is ordered by the barriers (P(c) exists only after the
-        // first product of chunk c retired and the epilogue consumed it).
-        if (!MOMENTS_ONLY && lane == 0) {
+        // first product of chunk c retired and the epilogue consumed it). Issuer gi of G2S takes
+        // the K steps j = gi mod G2S into accumulator gi.
+        const int gi = warp - kG2Warp;
+        if (!MOMENTS_ONLY && lane == 0 && gi < G2S) {
             const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(n_pad), 0);
-            const uint32_t dacc = tD2;
+            const uint32_t dacc = tD2 + static_cast<uint32_t>(gi) * kD2Cols;
             // Per-K-step descriptors of stage 0 / buffer 0, built once: inside the chunk loop an MMA
             // costs two 64-bit adds (stage and buffer offsets) besides the instruction itself.
-            constexpr int KS2 = TC / 16;
-            uint64_t pd[KS2], xd[KS2];
+            constexpr int KSI = TC / 16 / G2S;  // K steps of this issuer: gi, gi + G2S, ...
+            uint64_t pd[KSI], xd[KSI];
 #pragma unroll
-            for (int j = 0; j < KS2; ++j) {
-                const uint32_t ks = static_cast<uint32_t>(j);
+            for (int j = 0; j < KSI; ++j) {
+                const uint32_t ks = static_cast<uint32_t>(gi + j * G2S);
                 pd[j] = sw128_desc(sP + (ks >> 2) * 16384u + (ks & 3u) * 32u, 16u, 1024u);
                 xd[j] = sw128_desc(sX + (ks >> 2) * xsub_bytes + (ks & 3u) * 32u, 16u, 1024u);
             }
@@ -255,8 +259,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint64_t xo = static_cast<uint64_t>(static_cast<uint32_t>(s) * stage16);
                 umma_bf16(dacc, pd[0] + po, xd[0] + xo, id2, c > 0 ? 1u : 0u);
 #pragma unroll
-                for (int j = 1; j < KS2; ++j) umma_bf16_acc(dacc, pd[j] + po, xd[j] + xo, id2);
-                umma_commit(&empty[s]);  // releases the X~ stage and the P buffer
+                for (int j = 1; j < KSI; ++j) umma_bf16_acc(dacc, pd[j] + po, xd[j] + xo, id2);
+                umma_commit(&empty[s]);  // with the other issuers' commits: releases the X~ stage and P
                 if (++s == stages) s = 0;
                 if (++b == NB) {
                     b = 0;
@@ -351,7 +355,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int col = h * half + g * 8;
                     float v8[8];
                     tmem_ld8(tD2 + lane_off + static_cast<uint32_t>(col), v8);
-                    tmem_ld_wait();
+                    if constexpr (G2S == 2) {  // the odd K steps' accumulator
+                        float w8[8];
+                        tmem_ld8(tD2 + kD2Cols + lane_off + static_cast<uint32_t>(col), w8);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v8[i] += w8[i];
+                    } else {
+                        tmem_ld_wait();
+                    }
                     if (grow < M_act) {
                         float4* dst = reinterpret_cast<float4*>(part_acc + prow * n_pad + col);
                         dst[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);

@@ -30,6 +30,12 @@ namespace ica {
 #define ICA_TC_SPLIT_B 1
 #endif
 __host__ __device__ constexpr bool tc_split_b(int TC) { return ICA_TC_SPLIT_B && TC == 192; }
+// Second products issued by two threads (on different schedulers) into two accumulators, summed
+// when read out: measured on GB300, one thread sustained one M128 K16 MMA per 67 cycles at
+// N <= 64 and two threads one per 50 (N = 64) or 41 (N = 16) cycles. Both accumulators fit TMEM
+// next to the Z buffers for TC = 192 (n_pad <= 64) and TC = 128 (n_pad <= 128).
+__host__ __device__ constexpr int tc_g2_issuers(int TC) { return TC == 64 ? 1 : 2; }
+__host__ __device__ constexpr uint32_t tc_d2_cols(int TC) { return TC == 192 ? 64u : (TC == 128 ? 128u : 256u); }
 
 namespace {
 constexpr int kBars = 40;
@@ -39,8 +45,9 @@ constexpr int kBars = 40;
 constexpr int kEpiWarps = ICA_TC_EPI_WARPS;  // 4 lane quarters x kEpiWarps / 4 column groups
 constexpr int kGroups = kEpiWarps / 4;
 static_assert(kEpiWarps == 8 || kEpiWarps == 16, "two or four column groups");
-constexpr int kG2Warp = 2 + kEpiWarps;  // issues the second products
-constexpr int kThreads = 32 * (3 + kEpiWarps);
+constexpr int kG2Warp = 2 + kEpiWarps;   // issues the second products (even K steps)
+constexpr int kG2bWarp = 3 + kEpiWarps;  // issues their odd K steps when the issue is split
+constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr uint32_t kScratchBytes = 8192u;  // barriers, TMEM slot, moment exchange
 struct TcLayout {
     uint32_t a_bytes, xsub_bytes, xn_bytes, xstage_bytes, p_bytes, stages, off_x, off_p, off_bar, total;
