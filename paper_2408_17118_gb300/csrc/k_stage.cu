@@ -54,7 +54,7 @@ struct StageArgs {
 };
 
 // Grid-wide barrier over the CTAs of a cooperative launch: arrival counter with release (fence +
-// atomic) and a bounded acquire spin by one thread. `target` is the number of arrivals of all
+// red.release) and a bounded acquire spin by one thread. `target` is the number of arrivals of all
 // barriers so far. Returns false (and raises the abort flag) on timeout.
 __device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int target, volatile int* abort_flag,
                                              int* status) {
@@ -62,10 +62,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int tar
     if (threadIdx.x == 0) {
         if (!*abort_flag) {
             __threadfence();
-            atomicAdd(ctr, 1u);
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
             const uint64_t t0 = global_ns();
             for (uint32_t it = 0;; ++it) {
-                if (*reinterpret_cast<volatile unsigned int*>(ctr) >= target) break;
+                unsigned int seen;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(ctr) : "memory");
+                if (seen >= target) break;
                 if ((it & 15u) == 15u && global_ns() - t0 > ICA_WAIT_NS) {
                     atomicOr(status, DEV_TIMEOUT);
                     *abort_flag = 1;
@@ -216,9 +218,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             }
             fence_proxy_async_smem();
         }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
+        // The restart tile is complete for the first-product issuer (warp 1) once the epilogue
+        // warps pass this barrier; the TMA producer starts loading X~ without waiting for it.
+        if (active && warp >= 1 && warp < 2 + kEpiWarps) named_bar_sync(10, 32 * (1 + kEpiWarps));
 
         if (active) {
             if (warp == 0) {

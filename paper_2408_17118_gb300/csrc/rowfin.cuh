@@ -97,7 +97,7 @@ __device__ __forceinline__ void row_partials(const float* __restrict__ part_acc,
     for (int v = w; v < V; v += R) {
         CompSum acc[8];
         CompSum m2, m4;
-#pragma unroll 4
+#pragma unroll 8
         for (int sp = v; sp < splits; sp += V) {
             const float* p = part_acc + (static_cast<int64_t>(sp) * part_rows + j) * n_pad;
 #pragma unroll
