@@ -337,20 +337,28 @@ def run_ours(args):
     it = kinds.get("iteration", {"launches": 0, "ms": 0.0, "flops": 0.0})
     achieved = it["flops"] / (it["ms"] / 1e3) / 1e12 if it["ms"] > 0 else 0.0
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    # DRAM traffic per iteration launch: ncu measured 259.6 MB read+written for one launch at
-    # n = 64, M = 1024, T = 2e6 against 256.0 MB of algorithmic X~ reads (ratio 1.014; the
-    # split partials are the rest). Scaled here to the fit's mean algorithmic X~ bytes per launch.
+    # Dominant kernel: the persistent BF16 stage (one launch per component runs every iteration:
+    # update, row completion, removal of converged rows), or the per-launch update kernel when
+    # the stage ran per iteration. DRAM traffic per launch from ncu:
+    #   persistent: 25.96 MB read+written for component 3 (n_pad 64) against 25.6 MB of X~ (one
+    #     pass; later iterations re-read X~ from L2): 1.014 x n_pad T 2 bytes per launch;
+    #   per-launch: 259.6 MB for one launch at n = 64, M = 1024, T = 2e6 against 256.0 MB of X~:
+    #     1.014 x the X~ bytes of every iteration.
+    persistent = bool(stats) and stats[-1].get("stage_persistent_launches", 0) > 0
     xt_bytes = 0.0
     if stats:
         for comp in stats[-1].get("components", []):
-            n_c = N - comp["i"]
-            xt_bytes += comp["iterations"] * ((n_c + 15) // 16 * 16) * T * 2.0
+            n_pad_c = (N - comp["i"] + 1 + 15) // 16 * 16
+            xt_bytes += (1 if persistent else comp["iterations"]) * n_pad_c * T * 2.0
     traffic = 1.014 * xt_bytes / max(1, it["launches"] / max(1, args.steps)) if xt_bytes else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "ncu dram read+write of one launch at n=64 M=1024 T=2e6 / algorithmic X~ bytes "
-                                "(1.014), times the fit's mean algorithmic bytes per launch",
-                "kernel": "fused_tc_kernel (BF16 iteration)",
+                "traffic_note": ("ncu dram read+write of one stage launch (n_pad 64, T 2e5) / its X~ bytes (1.014), "
+                                 "times the fit's mean X~ bytes per launch" if persistent else
+                                 "ncu dram read+write of one launch at n=64 M=1024 T=2e6 / algorithmic X~ bytes "
+                                 "(1.014), times the fit's mean algorithmic bytes per launch"),
+                "kernel": ("stage_tc_kernel (persistent BF16 stage: tcgen05 update, row completion, removal "
+                           "of converged rows)" if persistent else "fused_tc_kernel (BF16 iteration)"),
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "launches": it["launches"], "avg_launch_ms": it["ms"] / max(1, it["launches"]),
                 "share_of_step": it["ms"] / sum(prof_ms)}

@@ -895,7 +895,11 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                                            n_pad, n, act[cur], counts + cur, M_host, B32, n_pad, inv_T, tol_iter, flags, itc,
                                            o.precision == ICA_PLAIN_FP32 ? nullptr : traj, t, status, act[cur ^ 1],
                                            counts + (cur ^ 1), crows + 2 * i, done_ctr, fa.shape_dev,
-                                           fa.shape_dev != nullptr, fa.shape_dev ? 152 / c->cta_div : 0));
+                                           fa.shape_dev != nullptr,
+                                           // the persistent stage's summation order when this
+                                           // context may run it (identical results either way),
+                                           // else four virtual warps per row
+                                           fa.shape_dev && c->cta_div == 1 ? 152 : 0));
                         return ICA_OK;
                     });
                     if (rc) return rc;

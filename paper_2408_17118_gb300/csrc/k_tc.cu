@@ -13,9 +13,10 @@
 // used for the kurtosis of candidates, Eq. 2); the update variant accumulates the moments
 // only when asked (the first iterations, whose kurtosis trajectory is kept per restart).
 //
-// Warp roles (608 threads): warp 0 issues TMA loads; warp 1 allocates TMEM and issues the first
-// products (one thread); warp 18 issues the second products (one thread); warps 2..17 convert
-// TMEM rows (warp w reads TMEM lanes 32*(w%4).., quarter (w-2)/4 of the chunk's columns). The two
+// Warp roles (640 threads): warp 0 issues TMA loads; warp 1 allocates TMEM and issues the first
+// products (one thread); warps 18 and 19 issue the second products (one thread each: even and
+// odd K steps into two accumulators when TMEM has room, tc_g2_issuers); warps 2..17 convert
+// TMEM rows (warp w reads TMEM lanes 32*(w%4).., quarter (w-2)/4 of the chunk's columns). The
 // issuing threads sit on different schedulers: measured on GB300, one thread issuing both
 // products spent about 100 cycles per tcgen05.mma while sharing its scheduler with four busy
 // epilogue warps, and splitting the issue cut the time of a 64 x 1024 x 2e6 step by a quarter.
