@@ -263,6 +263,7 @@ struct FusedArgs {
     int64_t ldx = 0;
     int max_splits = 0;
     int* shape_dev = nullptr;  // BF16 update: shape the launch on the device, write {splits, part_rows} here
+    bool pdl = false;          // FP32 few-row update: programmatic dependent launch after the previous kernel
 };
 
 int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape) {
@@ -307,7 +308,7 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
             choose_splits(total_rows_chunks, 1, 2 * 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps);
             shape->part_rows = fp32_rows_tile(a.M_act);
             KL(launch_fused_fp32_rows(s, a.moments_only, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.Xt32, a.ldx,
-                                      a.n_pad, a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows));
+                                      a.n_pad, a.T, shape->splits, shape->cps, pacc, pmom, shape->part_rows, a.pdl));
             return ICA_OK;
         }
         const int tiles = (a.M_act + kFp32Rows - 1) / kFp32Rows;
@@ -979,19 +980,24 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                 fa.M_act = R_host;
                 fa.moments_only = false;
                 fa.moments = false;
+                fa.pdl = rt > 0;  // after the previous iteration's finalize (kernel to kernel)
                 rc = timed(K_REFINE, 4.0 * n * R_host * dT, [&] { return run_fused(c, L, fa, &sh); });
+                fa.pdl = false;
                 if (rc) return rc;
                 rc = timed(K_FINALIZE, 0.0, [&] {
                     KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
                                        n_pad, n, act[rcur], counts + rcur, R_host, B32, n_pad, inv_T, tol_ref, flags,
                                        itc, nullptr, kTrajLen, status, act[rcur ^ 1], counts + (rcur ^ 1),
-                                       crows + 2 * i + 1, done_ctr));
+                                       crows + 2 * i + 1, done_ctr, nullptr, true));
                     return ICA_OK;
                 });
                 if (rc) return rc;
                 rcur ^= 1;
                 ++rt;
-                if (sync_due(rt)) {
+                // launches size for the host bound and read the exact count on the device: the
+                // host reads it only every fourth iteration (a host round trip costs more than
+                // the few-row launches of an iteration that has nothing left to do)
+                if (sync_due_shaped(rt)) {
                     rc = read_count(counts + rcur, &R_host);
                     if (rc) return rc;
                 }

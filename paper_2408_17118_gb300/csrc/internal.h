@@ -108,7 +108,7 @@ size_t fp32_rows_smem_bytes(int n_pad, int R);
 cudaError_t launch_fused_fp32_rows(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
                                    const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
                                    int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
-                                   int part_rows);
+                                   int part_rows, bool pdl = false);
 
 // ---- k_mlp.cu (learned restart pruner) ----
 constexpr int kMlpIn = 13, kMlpHid = 64;

@@ -205,6 +205,8 @@ __global__ void __launch_bounds__(256) fused_fp32_rows_kernel(const float* __res
     const size_t work = static_cast<size_t>(CS) * SX + 256u * R + static_cast<size_t>(CS) * R;
     float* redm = Xs + (work > 1024u * R ? work : 1024u * R);  // [8][R][3]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_wait();  // the refinement loop's previous finalize wrote B, the list and the count
+    pdl_trigger();
     const int M_act = count_dev ? *count_dev : M_act_host;
     const int split = blockIdx.x;
 
@@ -370,23 +372,29 @@ template <int R>
 cudaError_t launch_rows_variant(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
                                 const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
                                 int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
-                                int part_rows) {
+                                int part_rows, bool pdl) {
     const size_t smem = fp32_rows_smem_bytes(n_pad, R);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(splits), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e;
     if (moments_only) {
         e = allow_max_dyn_smem(fused_fp32_rows_kernel<R, true>);
         if (e != cudaSuccess) return e;
-        fused_fp32_rows_kernel<R, true><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx,
-                                                                  n_pad, T, chunks_per_split, part_acc, part_mom,
-                                                                  part_rows);
-    } else {
-        e = allow_max_dyn_smem(fused_fp32_rows_kernel<R, false>);
-        if (e != cudaSuccess) return e;
-        fused_fp32_rows_kernel<R, false><<<splits, 256, smem, s>>>(B32, ldb, act_idx, count_dev, M_act_host, Xt,
-                                                                   ldx, n_pad, T, chunks_per_split, part_acc,
-                                                                   part_mom, part_rows);
+        return cudaLaunchKernelEx(&cfg, fused_fp32_rows_kernel<R, true>, B32, ldb, act_idx, count_dev, M_act_host, Xt,
+                                  ldx, n_pad, T, chunks_per_split, part_acc, part_mom, part_rows);
     }
-    return cudaGetLastError();
+    e = allow_max_dyn_smem(fused_fp32_rows_kernel<R, false>);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, fused_fp32_rows_kernel<R, false>, B32, ldb, act_idx, count_dev, M_act_host, Xt,
+                              ldx, n_pad, T, chunks_per_split, part_acc, part_mom, part_rows);
 }
 
 int fp32_rows_chunk(int n_pad) { return rows_cs(n_pad); }
@@ -394,13 +402,13 @@ int fp32_rows_chunk(int n_pad) { return rows_cs(n_pad); }
 cudaError_t launch_fused_fp32_rows(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
                                    const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
                                    int64_t T, int splits, int chunks_per_split, float* part_acc, float* part_mom,
-                                   int part_rows) {
+                                   int part_rows, bool pdl) {
     if (part_rows == 4)
         return launch_rows_variant<4>(s, moments_only, B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx, n_pad, T,
-                                      splits, chunks_per_split, part_acc, part_mom, part_rows);
+                                      splits, chunks_per_split, part_acc, part_mom, part_rows, pdl);
     if (part_rows == 16)
         return launch_rows_variant<16>(s, moments_only, B32, ldb, act_idx, count_dev, M_act_host, Xt, ldx, n_pad, T,
-                                       splits, chunks_per_split, part_acc, part_mom, part_rows);
+                                       splits, chunks_per_split, part_acc, part_mom, part_rows, pdl);
     return cudaErrorInvalidValue;
 }
 
