@@ -775,6 +775,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         // without pruning from the same initial restarts (attempt 1).
         int t = 0, rt = 0, n_pruned = 0, fell_back = 0;
         long long stage_rows_seen = 0;  // last value read of this component's stage row counter
+        long long refine_rows_seen = 0;  // the same for its refinement row counter
         std::vector<int> hist;
         bool pruned_now = false, dropped_all = false;
         FusedArgs fa;
@@ -973,6 +974,80 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             CK(cudaMemcpyAsync(counts + 0, counts + 2, sizeof(int), cudaMemcpyDeviceToDevice, s));
             int rcur = 0, R_host = k;
             fa.precision = ICA_FP32;
+            // persistent refinement (one cooperative launch for all its iterations; same
+            // arithmetic as the per-launch loop below) when the fit has the GPU to itself
+            bool rpersist = o.stage_persistent && c->persist_ok && c->cta_div == 1 && o.max_splits == 0 && k <= 4;
+            while (rpersist && rt < refine_iters && R_host > 0) {
+                const int64_t rchunks = (T + fp32_rows_chunk(n_pad) - 1) / fp32_rows_chunk(n_pad);
+                StepShape rsh;
+                choose_splits(rchunks, 1, 2 * 152, 0, &rsh.splits, &rsh.cps);
+                RefineLaunch rl{};
+                rl.B32 = B32;
+                rl.ldb = n_pad;
+                rl.act0 = act[0];
+                rl.act1 = act[1];
+                rl.count0 = counts + 0;
+                rl.count1 = counts + 1;
+                rl.cur0 = rcur;
+                rl.Xt = Xt32;
+                rl.ldx = ldx;
+                rl.n_pad = n_pad;
+                rl.n = n;
+                rl.T = T;
+                rl.splits = rsh.splits;
+                rl.cps = rsh.cps;
+                rl.rows_max = R_host;
+                rl.part_acc = at<float>(c, L.part_acc);
+                rl.part_mom = at<float>(c, L.part_mom);
+                rl.flags = flags;
+                rl.iters = itc;
+                rl.status = status;
+                rl.rows_accum = crows + 2 * i + 1;
+                rl.bar_ctr = stage_bar;
+                rl.ctl = stage_ctl;
+                rl.t_begin = rt;
+                rl.t_end = refine_iters;
+                rl.inv_T = static_cast<float>(inv_T);
+                rl.tol = static_cast<float>(tol_ref);
+                CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
+                cudaError_t le = cudaSuccess;
+                int resident = 0;
+                const size_t rec0 = c->recs.size();
+                rc = timed(K_REFINE, 0.0, [&] {
+                    le = launch_refine_fp32(s, rl, &resident);
+                    return ICA_OK;
+                });
+                if (rc) return rc;
+                if (le == cudaErrorCooperativeLaunchTooLarge) {  // not all CTAs can be resident
+                    cudaGetLastError();
+                    c->persist_ok = false;
+                    c->persist_note = "refinement: cooperative launch too large: " + std::to_string(resident) +
+                                      " resident CTAs";
+                    if (c->recs.size() > rec0) c->recs.pop_back();
+                    rpersist = false;
+                    break;
+                }
+                if (le != cudaSuccess) {
+                    note_cuda_error(le, "launch_refine_fp32", __LINE__);
+                    return ICA_ERR_CUDA;
+                }
+                ++c->launches;
+                ++c->launches_total;
+                ++persist_launches;
+                long long* rows_h = reinterpret_cast<long long*>(c->host_i + 100);
+                CK(cudaMemcpyAsync(c->host_i + 96, stage_ctl, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(rows_h, crows + 2 * i + 1, sizeof(long long), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                rc = map_device_status(c->host_i[1]);
+                if (rc) return rc;
+                if (c->recs.size() > rec0)  // exact FLOPs: rows updated x 4 n T
+                    c->recs.back().flops = 4.0 * n * static_cast<double>(*rows_h - refine_rows_seen) * dT;
+                refine_rows_seen = *rows_h;
+                rt = c->host_i[96];
+                R_host = c->host_i[97];
+                rcur = c->host_i[98];
+            }
             while (rt < refine_iters && R_host > 0) {
                 StepShape sh;
                 fa.act = act[rcur];

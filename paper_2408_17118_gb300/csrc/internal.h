@@ -190,6 +190,37 @@ struct StageLaunch {
 // resident (optional) receives the number of CTAs of the kernel that fit the GPU at once.
 cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident = nullptr);
 
+// ---- k_fp32.cu: persistent FP32 refinement ----
+// Iterations [t_begin, t_end) of the refinement of at most rows_max (<= 4) candidate rows in one
+// cooperative launch of `splits` CTAs (the per-launch loop's split of the sample range into
+// chunks of fp32_rows_chunk(n_pad) samples, cps chunks per split). act_{cur0} / count_{cur0}
+// hold the rows; ctl receives {iteration index reached, final count, final list index}; the
+// final count is also stored in count_{ctl[2]}. bar_ctr must be zero. part_acc / part_mom need
+// splits x 4 rows. Returns cudaErrorCooperativeLaunchTooLarge, launching nothing, when the CTAs
+// cannot all be resident.
+struct RefineLaunch {
+    float* B32;
+    int ldb;
+    int *act0, *act1, *count0, *count1;
+    int cur0;
+    const float* Xt;
+    int64_t ldx;
+    int n_pad, n;
+    int64_t T;
+    int splits, cps, rows_max;
+    float* part_acc;
+    float* part_mom;
+    int* flags;
+    int* iters;
+    int* status;
+    long long* rows_accum;
+    unsigned int* bar_ctr;
+    int* ctl;
+    int t_begin, t_end;
+    float inv_T, tol;
+};
+cudaError_t launch_refine_fp32(cudaStream_t s, const RefineLaunch& p, int* resident = nullptr);
+
 // ---- k_plain.cu ----
 cudaError_t launch_gather_rows(cudaStream_t s, const float* B32, int ldb, const int* act_idx,
                                const int* count_dev, int M_act, int n_pad, float* out);

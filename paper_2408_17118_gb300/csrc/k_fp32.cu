@@ -6,6 +6,7 @@
 // Outputs are per-split partial sums, reduced in a fixed order by the finalize kernels.
 #include "common.cuh"
 #include "internal.h"
+#include "rowfin.cuh"
 
 namespace ica {
 
@@ -187,15 +188,16 @@ size_t fp32_rows_smem_bytes(int n_pad, int R) {
     return sizeof(float) * (static_cast<size_t>(n_pad) * R + (work > red ? work : red) + 24 * R);
 }
 
+// One split (a contiguous range of sample chunks) of the few-row update for rows act_idx[0..M_act)
+// by a CTA of 256 threads: partial (z o z o z) X~^T (or the moments) of the split into
+// part_acc / part_mom. rsm: the CTA's dynamic shared memory (fp32_rows_smem_bytes). Restart
+// rows and the list are read with cache-global loads (the persistent refinement rewrites them
+// between its updates).
 template <int R, bool MOMENTS_ONLY>
-__global__ void __launch_bounds__(256) fused_fp32_rows_kernel(const float* __restrict__ B32, int ldb,
-                                                              const int* __restrict__ act_idx,
-                                                              const int* __restrict__ count_dev, int M_act_host,
-                                                              const float* __restrict__ Xt, int64_t ldx, int n_pad,
-                                                              int64_t T, int chunks_per_split,
-                                                              float* __restrict__ part_acc,
-                                                              float* __restrict__ part_mom, int part_rows) {
-    extern __shared__ __align__(16) float rsm[];
+__device__ __forceinline__ void rows_update(const float* __restrict__ B32, int ldb, const int* __restrict__ act_idx,
+                                            int M_act, const float* __restrict__ Xt, int64_t ldx, int n_pad,
+                                            int64_t T, int chunks_per_split, int split, float* __restrict__ part_acc,
+                                            float* __restrict__ part_mom, int part_rows, float* rsm) {
     const int CS = rows_cs(n_pad), SX = n_pad + 4, H = 256 / CS, KQ = n_pad / 4, G = 256 / KQ;
     float* Bs = rsm;                    // [n_pad][R]
     float* Xs = Bs + n_pad * R;         // [CS][SX]   sample-major X~ chunk
@@ -205,15 +207,10 @@ __global__ void __launch_bounds__(256) fused_fp32_rows_kernel(const float* __res
     const size_t work = static_cast<size_t>(CS) * SX + 256u * R + static_cast<size_t>(CS) * R;
     float* redm = Xs + (work > 1024u * R ? work : 1024u * R);  // [8][R][3]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    pdl_wait();  // the refinement loop's previous finalize wrote B, the list and the count
-    pdl_trigger();
-    const int M_act = count_dev ? *count_dev : M_act_host;
-    const int split = blockIdx.x;
-
     for (int e = tid; e < n_pad * R; e += 256) {
         const int k = e / R, r = e % R;
         float v = 0.f;
-        if (r < M_act) v = B32[static_cast<int64_t>(act_idx ? act_idx[r] : r) * ldb + k];
+        if (r < M_act) v = __ldcg(B32 + static_cast<int64_t>(act_idx ? __ldcg(act_idx + r) : r) * ldb + k);
         Bs[e] = v;
     }
     const int64_t total_chunks = (T + CS - 1) / CS;
@@ -368,6 +365,22 @@ __global__ void __launch_bounds__(256) fused_fp32_rows_kernel(const float* __res
     }
 }
 
+template <int R, bool MOMENTS_ONLY>
+__global__ void __launch_bounds__(256) fused_fp32_rows_kernel(const float* __restrict__ B32, int ldb,
+                                                              const int* __restrict__ act_idx,
+                                                              const int* __restrict__ count_dev, int M_act_host,
+                                                              const float* __restrict__ Xt, int64_t ldx, int n_pad,
+                                                              int64_t T, int chunks_per_split,
+                                                              float* __restrict__ part_acc,
+                                                              float* __restrict__ part_mom, int part_rows) {
+    extern __shared__ __align__(16) float rsm[];
+    pdl_wait();  // the refinement loop's previous finalize wrote B, the list and the count
+    pdl_trigger();
+    const int M_act = count_dev ? *count_dev : M_act_host;
+    rows_update<R, MOMENTS_ONLY>(B32, ldb, act_idx, M_act, Xt, ldx, n_pad, T, chunks_per_split, blockIdx.x, part_acc,
+                                 part_mom, part_rows, rsm);
+}
+
 template <int R>
 cudaError_t launch_rows_variant(cudaStream_t s, bool moments_only, const float* B32, int ldb, const int* act_idx,
                                 const int* count_dev, int M_act_host, const float* Xt, int64_t ldx, int n_pad,
@@ -430,6 +443,101 @@ cudaError_t launch_fused_fp32(cudaStream_t s, bool moments_only, const float* B3
                                                          chunks_per_split, part_acc, part_mom, part_rows);
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Persistent FP32 refinement (a8): every refinement iteration of the few candidate rows in one
+// cooperative launch, one CTA per split of the sample range (the per-launch loop's grid).
+// Per iteration: the few-row update of the CTA's split (rows_update); grid barrier; CTA j
+// finishes active row j (its 8 warps sum the split partials in the order of finalize_kernel<32>:
+// 32 virtual warps, warp w taking virtual warps w, w + 8, ...); grid barrier; every CTA compacts
+// the list of rows still moving. Same arithmetic as the per-launch loop (fused_fp32_rows_kernel +
+// finalize_kernel<32>), so both give identical rows.
+// ------------------------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(256, 2) refine_fp32_kernel(RefineLaunch a, int chunks_per_split) {
+    extern __shared__ __align__(16) float rsm[];
+    __shared__ int new_count;
+    __shared__ int abort_sh;
+    volatile int* abort_flag = &abort_sh;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int G = static_cast<int>(gridDim.x), bid = static_cast<int>(blockIdx.x);
+    if (tid == 0) abort_sh = 0;
+    __syncthreads();
+    const int nq = (a.n_pad + 31) >> 5;
+    unsigned int target = 0;
+    int cur = a.cur0;
+    int M_act = __ldcg(cur ? a.count1 : a.count0);
+    int t = a.t_begin;
+    for (; t < a.t_end && M_act > 0; ++t) {
+        const int* act = cur ? a.act1 : a.act0;
+        rows_update<R, false>(a.B32, a.ldb, act, M_act, a.Xt, a.ldx, a.n_pad, a.T, chunks_per_split, bid, a.part_acc,
+                              a.part_mom, R, rsm);
+        target += static_cast<unsigned int>(G);
+        if (!grid_barrier(a.bar_ctr, target, abort_flag, a.status)) break;
+        if (bid < M_act) {  // row j = bid
+            const int j = bid;
+            int r = 0;
+            float b[8];
+            if (warp == 0) {
+                r = __ldcg(act + j);
+                load_row(a.B32, a.ldb, r, nq, a.n, b);
+            }
+            row_partials(a.part_acc, a.part_mom, G, R, a.n_pad, j, false, 32, 8, warp, rsm);
+            __syncthreads();
+            if (warp == 0) {
+                float accv[8], e2, e4;
+                row_combine(rsm, 32, a.n_pad, a.n, false, accv, &e2, &e4);
+                finish_row_loaded(accv, b, nq, a.n, r, j, a.B32, a.ldb, a.inv_T, a.tol, a.flags, a.iters, nullptr,
+                                  kTrajLen, false, 0.f, 0.f, a.status);
+            }
+        }
+        target += static_cast<unsigned int>(G);
+        if (!grid_barrier(a.bar_ctr, target, abort_flag, a.status)) break;
+        compact_block(a.flags, act, M_act, cur ? a.act0 : a.act1, &new_count, bid == 0 ? a.rows_accum : nullptr, 256);
+        __syncthreads();
+        const int M_new = *reinterpret_cast<volatile int*>(&new_count);
+        __syncthreads();
+        cur ^= 1;
+        M_act = M_new;
+    }
+    if (bid == 0 && tid == 0 && !abort_sh) {
+        a.ctl[0] = t;
+        a.ctl[1] = M_act;
+        a.ctl[2] = cur;
+        *(cur ? a.count1 : a.count0) = M_act;
+    }
+}
+
+cudaError_t launch_refine_fp32(cudaStream_t s, const RefineLaunch& p, int* resident) {
+    constexpr int R = 4;
+    if (p.rows_max > R || p.n_pad > kMaxN) return cudaErrorInvalidValue;
+    const int64_t total = (p.T + rows_cs(p.n_pad) - 1) / rows_cs(p.n_pad);
+    if (p.splits < 1 || static_cast<int64_t>(p.splits) * p.cps < total) return cudaErrorInvalidValue;
+    // the finish step sums 32 virtual warps' partials in the kernel's shared memory
+    size_t smem = fp32_rows_smem_bytes(p.n_pad, R);
+    const size_t fin = sizeof(float) * 32 * (2 * static_cast<size_t>(p.n_pad) + 4);
+    if (fin > smem) smem = fin;
+    cudaError_t e = allow_max_dyn_smem(refine_fp32_kernel<R>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_fp32_kernel<R>, 256, smem)) != cudaSuccess)
+        return e;
+    if (resident) *resident = per_sm * sms;
+    if (per_sm * sms < p.splits) return cudaErrorCooperativeLaunchTooLarge;  // nothing launched
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(p.splits), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, refine_fp32_kernel<R>, p, p.cps);
 }
 
 }  // namespace ica

@@ -53,34 +53,6 @@ struct StageArgs {
     uint32_t a_bytes, xsub_bytes, xstage_bytes, off_x, off_p, off_bar;
 };
 
-// Grid-wide barrier over the CTAs of a cooperative launch: arrival counter with release (fence +
-// red.release) and a bounded acquire spin by one thread. `target` is the number of arrivals of all
-// barriers so far. Returns false (and raises the abort flag) on timeout.
-__device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int target, volatile int* abort_flag,
-                                             int* status) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!*abort_flag) {
-            __threadfence();
-            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
-            const uint64_t t0 = global_ns();
-            for (uint32_t it = 0;; ++it) {
-                unsigned int seen;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(ctr) : "memory");
-                if (seen >= target) break;
-                if ((it & 15u) == 15u && global_ns() - t0 > ICA_WAIT_NS) {
-                    atomicOr(status, DEV_TIMEOUT);
-                    *abort_flag = 1;
-                    break;
-                }
-            }
-            __threadfence();
-        }
-    }
-    __syncthreads();
-    return !*abort_flag;
-}
-
 // One active row j finished by a group of R warps (warp gw of the group, named barrier bar_id):
 // the split partials summed in the virtual-warp order of row_partials with V = R, the row
 // completed by the group's first warp (which loads the restart row while the sums run).

@@ -1,5 +1,5 @@
-// Row completion and active-list compaction shared by the finalize kernel and the fused
-// tcgen05 kernel's split reduction (one update of Section 3.1 / removal of Section 3.2).
+// Row completion, active-list compaction and the grid barrier shared by the finalize kernel and
+// the persistent stage and refinement kernels (one update of Section 3.1 / removal of Section 3.2).
 #pragma once
 
 #include "common.cuh"
@@ -161,6 +161,34 @@ __device__ __forceinline__ void row_combine(const float* red, int V, int n_pad, 
         }
     *e2sum = m2.value();
     *e4sum = m4.value();
+}
+
+// Grid-wide barrier over the CTAs of a cooperative launch: arrival counter with release (fence +
+// red.release) and a bounded acquire spin by one thread. `target` is the number of arrivals of all
+// barriers so far. Returns false (and raises the abort flag) on timeout.
+__device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int target, volatile int* abort_flag,
+                                             int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!*abort_flag) {
+            __threadfence();
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
+            const uint64_t t0 = global_ns();
+            for (uint32_t it = 0;; ++it) {
+                unsigned int seen;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(ctr) : "memory");
+                if (seen >= target) break;
+                if ((it & 15u) == 15u && global_ns() - t0 > ICA_WAIT_NS) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    *abort_flag = 1;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return !*abort_flag;
 }
 
 // Stable compaction of the active list (Section 3.2: converged rows leave B) by one block of

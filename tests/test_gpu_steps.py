@@ -91,6 +91,52 @@ def test_deflation_basis(ctx, N, k):
     assert np.abs(W @ G.T).max() < tol
 
 
+@pytest.mark.parametrize("N,k", [(64, 24), (64, 40), (40, 20)])
+def test_deflation_basis_repeated_eigenvalues(ctx, N, k):
+    # W = Q W0 with W0 rows cos(th) e_a + sin(th) e_b (a among the first n coordinates, b among
+    # the last k) and th from two values: the Gram matrix of the Jacobi solve has two clusters of
+    # exactly repeated eigenvalues and is not diagonal; G = (F~F~^T)^(-1/2) F~ is still unique
+    from paper_2408_17118_gb300 import ica
+
+    n = N - k
+    rng = np.random.default_rng(N + 3 * k)
+    W0 = np.zeros((k, N))
+    for i in range(k):
+        th = 0.4 if i % 2 == 0 else 1.1
+        W0[i, i % n] = np.cos(th) if i < n else 0.0
+        W0[i, n + i] = np.sin(th) if i < n else 1.0
+    W0 /= np.linalg.norm(W0, axis=1, keepdims=True)
+    # rows with the same first coordinate must stay orthogonal: use distinct first coordinates
+    assert np.abs(W0 @ W0.T - np.eye(k)).max() < 1e-12
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    W = np.ascontiguousarray(Q @ W0)
+    G = ica.ica_deflation_basis(ctx, torch.from_numpy(W).cuda(), N).cpu().numpy()
+    ref = oracle.deflation_basis(W, N)
+    Ft = (np.eye(N) - W.T @ W)[:n]
+    tol = max(1e-12, 100 * np.finfo(np.float64).eps / np.linalg.eigvalsh(Ft @ Ft.T).min())
+    assert np.abs(G - ref).max() < tol, (np.abs(G - ref).max(), tol)
+    assert np.abs(G @ G.T - np.eye(n)).max() < tol
+    assert np.abs(W @ G.T).max() < tol
+
+
+def test_whiten_repeated_eigenvalues(ctx):
+    # X = A S with S S^T / T = I exactly and A = Q diag(d), d with repeated values: the covariance
+    # A A^T has clusters of exactly repeated eigenvalues; V = C^(-1/2) is unique
+    from paper_2408_17118_gb300 import ica
+
+    N, T = 48, 6000
+    rng = np.random.default_rng(11)
+    S, _ = np.linalg.qr(rng.standard_normal((T, N)))
+    S = S.T * np.sqrt(T)
+    S -= S.mean(axis=1, keepdims=True)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    d = np.repeat([0.5, 2.0, 7.0], N // 3)
+    X = (Q * d) @ S + 3.0
+    Xw, V, mean = ica.ica_whiten(ctx, torch.from_numpy(X.astype(np.float32)).cuda())
+    Xw_o, V_o, mean_o = oracle.whiten(X.astype(np.float32).astype(np.float64))
+    assert np.abs(V.cpu().numpy() - V_o).max() < 1e-8 * np.abs(V_o).max()
+
+
 def test_deflation_basis_identity(ctx):
     from paper_2408_17118_gb300 import ica
 
