@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
                                                         const double* __restrict__ bias, float* __restrict__ out32,
                                                         int64_t ld32, uint16_t* __restrict__ out16, int64_t ld16,
                                                         uint16_t* __restrict__ out16t, int64_t ld16t, int n_pad) {
-    __shared__ __align__(16) float Gs[RG_BK][RG_BM];
+    __shared__ __align__(16) float Gs[RG_BK][RG_BM + 4];  // padded: the transposing stores spread over banks
     __shared__ __align__(16) float Xs[RG_BK][RG_BT];
     __shared__ __align__(16) uint16_t Ts[RG_BT][RG_BM];  // transposed BF16 tile
     const int rb = blockIdx.x, tb = blockIdx.y;
@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     const bool vec_ok = (ldxin % 4 == 0);
     for (int k0 = 0; k0 < N; k0 += RG_BK) {
-        for (int e = threadIdx.x; e < RG_BK * RG_BM; e += 256) {
-            const int kk = e / RG_BM, rr = e % RG_BM;
+        for (int e = threadIdx.x; e < RG_BK * RG_BM; e += 256) {  // a row's 16 coefficients per 16 threads
+            const int rr = e / RG_BK, kk = e % RG_BK;
             const int r = rb * RG_BM + rr, k = k0 + kk;
             Gs[kk][rr] = (r < n && k < N) ? static_cast<float>(G[static_cast<int64_t>(r) * N + k]) : 0.f;
         }
@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
 #pragma unroll
         for (int kk = 0; kk < RG_BK; ++kk) {
             const float4 g = *reinterpret_cast<const float4*>(&Gs[kk][ty * 4]);
-            const float4 xa = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8]);
-            const float4 xb = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8 + 4]);
+            // samples tx*4.. and 64 + tx*4..: consecutive threads read consecutive 16-byte words
+            const float4 xa = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4]);
+            const float4 xb = *reinterpret_cast<const float4*>(&Xs[kk][RG_BT / 2 + tx * 4]);
             const float gv[4] = {g.x, g.y, g.z, g.w};
             const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
@@ -71,37 +72,40 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
     for (int i = 0; i < 4; ++i) {
         const int r = rb * RG_BM + ty * 4 + i;
         const float b = (bias && r < n) ? static_cast<float>(bias[r]) : 0.f;
-        float v[8];
+        float v[8];  // samples tx*4 + j (j < 4) and 64 + tx*4 + (j - 4)
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = r < n ? acc[i][j] - b : 0.f;
         if (out16t) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) Ts[tx * 8 + j][ty * 4 + i] = static_cast<uint16_t>(pack_bf16x2(v[j], 0.f) & 0xffffu);
+            for (int j = 0; j < 8; ++j)
+                Ts[(j < 4 ? 0 : RG_BT / 2 - 4) + tx * 4 + j][ty * 4 + i] =
+                    static_cast<uint16_t>(pack_bf16x2(v[j], 0.f) & 0xffffu);
         }
         if (r >= n_pad) continue;
-        const int64_t t = t0 + tx * 8;
-        if (out32) {
-            float* dst = out32 + static_cast<int64_t>(r) * ld32 + t;
-            if (t + 7 < T && (ld32 % 4 == 0)) {
-                *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-                *reinterpret_cast<float4*>(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
-            } else {
-                for (int j = 0; j < 8; ++j)
-                    if (t + j < T) dst[j] = v[j];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const float* vh = v + 4 * half;
+            const int64_t t = t0 + half * (RG_BT / 2) + tx * 4;
+            if (out32) {
+                float* dst = out32 + static_cast<int64_t>(r) * ld32 + t;
+                if (t + 3 < T && (ld32 % 4 == 0)) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(vh[0], vh[1], vh[2], vh[3]);
+                } else {
+                    for (int j = 0; j < 4; ++j)
+                        if (t + j < T) dst[j] = vh[j];
+                }
             }
-        }
-        if (out16) {
-            uint16_t* dst = out16 + static_cast<int64_t>(r) * ld16 + t;
-            if (t + 7 < T && (ld16 % 8 == 0)) {
-                uint4 pk;
-                pk.x = pack_bf16x2(v[0], v[1]);
-                pk.y = pack_bf16x2(v[2], v[3]);
-                pk.z = pack_bf16x2(v[4], v[5]);
-                pk.w = pack_bf16x2(v[6], v[7]);
-                *reinterpret_cast<uint4*>(dst) = pk;
-            } else {
-                for (int j = 0; j < 8; ++j)
-                    if (t + j < T) dst[j] = static_cast<uint16_t>(pack_bf16x2(v[j], 0.f) & 0xffffu);
+            if (out16) {
+                uint16_t* dst = out16 + static_cast<int64_t>(r) * ld16 + t;
+                if (t + 3 < T && (ld16 % 4 == 0)) {
+                    uint2 pk;
+                    pk.x = pack_bf16x2(vh[0], vh[1]);
+                    pk.y = pack_bf16x2(vh[2], vh[3]);
+                    *reinterpret_cast<uint2*>(dst) = pk;
+                } else {
+                    for (int j = 0; j < 4; ++j)
+                        if (t + j < T) dst[j] = static_cast<uint16_t>(pack_bf16x2(vh[j], 0.f) & 0xffffu);
+                }
             }
         }
     }
