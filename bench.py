@@ -340,8 +340,8 @@ def run_ours(args):
     # Dominant kernel: the persistent BF16 stage (one launch per component runs every iteration:
     # update, row completion, removal of converged rows), or the per-launch update kernel when
     # the stage ran per iteration. DRAM traffic per launch from ncu:
-    #   persistent: 25.96 MB read+written for component 3 (n_pad 64) against 25.6 MB of X~ (one
-    #     pass; later iterations re-read X~ from L2): 1.014 x n_pad T 2 bytes per launch;
+    #   persistent: 26.20 MB read+written for component 3 (n_pad 64) against 25.6 MB of X~ (one
+    #     pass; later iterations re-read X~ from L2): 1.023 x n_pad T 2 bytes per launch;
     #   per-launch: 259.6 MB for one launch at n = 64, M = 1024, T = 2e6 against 256.0 MB of X~:
     #     1.014 x the X~ bytes of every iteration.
     persistent = bool(stats) and stats[-1].get("stage_persistent_launches", 0) > 0
@@ -350,10 +350,11 @@ def run_ours(args):
         for comp in stats[-1].get("components", []):
             n_pad_c = (N - comp["i"] + 1 + 15) // 16 * 16
             xt_bytes += (1 if persistent else comp["iterations"]) * n_pad_c * T * 2.0
-    traffic = 1.014 * xt_bytes / max(1, it["launches"] / max(1, args.steps)) if xt_bytes else None
+    traffic = (1.023 if persistent else 1.014) * xt_bytes / max(1, it["launches"] / max(1, args.steps)) \
+        if xt_bytes else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": ("ncu dram read+write of one stage launch (n_pad 64, T 2e5) / its X~ bytes (1.014), "
+                "traffic_note": ("ncu dram read+write of one stage launch (n_pad 64, T 2e5) / its X~ bytes (1.023), "
                                  "times the fit's mean X~ bytes per launch" if persistent else
                                  "ncu dram read+write of one launch at n=64 M=1024 T=2e6 / algorithmic X~ bytes "
                                  "(1.014), times the fit's mean algorithmic bytes per launch"),
