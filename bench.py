@@ -190,6 +190,21 @@ def run_reference(args):
     return 0
 
 
+def aggregate_over_ranks(total_ms, flops, nominal, world, device):
+    """Whole-job figures of N replicas (one per rank, no exchange step): the time of the slowest
+    rank, FLOPs summed over the ranks. Needs an initialised process group when world > 1."""
+    if world <= 1:
+        return total_ms, flops, nominal
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([total_ms, flops, nominal], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1]), float(t[2])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -281,14 +296,7 @@ def run_ours(args):
             phases[k] = phases.get(k, 0.0) + v["ms"] / args.steps
 
     # whole-job aggregate over ranks: FLOPs summed, time = slowest rank
-    if world > 1:
-        t = torch.tensor([total_ms, flops, nominal], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, flops_all, nominal_all = float(tmax[0]), float(t[1]), float(t[2])
-    else:
-        total_ms_max, flops_all, nominal_all = total_ms, flops, nominal
+    total_ms_max, flops_all, nominal_all = aggregate_over_ranks(total_ms, flops, nominal, world, dev)
     tflops = flops_all / (total_ms_max / 1e3) / 1e12
 
     # e2e through the public API with host buffers: H2D of X (pinned), whiten + fit, D2H of W, kurt
