@@ -13,8 +13,10 @@
  *     workspace is set the library allocates no device memory (the optional plain FP32
  *     comparator creates a cuBLAS handle on first use, which allocates inside cuBLAS).
  *   - Work is enqueued on the context's stream (ica_set_stream). ica_order_fit synchronises
- *     that stream on a sparse schedule of iterations (it reads the active-restart count, every
- *     iteration at first, then every second and every fourth); ica_whiten,
+ *     that stream a few times per component: once after each persistent BF16 stage and FP32
+ *     refinement launch (opts.stage_persistent), otherwise on a sparse schedule of iterations
+ *     (it reads the active-restart count every fourth iteration on the BF16 path; every
+ *     iteration at first, then every second and every fourth on the FP32 path); ica_whiten,
  *     ica_deflation_basis, ica_fp_step and ica_kurtosis synchronise once at the end to read
  *     the device status word; ica_init_restarts and ica_reduce only enqueue.
  *   - The return value is an ica_status. Nothing is thrown across the ABI. After an error the
