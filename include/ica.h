@@ -98,11 +98,27 @@ typedef struct {
                               multi-worker ica_order_fit_batched) and M <= 152 * 128; 0 launches
                               the update and the row completion per iteration. Both give the
                               same results. */
+    int64_t wait_ns;       /* limit (ns) of every bounded wait of the persistent stage and
+                              refinement kernels (mbarrier waits, grid barriers); 0: 2 s. When it
+                              runs out the kernel stops, frees its resources and returns, and the
+                              call reports ICA_ERR_TIMEOUT. The per-launch kernels and every
+                              teardown drain keep the 2 s limit. */
+    int stall_test;        /* test hook, 0 in normal use: 1 makes the first grid barrier of the
+                              persistent stage wait for one arrival more than there are CTAs, so
+                              that its wait runs out (exercises the timeout path on the host's
+                              request, without a fault) */
+    double* record_cands;  /* optional (device, BF16 path): n_components x refine_topk x N FP64.
+                              Row (i, j) = w = G^T b of the j-th distinct candidate of component i
+                              after the FP32 refinement (Section 3.3: the candidate in the full
+                              whitened space), normalised; zero rows where fewer candidates
+                              were distinct. The pick of component i is among them. For an FP64
+                              re-check of the pick outside the library. */
 } ica_opts;
 
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
-   no profiling, no pruner (prune_tau 0.05), no recording. */
+   no profiling, no pruner (prune_tau 0.05), no recording, persistent stage, 2 s wait limit,
+   no stall. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */
@@ -208,20 +224,24 @@ int ica_kurtosis(ica_ctx* ctx, int precision, const float* B, int M, int n, cons
    device synchronisation. It needs no context and no workspace: the split-T partial sums live
    in a 16 MiB array inside this library (one per GPU that loads the library, held until the
    process exits). It calls no cudaMalloc, cudaFree or other allocating routine.
-   - The first call made with a given device current looks up that array's device address
-     (cudaGetSymbolAddress) and the tensor-map encoder; make that first call before any stream
-     capture that might include this entry point.
-   - Limit: M rows rounded up to the kernel's restart tile (128 for ICA_BF16, 64 for ICA_FP32)
-     times (round_up(n, 16) + 4) * 4 bytes must fit in 16 MiB less 256 bytes, i.e. about
-     16,000 rows at n = 256; beyond it the call returns ICA_ERR_WORKSPACE without launching
-     anything. Arguments outside ica_fp_step's range (M > 65536, ...) return ICA_ERR_ARG. Within the limit the sample range is split
-     into fewer pieces than ica_fp_step may use, so results can differ from it by FP32
+   - Device: the call works on the CUDA device that is current on the calling host thread. B,
+     Xt, Bnew, moments and the stream must belong to that device. The first call made with a
+     given device current looks up that device's copy of the array (cudaGetSymbolAddress) and
+     the tensor-map encoder.
+   - Limit: M rows rounded up to the kernel's row tile (128 for ICA_BF16; 4 or 16 for ICA_FP32
+     with M <= 16, else 64) times (round_up(n, 16) + 4) * 4 bytes must fit in 16 MiB less 256
+     bytes, i.e. about 16,000 rows at n = 256; beyond it the call returns ICA_ERR_WORKSPACE
+     without launching anything. Arguments outside ica_fp_step's range (M > 65536, ...) return
+     ICA_ERR_ARG. The call runs the kernels ica_fp_step runs, with the same split of the sample
+     range, so both give identical results, except when that split needs more than 16 MiB of
+     partial sums: then it uses fewer pieces and results can differ from ica_fp_step's by FP32
      summation order.
    - Every call on a device shares the same array and the array keeps the last call's contents
      (the call clears the status word it needs zeroed). Calls whose kernels overlap on the GPU
      (different streams, or different host threads) race on it: serialise them.
-   - stream: the cudaStream_t to enqueue on (NULL = legacy default stream); the call
-     synchronises it once at the end to read the status word. */
+   - stream: the cudaStream_t to enqueue on (NULL = legacy default stream). The call
+     synchronises that stream at the end and copies the status word to host memory, so it must
+     not be called while the stream is being captured into a CUDA graph. */
 int ica_fp_step_noalloc(int precision, const float* B, int M, int n, const void* Xt, int64_t T,
                         int64_t ldx, float* Bnew, float* moments, void* stream);
 

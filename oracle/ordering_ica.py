@@ -10,7 +10,7 @@ Every function follows a passage of the paper, cited by section, equation or alg
 paper writes samples as M and restarts as L; this file uses T for samples and M (or L inside
 the algorithm functions) for restarts, matching the library's argument names.
 
-Readings where the paper is silent or self-contradictory (each listed in the design doc):
+Readings where the paper is silent or self-contradictory:
 
 * convergence: a run has converged when min(||w - w_prev||, ||w + w_prev||) <= eps. The
   printed test in Algorithm 1 ("||w+w_prev|| > eps or ||w-w_prev|| > eps") can never fail for

@@ -39,6 +39,9 @@ class ica_opts(C.Structure):
         ("record_features", C.c_void_p),
         ("record_labels", C.c_void_p),
         ("stage_persistent", C.c_int),
+        ("wait_ns", C.c_int64),
+        ("stall_test", C.c_int),
+        ("record_cands", C.c_void_p),
     ]
 
 

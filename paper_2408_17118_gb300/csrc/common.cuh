@@ -75,17 +75,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the phase with the given parity. Returns false (and raises *abort and the
-// device status word) when the phase does not complete within ICA_WAIT_NS, or when another
-// role of the CTA has already aborted.
+// device status word) when the phase does not complete within limit_ns (ICA_WAIT_NS unless the
+// caller passes its run-time limit), or when another role of the CTA has already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status) {
+                                          int* status, uint64_t limit_ns = ICA_WAIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > ICA_WAIT_NS) {
+            if (global_ns() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicOr(status, DEV_TIMEOUT);
                 return false;

@@ -547,7 +547,7 @@ int ica_whiten(ica_ctx* c, const float* X, int N, int64_t T, float* Xw, double* 
     double *A = at<double>(c, L.jA), *E = at<double>(c, L.jV), *lam = at<double>(c, L.lam);
     double *T1 = at<double>(c, L.t1), *bias = at<double>(c, L.t2);
     const int splits = covariance_splits(N, T);
-    KL(launch_row_mean(s, X, N, T, T, mean));
+    KL(launch_row_mean(s, X, N, T, T, mean, status));
     KL(launch_covariance(s, X, mean, N, T, T, at<double>(c, L.cov_part), splits, A));
     ++c->launches;  // partial + reduce
     ++c->launches_total;
@@ -556,7 +556,11 @@ int ica_whiten(ica_ctx* c, const float* X, int N, int64_t T, float* Xw, double* 
     KL(launch_gemm_f64(s, N, N, N, 1.0, T1, N, 1, E, 1, N, 0.0, V, N));     // V = E diag(l^-1/2) E^T
     KL(launch_gemm_f64(s, N, 1, N, 1.0, V, N, 1, mean, 1, 1, 0.0, bias, 1));  // V mean
     KL(launch_rows_gemm(s, V, N, N, N, X, T, T, bias, Xw, T, nullptr, 0));
-    return read_status(c, L);
+    CK(cudaMemcpyAsync(c->host_i + 1, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // NaN or Inf in X also breaks the eigendecomposition: report the cause, not the symptom
+    if (c->host_i[1] & DEV_NONFINITE) return ICA_ERR_NONFINITE;
+    return map_device_status(c->host_i[1]);
 }
 
 int ica_init_restarts(ica_ctx* c, uint64_t seed, int component, int M, int n, float* B, int ldb) {
@@ -671,6 +675,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     const ica_opts o = opts ? *opts : d;
     if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_PLAIN_FP32) return ICA_ERR_UNSUPPORTED;
     if (o.precision == ICA_BF16 && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
+    if (o.wait_ns < 0 || (o.record_cands && o.precision != ICA_BF16)) return ICA_ERR_ARG;
     const Layout L = make_layout(N, T, M, o.precision);
     int rc = check_ws(c, L);
     if (rc) return rc;
@@ -842,6 +847,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     sl.t_end = t_end;
                     sl.inv_T = inv_T;
                     sl.tol = tol_iter;
+                    sl.wait_ns = static_cast<uint64_t>(o.wait_ns);
+                    sl.stall = o.stall_test != 0;
                     CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
                     cudaError_t le = cudaSuccess;
                     int resident = 0;
@@ -1009,6 +1016,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                 rl.t_end = refine_iters;
                 rl.inv_T = static_cast<float>(inv_T);
                 rl.tol = static_cast<float>(tol_ref);
+                rl.wait_ns = static_cast<uint64_t>(o.wait_ns);
                 CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
                 cudaError_t le = cudaSuccess;
                 int resident = 0;
@@ -1087,6 +1095,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, cand_list, counts + 2, k,
                                     inv_T, alpha, ups));
             KL(launch_argmax(s, ups, nullptr, cand_list, counts + 2, k, slots));
+            if (o.record_cands)
+                KL(launch_record_cands(s, G, n, N, B32, n_pad, cand, k, o.record_cands + static_cast<int64_t>(i) * k * N));
         }
         if (o.record_features && o.record_labels)
             KL(launch_record(s, traj, itc, B32, n_pad, n, M, slots, std::log(static_cast<double>(T)), uref,

@@ -69,9 +69,12 @@ cudaError_t launch_exclude(cudaStream_t s, const float* B32, int ldb, int n, int
 cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
                           const int* p_slot, const double* alpha, const double* ups, double* W, int i,
                           double* kurt_out, double* comp_stats);
+cudaError_t launch_record_cands(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
+                                const int* cand, int k, double* out);
 
 // ---- k_linalg.cu ----
-cudaError_t launch_row_mean(cudaStream_t s, const float* X, int N, int64_t T, int64_t ld, double* mean);
+cudaError_t launch_row_mean(cudaStream_t s, const float* X, int N, int64_t T, int64_t ld, double* mean,
+                            int* status = nullptr);
 cudaError_t launch_covariance(cudaStream_t s, const float* X, const double* mean, int N, int64_t T,
                               int64_t ld, double* part, int splits, double* C);
 int covariance_splits(int N, int64_t T);
@@ -186,6 +189,8 @@ struct StageLaunch {
     int* ctl;
     int t_begin, t_end;
     double inv_T, tol;
+    uint64_t wait_ns;  // limit of the kernel's waits (0: ICA_WAIT_NS); its teardown drains keep ICA_WAIT_NS
+    int stall;         // test hook: 1 makes the first grid barrier wait for an arrival that never comes
 };
 // resident (optional) receives the number of CTAs of the kernel that fit the GPU at once.
 cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident = nullptr);
@@ -218,6 +223,7 @@ struct RefineLaunch {
     int* ctl;
     int t_begin, t_end;
     float inv_T, tol;
+    uint64_t wait_ns;  // limit of the grid barriers (0: ICA_WAIT_NS)
 };
 cudaError_t launch_refine_fp32(cudaStream_t s, const RefineLaunch& p, int* resident = nullptr);
 

@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(256, 2) refine_fp32_kernel(RefineLaunch a, int
         rows_update<R, false>(a.B32, a.ldb, act, M_act, a.Xt, a.ldx, a.n_pad, a.T, chunks_per_split, bid, a.part_acc,
                               a.part_mom, R, rsm);
         target += static_cast<unsigned int>(G);
-        if (!grid_barrier(a.bar_ctr, target, abort_flag, a.status)) break;
+        if (!grid_barrier(a.bar_ctr, target, abort_flag, a.status, a.wait_ns ? a.wait_ns : ICA_WAIT_NS)) break;
         if (bid < M_act) {  // row j = bid
             const int j = bid;
             int r = 0;
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256, 2) refine_fp32_kernel(RefineLaunch a, int
             }
         }
         target += static_cast<unsigned int>(G);
-        if (!grid_barrier(a.bar_ctr, target, abort_flag, a.status)) break;
+        if (!grid_barrier(a.bar_ctr, target, abort_flag, a.status, a.wait_ns ? a.wait_ns : ICA_WAIT_NS)) break;
         compact_block(a.flags, act, M_act, cur ? a.act0 : a.act1, &new_count, bid == 0 ? a.rows_accum : nullptr, 256);
         __syncthreads();
         const int M_new = *reinterpret_cast<volatile int*>(&new_count);

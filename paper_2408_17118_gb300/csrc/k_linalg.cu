@@ -9,8 +9,10 @@
 namespace ica {
 
 // ------------------------------------------------------------------------------ row means
+// Row means in FP64. A row holding NaN or Inf makes its sum non-finite: DEV_NONFINITE is raised
+// (status may be null).
 __global__ void __launch_bounds__(256) row_mean_kernel(const float* __restrict__ X, int N, int64_t T, int64_t ld,
-                                                       double* __restrict__ mean) {
+                                                       double* __restrict__ mean, int* status) {
     __shared__ double red[8];
     const int r = blockIdx.x;
     double s = 0.0;
@@ -22,10 +24,11 @@ __global__ void __launch_bounds__(256) row_mean_kernel(const float* __restrict__
         double tot = 0.0;
         for (int i = 0; i < 8; ++i) tot += red[i];
         mean[r] = tot / static_cast<double>(T);
+        if (!isfinite(tot) && status) atomicOr(status, DEV_NONFINITE);
     }
 }
-cudaError_t launch_row_mean(cudaStream_t s, const float* X, int N, int64_t T, int64_t ld, double* mean) {
-    row_mean_kernel<<<N, 256, 0, s>>>(X, N, T, ld, mean);
+cudaError_t launch_row_mean(cudaStream_t s, const float* X, int N, int64_t T, int64_t ld, double* mean, int* status) {
+    row_mean_kernel<<<N, 256, 0, s>>>(X, N, T, ld, mean, status);
     return cudaGetLastError();
 }
 

@@ -528,4 +528,35 @@ cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const f
     return cudaGetLastError();
 }
 
+// Candidates of component i in the full whitened space (Section 3.3: w = G^T b), one block per
+// slot j < k: the refined restart row b_r (r = cand[j]) normalised in FP64, w = G^T b normalised,
+// written to out[j * N ..]; a zero row when the slot is empty (cand[j] < 0).
+__global__ void __launch_bounds__(256) record_cands_kernel(const double* __restrict__ G, int n, int N,
+                                                           const float* __restrict__ B32, int ldb,
+                                                           const int* __restrict__ cand, double* __restrict__ out) {
+    __shared__ double b[kMaxN];
+    __shared__ double red[8];
+    const int j = blockIdx.x, t = threadIdx.x;
+    const int r = cand[j];
+    double* row = out + static_cast<int64_t>(j) * N;
+    if (r < 0) {
+        if (t < N) row[t] = 0.0;
+        return;
+    }
+    const double v = t < n ? static_cast<double>(B32[static_cast<int64_t>(r) * ldb + t]) : 0.0;
+    const double ss = block_sum256(v * v, red);
+    if (t < n) b[t] = v / sqrt(ss);
+    __syncthreads();
+    double acc = 0.0;
+    if (t < N)
+        for (int l = 0; l < n; ++l) acc += b[l] * G[static_cast<int64_t>(l) * N + t];
+    const double nn = block_sum256(t < N ? acc * acc : 0.0, red);
+    if (t < N) row[t] = acc / sqrt(nn);
+}
+cudaError_t launch_record_cands(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
+                                const int* cand, int k, double* out) {
+    record_cands_kernel<<<k, 256, 0, s>>>(G, n, N, B32, ldb, cand, out);
+    return cudaGetLastError();
+}
+
 }  // namespace ica

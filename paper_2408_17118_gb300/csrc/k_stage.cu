@@ -49,6 +49,8 @@ struct StageArgs {
     int* ctl;               // out: iteration index reached, final active count, final list index
     int t_begin, t_end;
     float inv_T, tol;
+    uint64_t wait_ns;  // limit of every wait except the teardown drains
+    unsigned int stall;  // test hook: arrivals the grid barriers expect beyond the CTAs (0)
     int stages;
     uint32_t a_bytes, xsub_bytes, xstage_bytes, off_x, off_p, off_bar;
 };
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                     for (int c = 0; c < nch; ++c) {
                         const uint32_t s = pc % stages;
                         if (pc >= stages &&
-                            !mbar_wait(&empty[s], ((pc / stages) - 1u) & 1u, abort_flag, a.status))
+                            !mbar_wait(&empty[s], ((pc / stages) - 1u) & 1u, abort_flag, a.status, a.wait_ns))
                             break;
                         mbar_arrive_expect_tx(&full[s], a.xstage_bytes);
                         const int tg = (c_begin + c) * TC;
@@ -223,9 +225,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                     const int ksteps1 = a.n_pad / 16;
                     for (int c = 0; c < nch; ++c) {
                         const uint32_t s = g1c % stages, b = g1c % NB;
-                        bool ok = mbar_wait(&full[s], (g1c / stages) & 1u, abort_flag, a.status);
+                        bool ok = mbar_wait(&full[s], (g1c / stages) & 1u, abort_flag, a.status, a.wait_ns);
                         if (ok && g1c >= static_cast<uint32_t>(NB))
-                            ok = mbar_wait(&d1_empty[b], ((g1c - NB) / NB) & 1u, abort_flag, a.status);
+                            ok = mbar_wait(&d1_empty[b], ((g1c - NB) / NB) & 1u, abort_flag, a.status, a.wait_ns);
                         if (!ok) break;
                         tc_fence_after();
                         const uint32_t d1 = tmem + kD1Col + b * TC;
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                     bool ok = true;
                     for (int c = 0; c < nch; ++c) {
                         const uint32_t b = g2c % NB, s = g2c % stages;
-                        ok = mbar_wait(&p_full[b], (g2c / NB) & 1u, abort_flag, a.status);
+                        ok = mbar_wait(&p_full[b], (g2c / NB) & 1u, abort_flag, a.status, a.wait_ns);
                         if (!ok) break;
                         tc_fence_after();
                         const uint64_t po = static_cast<uint64_t>((b * p_bytes) >> 4);
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                     const uint32_t g = ec + static_cast<uint32_t>(c);
                     if (static_cast<int>(g & 1u) != team) continue;
                     const uint32_t b = g % NB;
-                    ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], (g / NB) & 1u, abort_flag, a.status));
+                    ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], (g / NB) & 1u, abort_flag, a.status, a.wait_ns));
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t pbase = sP + b * p_bytes;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             // P[b] is free once the second product of chunk g - NB retired
                             const uint32_t cr = g - NB;
                             ok = __all_sync(0xffffffffu,
-                                            mbar_wait(&empty[cr % stages], (cr / stages) & 1u, abort_flag, a.status));
+                                            mbar_wait(&empty[cr % stages], (cr / stages) & 1u, abort_flag, a.status, a.wait_ns));
                             if (!ok) break;
                         }
 #pragma unroll
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 const int grow = m0 + row;
                 const int64_t prow = static_cast<int64_t>(split) * part_rows + grow;
                 if (ok && h < 2) {  // accumulator read-out: two warps per lane quarter
-                    ok = __all_sync(0xffffffffu, mbar_wait(d2_full, d2n & 1u, abort_flag, a.status));
+                    ok = __all_sync(0xffffffffu, mbar_wait(d2_full, d2n & 1u, abort_flag, a.status, a.wait_ns));
                     if (ok) {
                         tc_fence_after();
                         const int half = a.n_pad / 2;
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         // ---------------------------------------------------------------- finish the rows
         tc_fence_before();
         bar_target += static_cast<unsigned int>(G);
-        if (!grid_barrier(a.bar_ctr, bar_target, abort_flag, a.status)) break;
+        if (!grid_barrier(a.bar_ctr, bar_target + a.stall, abort_flag, a.status, a.wait_ns)) break;
         tc_fence_after();
         if (warp < 16) {  // groups of R warps, one row per group and round (fin_vwarps)
             const int R = fin_vwarps(M_act, G), ngrp = 16 / R;
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 group_finish_row(a, act, j, sp, part_rows, t, red, R, gw, 2 + grp);
         }
         bar_target += static_cast<unsigned int>(G);
-        if (!grid_barrier(a.bar_ctr, bar_target, abort_flag, a.status)) break;
+        if (!grid_barrier(a.bar_ctr, bar_target + a.stall, abort_flag, a.status, a.wait_ns)) break;
         // ---------------------------------------------------------------- remove converged rows
         compact_block(a.flags, act, M_act, cur ? a.act[0] : a.act[1], new_count, bid == 0 ? a.rows_accum : nullptr, kThreads);
         __syncthreads();
@@ -512,6 +514,8 @@ static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, co
     a.t_end = p.t_end;
     a.inv_T = static_cast<float>(p.inv_T);
     a.tol = static_cast<float>(p.tol);
+    a.wait_ns = p.wait_ns ? p.wait_ns : ICA_WAIT_NS;
+    a.stall = p.stall ? 1u : 0u;
     a.stages = static_cast<int>(L.stages);
     a.a_bytes = L.a_bytes;
     a.xsub_bytes = L.xsub_bytes;

@@ -60,13 +60,18 @@ int scratch_for_current_device(unsigned char** out) {
     return ICA_OK;
 }
 
-// Split of the sample range that keeps splits * rows * (n_pad + 4) floats inside the scratch.
-int splits_within(int64_t total_chunks, int tiles, int rows_per_tile, int n_pad, int target_ctas, int* splits,
-                  int* cps) {
-    const size_t per_split = sizeof(float) * static_cast<size_t>(tiles) * rows_per_tile * (n_pad + 4);
+// Split of the sample range with the rule ica_fp_step uses, then capped so that
+// splits * part_rows * (n_pad + 4) floats fit in the scratch. one_wave (the BF16 kernel, which
+// holds all 512 TMEM columns and so runs one CTA per SM): at most target_ctas CTAs, never a
+// partial second wave; otherwise about target_ctas CTAs, rounded up.
+int splits_within(int64_t total_chunks, int tiles, int part_rows, int n_pad, int target_ctas, bool one_wave,
+                  int* splits, int* cps) {
+    const size_t per_split = sizeof(float) * static_cast<size_t>(part_rows) * (n_pad + 4);
     const size_t cap = (kNoallocScratchBytes - kStatusBytes) / per_split;
     if (cap < 1) return ICA_ERR_WORKSPACE;
-    int64_t s = (target_ctas + tiles - 1) / tiles;
+    int64_t s = one_wave ? (tiles <= target_ctas ? target_ctas / tiles : 1) : (target_ctas + tiles - 1) / tiles;
+    const int64_t cta_cap = kMaxCTAs / tiles > 0 ? kMaxCTAs / tiles : 1;
+    if (s > cta_cap) s = cta_cap;
     if (s > static_cast<int64_t>(cap)) s = static_cast<int64_t>(cap);
     if (s > total_chunks) s = total_chunks;
     if (s < 1) s = 1;
@@ -85,19 +90,23 @@ extern "C" int ica_fp_step_noalloc(int precision, const float* B, int M, int n, 
     if (precision != ICA_FP32 && precision != ICA_BF16) return ICA_ERR_UNSUPPORTED;
     const int n_pad = round_up(n, 16);
     const bool bf16 = precision == ICA_BF16;
-    const int rows_per_tile = bf16 ? kTcRows : kFp32Rows;
+    // the kernel and launch shape ica_fp_step takes for these sizes: 128-row tcgen05 tiles in one
+    // wave (BF16), the few-row FP32 kernel for at most kFp32SmallRows rows, 64-row FP32 tiles
+    const bool few_rows = !bf16 && M <= kFp32SmallRows;
+    const int rows_per_tile = bf16 ? kTcRows : (few_rows ? fp32_rows_tile(M) : kFp32Rows);
     const int tiles = (M + rows_per_tile - 1) / rows_per_tile;
-    const int chunk = bf16 ? tc_chunk(n_pad) : 64;
+    const int chunk = bf16 ? tc_chunk(n_pad) : (few_rows ? fp32_rows_chunk(n_pad) : 64);
     const int64_t total = (T + chunk - 1) / chunk;
+    const int part_rows = tiles * rows_per_tile;
     int splits = 1, cps = 1;
-    int rc = splits_within(total, tiles, rows_per_tile, n_pad, bf16 ? 2 * 152 : 4 * 152, &splits, &cps);
-    if (rc) return rc;  // M * (n_pad + 4) * 4 bytes do not fit in the 16 MiB scratch
+    int rc = splits_within(total, tiles, part_rows, n_pad, bf16 ? 152 : (few_rows ? 2 * 152 : 4 * 152), bf16,
+                           &splits, &cps);
+    if (rc) return rc;  // one split of M * (n_pad + 4) * 4 bytes does not fit in the 16 MiB scratch
     unsigned char* base = nullptr;
     rc = scratch_for_current_device(&base);
     if (rc) return rc;
     if (bf16 && !g_encode) return ICA_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int part_rows = tiles * rows_per_tile;
     int* status = reinterpret_cast<int*>(base);
     float* part_mom = reinterpret_cast<float*>(base + kStatusBytes);
     float* part_acc = part_mom + static_cast<size_t>(splits) * part_rows * 4;
@@ -116,6 +125,9 @@ extern "C" int ica_fp_step_noalloc(int precision, const float* B, int M, int n, 
             return ICA_ERR_CUDA;
         e = launch_fused_tc(s, false, true, map, nullptr, B, n_pad, nullptr, nullptr, M, n_pad, T, splits, cps,
                             static_cast<int>(total), part_acc, part_mom, part_rows, status);
+    } else if (few_rows) {
+        e = launch_fused_fp32_rows(s, false, B, n_pad, nullptr, nullptr, M, static_cast<const float*>(Xt), ldx, n_pad,
+                                   T, splits, cps, part_acc, part_mom, part_rows);
     } else {
         e = launch_fused_fp32(s, false, B, n_pad, nullptr, nullptr, M, static_cast<const float*>(Xt), ldx, n_pad, T,
                               splits, cps, part_acc, part_mom, part_rows);

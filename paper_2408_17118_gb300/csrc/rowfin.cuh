@@ -165,9 +165,10 @@ __device__ __forceinline__ void row_combine(const float* red, int V, int n_pad, 
 
 // Grid-wide barrier over the CTAs of a cooperative launch: arrival counter with release (fence +
 // red.release) and a bounded acquire spin by one thread. `target` is the number of arrivals of all
-// barriers so far. Returns false (and raises the abort flag) on timeout.
+// barriers so far. Returns false (and raises the abort flag) when the arrivals do not reach the
+// target within limit_ns.
 __device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int target, volatile int* abort_flag,
-                                             int* status) {
+                                             int* status, uint64_t limit_ns = ICA_WAIT_NS) {
     __syncthreads();
     if (threadIdx.x == 0) {
         if (!*abort_flag) {
@@ -178,7 +179,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* ctr, unsigned int tar
                 unsigned int seen;
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(ctr) : "memory");
                 if (seen >= target) break;
-                if ((it & 15u) == 15u && global_ns() - t0 > ICA_WAIT_NS) {
+                if ((it & 15u) == 15u && global_ns() - t0 > limit_ns) {
                     atomicOr(status, DEV_TIMEOUT);
                     *abort_flag = 1;
                     break;

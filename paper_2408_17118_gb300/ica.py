@@ -107,10 +107,13 @@ def ica_whiten(ctx: Context, X: torch.Tensor, Xw: torch.Tensor | None = None):
 
 def ica_order_fit(ctx: Context, Xw: torch.Tensor, M: int, n_components: int, iters: int, tol: float, seed: int,
                   opts: ica_opts | None = None, B0: torch.Tensor | None = None,
-                  prune_params: torch.Tensor | None = None, record: bool = False):
+                  prune_params: torch.Tensor | None = None, record: bool = False,
+                  record_cands: torch.Tensor | None = None):
     """Fast ordering ICA on whitened Xw (N x T float32). Returns (W float64 n_found x N,
-    kurtosis float64 n_found); with record=True also (features n_components x M x 12,
-    labels n_components x M) for training the restart pruner."""
+    kurtosis float64 n_found); with record=True also (features n_components x M x ICA_MLP_IN,
+    labels n_components x M) for training the restart pruner. record_cands (optional, float64
+    n_components x refine_topk x N, BF16 precision) receives each component's refined distinct
+    candidates in the whitened space."""
     N, T = Xw.shape
     opts = ica_default_opts() if opts is None else opts
     if B0 is not None:
@@ -127,6 +130,10 @@ def ica_order_fit(ctx: Context, Xw: torch.Tensor, M: int, n_components: int, ite
                torch.zeros((n_components, M), dtype=torch.float32, device=Xw.device))
         opts.record_features = rec[0].data_ptr()
         opts.record_labels = rec[1].data_ptr()
+    if record_cands is not None:
+        if tuple(record_cands.shape) != (n_components, opts.refine_topk, N):
+            raise ValueError("record_cands must be n_components x refine_topk x N")
+        opts.record_cands = _ptr(record_cands, torch.float64, "record_cands")
     ctx.ensure_workspace(N, T, M, opts)
     W = torch.zeros((n_components, N), dtype=torch.float64, device=Xw.device)
     kurt = torch.zeros(n_components, dtype=torch.float64, device=Xw.device)
@@ -250,11 +257,14 @@ def ica_fp_step_noalloc(precision: int, B: torch.Tensor, n: int, Xt: torch.Tenso
     convenience - a C caller passes its own."""
     M, n_pad = B.shape
     xp, ldx = _xt_args(Xt, precision)
+    if Xt.device != B.device:
+        raise ValueError("B and Xt must be on the same device")
     stream = torch.cuda.current_stream(B.device) if stream is None else stream
     Bnew = torch.empty_like(B)
     mom = torch.empty((M, 4), dtype=torch.float32, device=B.device)
-    _check(_lib.load().ica_fp_step_noalloc(precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(Bnew),
-                                           _ptr(mom), C.c_void_p(stream.cuda_stream)), "ica_fp_step_noalloc")
+    with torch.cuda.device(B.device):  # the C call works on the current device
+        _check(_lib.load().ica_fp_step_noalloc(precision, _ptr(B, torch.float32, "B"), M, n, xp, T, ldx, _ptr(Bnew),
+                                               _ptr(mom), C.c_void_p(stream.cuda_stream)), "ica_fp_step_noalloc")
     return Bnew, mom
 
 

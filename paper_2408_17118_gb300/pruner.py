@@ -17,7 +17,7 @@ from . import ica
 
 def collect(ctx: ica.Context, datasets, M: int, iters: int, tol: float, seed: int, opts=None):
     """Record (features, labels) of every restart of every component of each whitened data set
-    (a list of N x T float32 CUDA tensors). Returns (F rows x 12, y rows) on the device."""
+    (a list of N x T float32 CUDA tensors). Returns (F rows x ICA_MLP_IN, y rows) on the device."""
     Fs, ys = [], []
     for k, Xw in enumerate(datasets):
         N = Xw.shape[0]

@@ -42,13 +42,22 @@ def gpu_fit(ctx, w, prec, B0=None, seed=0, gauss=False, iters=None, tol=None, **
     return W.cpu().numpy(), kurt.cpu().numpy(), Xw, V.cpu().numpy()
 
 
+def sign_near_tie(w, rel=1e-4):
+    """The two largest magnitudes of w agree to `rel`: the canonical sign (largest-magnitude
+    entry positive) is then decided by rounding and may differ between two correct fits."""
+    a = np.sort(np.abs(w))[::-1]
+    return len(a) > 1 and a[0] - a[1] <= rel * a[0]
+
+
 def check_parity(W, kurt, ref, label):
     assert W.shape == ref.W.shape, (label, W.shape, ref.W.shape)
     assert np.abs(W @ W.T - np.eye(W.shape[0])).max() < 1e-12, label
-    cos = np.abs(np.sum(W * ref.W, axis=1))
+    cos = np.sum(W * ref.W, axis=1)  # signed: both sides make the largest-magnitude entry positive
     ups = oracle.upsilon(ref.alpha)
     margin = np.abs(np.diff(ups)) if len(ups) > 1 else np.array([np.inf])
-    assert np.all(cos >= 1 - 1e-5), (label, "cos", cos, "oracle Upsilon margins", margin)
+    assert np.all(np.abs(cos) >= 1 - 1e-5), (label, "cos", cos, "oracle Upsilon margins", margin)
+    flipped = [i for i in range(len(cos)) if cos[i] < 0]
+    assert all(sign_near_tie(ref.W[i]) for i in flipped), (label, "sign differs", flipped)
     rel = np.abs(kurt - ref.alpha) / np.abs(ref.alpha)
     assert np.all(rel <= 1e-4), (label, "rel kurtosis error", rel)
 
@@ -152,7 +161,32 @@ def test_full_size_eeg_like_sampled(ctx):
         assert oracle.upsilon(oracle.kurtosis_alpha(yl)) <= ups0 + 1e-6, l
 
 
-@pytest.mark.parametrize("case", ["small", "eeg32", "ragged"])
+@pytest.mark.parametrize("N,T,M,ncomp,seed", [(80, 12_003, 300, 5, 85), (128, 16_001, 300, 6, 129),
+                                              (136, 12_345, 130, 6, 136), (256, 12_007, 130, 5, 256)])
+def test_wide_stage_parity(ctx, N, T, M, ncomp, seed):
+    """Reduced dimensions above 64: the persistent BF16 stage takes its 128-sample-chunk form
+    (n_pad 80 and 128) and its 64-sample-chunk form with a 256-column accumulator (n_pad 144 and
+    256); whitening runs the FP64 Jacobi at m = N. EEG-like mixtures (the workload's source mix
+    and noise), ragged T and restart tiles. Same bar as the small case against the FP64 oracle."""
+    import json
+
+    from paper_2408_17118_gb300 import ica
+
+    # seeds whose oracle winners are each reached by many restarts (at these small T a winner
+    # reached by a single restart is common, and its trajectory may leave the basin under BF16
+    # rounding: a different, equally valid pick rather than an error of the kernels)
+    w = synth.eeg_like(N, T, M, seed=seed, iters=100, tol=1e-8, n_components=ncomp)
+    B0 = synth.restart_inits(M, N, ncomp, 13 + seed)
+    ref, _, _, _ = oracle.order_fit(w.X, M, ncomp, 100, 1e-8, B0)
+    W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, B0=B0)
+    st = json.loads(ica.ica_last_stats(ctx))
+    assert st["stage_persistent_launches"] >= ncomp, st["stage_persistent_note"]
+    check_parity(W, kurt, ref, f"N{N} T{T} M{M} bf16")
+    W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_FP32, B0=B0)
+    check_parity(W, kurt, ref, f"N{N} T{T} M{M} fp32")
+
+
+@pytest.mark.parametrize("case", ["small", "eeg32", "ragged", "wide100", "wide200"])
 def test_persistent_stage_equals_per_launch(ctx, case):
     """The persistent cooperative BF16 stage (one launch per component: update, grid barrier,
     row completion, grid barrier, removal of converged rows) runs the same arithmetic as the
@@ -167,8 +201,12 @@ def test_persistent_stage_equals_per_launch(ctx, case):
         w = synth.small_mixture(0)
     elif case == "eeg32":
         w = synth.eeg_like(32, 50_000, 512, seed=4)
-    else:
+    elif case == "ragged":
         w = synth.eeg_like(21, 9_999, 300, seed=5)  # ragged n, T and M
+    elif case == "wide100":  # n_pad 112 .. 96: 128-sample chunks, two second-product issuers
+        w = synth.eeg_like(100, 20_000, 300, seed=6, n_components=8)
+    else:  # n_pad 208: 64-sample chunks, one issuer, 256-column accumulator
+        w = synth.eeg_like(200, 12_000, 200, seed=7, n_components=4)
     out = []
     for persistent in (1, 0):
         W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, seed=7, stage_persistent=persistent)
