@@ -1,23 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the fast ordering ICA hot path on GB300: time to all components and
-algorithmic TFLOP/s (BF16 fused tcgen05 path), with the plain FP32 matrix form (cuBLAS SGEMM,
-Z in device memory) timed beside it on the same GPU and the FP64 CPU oracle as a baseline.
+algorithmic TFLOP/s of the BF16 fused tcgen05 path with the learned restart pruner (the
+headline), beside the same path without the pruner and the plain FP32 matrix form (cuBLAS
+SGEMM, Z in device memory) on the same GPU, and the FP64 CPU oracle as a baseline.
 
 One step = one whole fit of one synthetic data set: whitening (ica_whiten) plus every
 component (ica_order_fit), inputs resident in device memory when the timed region starts.
-Default workload: EEG-like mixture, N = 64 channels, T = 200,000 samples, M = 1024 restarts,
-all 64 components, at most 30 fixed-point iterations, tolerance 1e-6.
+Default workload: EEG-like mixture, N = 256 channels, T = 1,000,000 samples, M = 8192
+restarts, all 256 components, at most 30 fixed-point iterations, tolerance 1e-6 (--config
+eeg128: N = 128, T = 500,000, M = 4096; eeg64: N = 64, T = 200,000, M = 1024).
 
 Algorithmic FLOPs: 4 n M_act T per fused update of M_act active restarts on n reduced
-dimensions (two products of n x T per restart), 2 n M T per kurtosis pass, summed over every
-launch the fit made (counted by the library). `nominal_tflops` uses the fixed 4 N M T per
-iteration instead.
+dimensions (two products of n x T per restart; the rows actually updated, counted on the
+device), 2 n M T per kurtosis pass, summed over the fit. `nominal_tflops` uses the fixed
+4 N M T per iteration instead.
+
+The pruner (a 13-64-64-1 network, not part of the paper) is trained untimed, by the library's
+own kernels, on restart trajectories the method records on workloads shaped like the small
+N = 8 mixture and the EEG-like N = 64 and N = 128 cases (other seeds than the timed data).
 
 Multi-GPU (torchrun): every rank fits its own data set (weak scaling, replicas: the fit has
 no exchange step); value = all ranks' FLOPs / the slowest rank's time.
 
 --impl reference: the FP64 CPU oracle (Algorithm 2 in numpy) timed on the host cores on a
-bounded sample of the same workload (whitening + first component, 256 of the restarts), same metric.
+bounded sample of the same workload (whitening + first component with a subset of the
+restarts), same metric.
 """
 from __future__ import annotations
 
@@ -37,20 +44,29 @@ if ROOT not in sys.path:
 
 METRIC = "time-to-all-components & TFLOP/s, BF16 fused+pruned vs plain FP32, same GB300"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# restarts of the bounded oracle sample (whitening + component 1 at full T) per workload
+ORACLE_RESTARTS = {"small": 64, "eeg64": 256, "eeg128": 64, "eeg256": 16}
+# ncu DRAM bytes (read + write) of one persistent stage launch divided by its algorithmic X~
+# bytes (n_pad T 2, one pass), per workload, from the capture of the current kernel
+# (profiles/); None where no capture of the current kernel exists
+STAGE_TRAFFIC_RATIO = {}
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["small", "eeg64", "eeg128", "eeg256", "batch"], default="eeg64")
+    ap.add_argument("--config", choices=["small", "eeg64", "eeg128", "eeg256", "batch"], default="eeg256")
     ap.add_argument("--workers", type=int, default=8, help="concurrent fits of --config batch")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-prune", action="store_true", help="skip the learned-pruner leg")
+    ap.add_argument("--no-prune", action="store_true", help="headline without the learned pruner")
+    ap.add_argument("--side-steps", type=int, default=2, help="timed steps of the unpruned and e2e legs")
+    ap.add_argument("--certify", type=int, default=0, metavar="K",
+                    help="FP64 certification (oracle.certify_picks) of the first K components of one extra fit")
     ap.add_argument("--kernel-step", type=int, default=0, metavar="T",
                     help="instead of fits: time ica_fp_step (BF16) at the workload's N and M on T random "
                          "samples (used for ncu captures of the fused kernel on data larger than L2)")
@@ -169,12 +185,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = workload(args.config, args.seed)
+    R = ORACLE_RESTARTS.get(args.config, 64)
     for _ in range(args.warmup):
-        oracle_sample(w, 256)
+        oracle_sample(w, R)
     times, flops = [], 0.0
     desc = ""
     for _ in range(args.steps):
-        dt, fl, desc = oracle_sample(w, 256)
+        dt, fl, desc = oracle_sample(w, R)
         times.append(dt)
         flops += fl
     tflops = flops / sum(times) / 1e12
@@ -205,6 +222,71 @@ def aggregate_over_ranks(total_ms, flops, nominal, world, device):
     return float(tmax[0]), float(t[1]), float(t[2])
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+def train_pruner(ctx, dev, seed: int):
+    """The learned restart pruner, trained untimed on the method's own restart trajectories from
+    workloads shaped like the small N = 8 mixture and the EEG-like N = 64 and N = 128 cases
+    (seeds disjoint from the timed data). Returns (params, tau, report)."""
+    import torch
+
+    import synth
+    from paper_2408_17118_gb300 import ica
+    from paper_2408_17118_gb300 import pruner as pr
+
+    t0 = time.perf_counter()
+    shapes = [synth.small_mixture(seed + 101, iters=30, tol=1e-6), synth.eeg64(seed + 102), synth.eeg128(seed + 103)]
+    sets = [(ica.ica_whiten(ctx, torch.from_numpy(w.X).to(dev))[0], w.M) for w in shapes]
+    F, y = pr.collect_sets(ctx, sets, 30, 1e-6, seed=4321)
+    t_col = time.perf_counter() - t0
+    params, tau, report = pr.train(ctx, F, y, steps=400, recall=0.99)
+    report["collect_seconds"] = t_col
+    report["collect_and_train_seconds"] = time.perf_counter() - t0
+    report["trained_on"] = [f"N={w.N} T={w.T} M={w.M}" for w in shapes]
+    return params, tau, report
+
+
+def upsilon64(w, Xw_host):
+    """Eq. 1 of the kurtosis (Eq. 2) of y = w Xw in FP64 (host, chunks of samples)."""
+    import numpy as np
+
+    T = Xw_host.shape[1]
+    s4 = 0.0
+    for t0 in range(0, T, 1 << 18):
+        y = w @ Xw_host[:, t0:t0 + (1 << 18)].astype(np.float64)
+        y2 = y * y
+        s4 += float(np.sum(y2 * y2))
+    a = s4 / T - 3.0
+    return a - 2.0 * math.log(a / 2.0 + 1.0) if a > -2.0 else math.inf
+
+
+def judge_same_components(Wu, Wp, Xw_host):
+    """The pruner's judge: the pruned fit must pick the unpruned fit's components, in order.
+    Components are compared in order while both fits agree (|w_u . w_p| >= 1 - 1e-5); at the first
+    difference the two picks (same earlier components) are compared by their FP64 objective
+    Upsilon: a pruned pick worse by more than the FP32 error of Upsilon (1e-4 relative) fails the
+    judge, a difference within it is a tie that FP32 cannot order (after it the deflation
+    subspaces differ and the remaining components are not compared)."""
+    import numpy as np
+
+    n = min(len(Wu), len(Wp))
+    for i in range(n):
+        if abs(float(Wu[i] @ Wp[i])) >= 1 - 1e-5:
+            continue
+        uu, up = upsilon64(Wu[i], Xw_host), upsilon64(Wp[i], Xw_host)
+        tol = 1e-4 * max(1.0, abs(uu))
+        return {"components": n, "agree_prefix": i, "first_difference": i + 1, "ups_unpruned": uu, "ups_pruned": up,
+                "tie": abs(up - uu) <= tol, "pruned_not_worse": up >= uu - tol,
+                "ok": bool(up >= uu - tol)}
+    return {"components": n, "agree_prefix": n, "first_difference": None, "ok": len(Wu) == len(Wp)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -229,39 +311,26 @@ def run_ours(args):
     X_host = torch.from_numpy(w.X).pin_memory()
     X = X_host.to(dev)
     ctx = ica.Context(local)
-    opts = ica.ica_default_opts(precision=ica.ICA_BF16)               # timed steps: no per-launch events
-    opts_prof = ica.ica_default_opts(precision=ica.ICA_BF16, profile=1)  # separate pass: per-kernel times
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
+    seed_fit = 1234 + rank
 
-    def step(o=opts, prune=None):
-        Xw, V, mean = ica.ica_whiten(ctx, X)
-        W, kurt = ica.ica_order_fit(ctx, Xw, M, K, w.iters, w.tol, 1234 + rank, o, prune_params=prune)
-        return W, kurt
+    prune = not args.no_prune
+    params, tau, train_report = None, None, None
+    log(f"workload {w.name} ready")
+    if prune:
+        params, tau, train_report = train_pruner(ctx, dev, args.seed)
+        log(f"pruner trained: {train_report}")
+    # headline: BF16 (+ pruner); profile = 1 records CUDA events around each stage launch on the
+    # library's stream inside the timed steps (the roofline's kernel time)
+    opts_head = ica.ica_default_opts(precision=ica.ICA_BF16, profile=1)
+    if prune:
+        opts_head.prune_tau = tau
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    launches0 = json.loads(ica.ica_last_stats(ctx))["launches_total"]
-
-    sampler = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    step_ms, stats = [], []
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flushed between timed steps (outside the events)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        W, kurt = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        stats.append(json.loads(ica.ica_last_stats(ctx)))
-    barrier()
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    launches = stats[-1]["launches_total"] - launches0
+    def fit(o, pp, Xd=X):
+        Xw, V, mean = ica.ica_whiten(ctx, Xd)
+        W, kurt = ica.ica_order_fit(ctx, Xw, M, K, w.iters, w.tol, seed_fit, o, prune_params=pp)
+        return W, kurt, Xw
 
     def fit_flops(st):
         return sum(v["flops"] for v in st["fused"].values())
@@ -269,153 +338,145 @@ def run_ours(args):
     def fit_nominal(st):
         return sum(c["iterations"] for c in st["components"]) * 4.0 * N * M * T
 
+    def timed_steps(o, pp, steps, sampler=None):
+        ms, sts, out = [], [], None
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        for _ in range(steps):
+            flush.zero_()  # L2 flushed between timed steps (outside the events)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fit(o, pp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            sts.append(json.loads(ica.ica_last_stats(ctx)))
+        barrier()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        return ms, sts, out, clocks
+
+    for _ in range(max(args.warmup, 3)):
+        fit(opts_head, params)
+    torch.cuda.synchronize()
+    log("warm-up done")
+    launches0 = json.loads(ica.ica_last_stats(ctx))["launches_total"]
+    step_ms, stats, (W, kurt, Xw), clocks = timed_steps(opts_head, params, args.steps, ClockSampler(local))
+    launches = stats[-1]["launches_total"] - launches0
     total_ms = sum(step_ms)
     flops = sum(fit_flops(s) for s in stats)
     nominal = sum(fit_nominal(s) for s in stats)
-    # profiled pass (same fits with CUDA events around every launch): per-kernel device times
-    prof_stats, prof_ms = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(opts_prof)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        prof_ms.append(e0.elapsed_time(e1))
-        prof_stats.append(json.loads(ica.ica_last_stats(ctx)))
+    total_ms_max, flops_all, nominal_all = aggregate_over_ranks(total_ms, flops, nominal, world, dev)
+    tflops = flops_all / (total_ms_max / 1e3) / 1e12
+
+    # per-kernel device times of the timed steps (library events around each launch)
     kinds = {}
-    for s in prof_stats:
-        for k, v in s["fused"].items():
+    for st in stats:
+        for k, v in st["fused"].items():
             a = kinds.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0})
             for f in a:
                 a[f] += v[f]
-    # device time per step of every phase of the fit (CUDA events around each launch)
     phases = {k: v["ms"] / args.steps for k, v in kinds.items()}
-    for s in prof_stats:
-        for k, v in s.get("phases", {}).items():
+    for st in stats:
+        for k, v in st.get("phases", {}).items():
             phases[k] = phases.get(k, 0.0) + v["ms"] / args.steps
 
-    # whole-job aggregate over ranks: FLOPs summed, time = slowest rank
-    total_ms_max, flops_all, nominal_all = aggregate_over_ranks(total_ms, flops, nominal, world, dev)
-    tflops = flops_all / (total_ms_max / 1e3) / 1e12
+    def summary(sts, ms):
+        last = sts[-1]["components"]
+        return {"time_to_all_components_s": statistics.median(ms) / 1e3,
+                "tflops": sum(fit_flops(x) for x in sts) / (sum(ms) / 1e3) / 1e12,
+                "rows_updated": sum(c["rows_updated"] for c in last),
+                "restarts_pruned": sum(c["pruned"] for c in last),
+                "fallbacks": sum(c["fallback"] for c in last)}
+
+    head = summary(stats, step_ms)
+    log(f"headline {head}")
+    # the same fits without the pruner (the pruner's fallback and judge)
+    unpruned, judge = None, None
+    if prune:
+        opts_u = ica.ica_default_opts(precision=ica.ICA_BF16)
+        fit(opts_u, None)
+        u_ms, u_st, (Wu, ku, _), _ = timed_steps(opts_u, None, max(1, args.side_steps))
+        unpruned = summary(u_st, u_ms)
+        judge = judge_same_components(Wu.cpu().numpy(), W.cpu().numpy(), Xw.cpu().numpy())
+        log(f"unpruned {unpruned} judge {judge}")
 
     # e2e through the public API with host buffers: H2D of X (pinned), whiten + fit, D2H of W, kurt
     e2e_ms, e2e_flops = [], 0.0
     W_host = torch.empty((K, N), dtype=torch.float64).pin_memory()
     k_host = torch.empty(K, dtype=torch.float64).pin_memory()
-    for _ in range(args.steps):
+    for _ in range(max(1, args.side_steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Xd = X_host.to(dev, non_blocking=True)
-        Xw, V, mean = ica.ica_whiten(ctx, Xd)
-        Wd, kd = ica.ica_order_fit(ctx, Xw, M, K, w.iters, w.tol, 1234 + rank, opts)
+        Wd, kd, _ = fit(opts_head, params, Xd)
         W_host[: Wd.shape[0]].copy_(Wd, non_blocking=True)
         k_host[: kd.shape[0]].copy_(kd, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         e2e_flops += fit_flops(json.loads(ica.ica_last_stats(ctx)))
     e2e_tflops = e2e_flops / (sum(e2e_ms) / 1e3) / 1e12
+    log(f"e2e {e2e_ms}")
 
-    # plain FP32 matrix form on the same GPU (comparator)
+    # plain FP32 matrix form on the same GPU (the comparator): one fit after a small untimed one
+    # that creates the cuBLAS handle
     plain = None
-    if not args.no_compare:
-        popts = ica.ica_default_opts(precision=ica.ICA_PLAIN_FP32, profile=1)
-        Xw, V, mean = ica.ica_whiten(ctx, X)
-        ica.ica_order_fit(ctx, Xw, M, K, w.iters, w.tol, 1234 + rank, popts)
-        pt, pf = [], 0.0
-        for _ in range(2):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            Xw, V, mean = ica.ica_whiten(ctx, X)
-            ica.ica_order_fit(ctx, Xw, M, K, w.iters, w.tol, 1234 + rank, popts)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            pt.append(e0.elapsed_time(e1))
-            pf += fit_flops(json.loads(ica.ica_last_stats(ctx)))
-        plain = {"time_to_all_components_s": statistics.median(pt) / 1e3,
-                 "tflops": pf / (sum(pt) / 1e3) / 1e12, "dtype": "f32", "impl": "cuBLAS SGEMM, Z materialised"}
+    if not args.no_compare and world == 1:
+        popts = ica.ica_default_opts(precision=ica.ICA_PLAIN_FP32)
+        Xw_s, _, _ = ica.ica_whiten(ctx, X[:8, :4096].contiguous())
+        ica.ica_order_fit(ctx, Xw_s, 64, 2, 5, 1e-6, 1, popts)
+        p_ms, p_st, _, _ = timed_steps(popts, None, 1)
+        plain = summary(p_st, p_ms)
+        plain.update({"dtype": "f32", "impl": "cuBLAS SGEMM (no TF32), Z materialised in device memory"})
+        log(f"plain {plain}")
 
     # parity spot check of the last timed result: orthonormal rows
     Wc = W.cpu().numpy()
     orth = float(np.abs(Wc @ Wc.T - np.eye(Wc.shape[0])).max())
 
+    # roofline of the dominant kernel: the persistent BF16 stage (one launch per component runs
+    # every iteration: update, row completion, removal of converged rows)
     peaks, peak_src = load_peaks()
     it = kinds.get("iteration", {"launches": 0, "ms": 0.0, "flops": 0.0})
     achieved = it["flops"] / (it["ms"] / 1e3) / 1e12 if it["ms"] > 0 else 0.0
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    # Dominant kernel: the persistent BF16 stage (one launch per component runs every iteration:
-    # update, row completion, removal of converged rows), or the per-launch update kernel when
-    # the stage ran per iteration. DRAM traffic per launch from ncu:
-    #   persistent: 26.20 MB read+written for component 3 (n_pad 64) against 25.6 MB of X~ (one
-    #     pass; later iterations re-read X~ from L2): 1.023 x n_pad T 2 bytes per launch;
-    #   per-launch: 259.6 MB for one launch at n = 64, M = 1024, T = 2e6 against 256.0 MB of X~:
-    #     1.014 x the X~ bytes of every iteration.
-    persistent = bool(stats) and stats[-1].get("stage_persistent_launches", 0) > 0
-    xt_bytes = 0.0
-    if stats:
-        for comp in stats[-1].get("components", []):
-            n_pad_c = (N - comp["i"] + 1 + 15) // 16 * 16
-            xt_bytes += (1 if persistent else comp["iterations"]) * n_pad_c * T * 2.0
-    traffic = (1.023 if persistent else 1.014) * xt_bytes / max(1, it["launches"] / max(1, args.steps)) \
-        if xt_bytes else None
+    xt_bytes = sum((N - c["i"] + 1 + 15) // 16 * 16 * T * 2.0 for c in stats[-1]["components"])
+    ratio = STAGE_TRAFFIC_RATIO.get(args.config)
+    traffic = ratio * xt_bytes / len(stats[-1]["components"]) if ratio else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": ("ncu dram read+write of one stage launch (n_pad 64, T 2e5) / its X~ bytes (1.023), "
-                                 "times the fit's mean X~ bytes per launch" if persistent else
-                                 "ncu dram read+write of one launch at n=64 M=1024 T=2e6 / algorithmic X~ bytes "
-                                 "(1.014), times the fit's mean algorithmic bytes per launch"),
-                "kernel": ("stage_tc_kernel (persistent BF16 stage: tcgen05 update, row completion, removal "
-                           "of converged rows)" if persistent else "fused_tc_kernel (BF16 iteration)"),
+                "traffic_note": ("ncu dram read+write of a stage launch / its X~ bytes, times the fit's mean X~ bytes "
+                                 "per launch" if ratio else "no ncu capture of the current stage kernel at this workload"),
+                "kernel": "stage_tc_kernel (persistent BF16 stage: tcgen05 update, row completion, removal of "
+                          "converged rows)",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "launches": it["launches"], "avg_launch_ms": it["ms"] / max(1, it["launches"]),
-                "share_of_step": it["ms"] / sum(prof_ms)}
+                "algorithmic_flops_per_launch": it["flops"] / max(1, it["launches"]),
+                "share_of_step": it["ms"] / total_ms if total_ms else None,
+                "timing": "CUDA events on the library stream around each launch, inside the timed steps"}
 
-    # BF16 fused + learned pruner: trained (untimed) on the method's own trajectories from two
-    # other seeds of the same workload, then timed like the main steps; its result is checked
-    # against the unpruned one (the pruner's judge)
-    pruned = None
-    if world == 1 and not args.no_prune:
-        from paper_2408_17118_gb300 import pruner as pr
+    cert = None
+    if args.certify and rank == 0:
+        import oracle
 
-        t_tr = time.perf_counter()
-        train_sets = [ica.ica_whiten(ctx, torch.from_numpy(workload(args.config, args.seed + 101 + j).X).to(dev))[0]
-                      for j in range(2)]
-        F, y = pr.collect(ctx, train_sets, M, w.iters, w.tol, seed=4321)
-        params, tau, report = pr.train(ctx, F, y, steps=400, recall=0.99)
-        report["collect_and_train_seconds"] = time.perf_counter() - t_tr
-        del train_sets, F, y
-        popts = ica.ica_default_opts(precision=ica.ICA_BF16)
-        popts.prune_tau = tau
-        step(popts, params)
-        p_ms, p_st = [], []
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            Wp, kp = step(popts, params)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            p_ms.append(e0.elapsed_time(e1))
-            p_st.append(json.loads(ica.ica_last_stats(ctx)))
-        Wu, ku = W.cpu().numpy(), kurt.cpu().numpy()
-        Wpn = Wp.cpu().numpy()
-        ng = np.abs(ku) > 0.3  # non-Gaussian components: unique up to sign
-        same = bool(Wpn.shape == Wu.shape and np.all(np.abs(np.sum(Wu * Wpn, axis=1))[ng] >= 1 - 1e-5))
-        last = p_st[-1]["components"]
-        pruned = {"time_to_all_components_s": statistics.median(p_ms) / 1e3,
-                  "tflops": sum(fit_flops(s) for s in p_st) / (sum(p_ms) / 1e3) / 1e12,
-                  "rows_updated": sum(c["rows_updated"] for c in last),
-                  "rows_updated_unpruned": sum(c["rows_updated"] for c in stats[-1]["components"]),
-                  "restarts_pruned": sum(c["pruned"] for c in last),
-                  "fallbacks": sum(c["fallback"] for c in last),
-                  "same_non_gaussian_components_as_unpruned": same, "tau": tau, "training": report}
+        opts_c = ica.ica_default_opts(precision=ica.ICA_BF16)
+        cands = torch.zeros((K, opts_c.refine_topk, N), dtype=torch.float64, device=dev)
+        Xw_c, _, _ = ica.ica_whiten(ctx, X)
+        Wc2, kc2 = ica.ica_order_fit(ctx, Xw_c, M, K, w.iters, w.tol, seed_fit, opts_c, record_cands=cands)
+        t0 = time.perf_counter()
+        kk = min(args.certify, Wc2.shape[0])
+        checks = oracle.certify_picks(Xw_c.cpu().numpy().astype(np.float64), Wc2.cpu().numpy(), cands.cpu().numpy(),
+                                      K=30, eps=1e-9, components=range(kk))
+        cert = {"components": kk, "seconds": time.perf_counter() - t0,
+                "min_pick_cos": min(c.pick_cos for c in checks), "min_margin": min(c.margin for c in checks),
+                "failed": [c.i + 1 for c in checks if c.pick_cos < 1 - 1e-5 or c.margin < -1e-4 * max(1, abs(c.ups_pick))]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, fl, desc = oracle_sample(w, 512)
+        dt, fl, desc = oracle_sample(w, ORACLE_RESTARTS.get(args.config, 64))
         cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": blas_threads(), "kind": "oracle", "sample": desc,
                "seconds": dt}
 
@@ -426,26 +487,28 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (seeded generators, synth/; stands in for the paper's EEG recordings)",
             "config": {"workload": workload_desc(w), "precision": "bf16 tcgen05 + fp32 refinement",
-                       "pruner": "off", "l2": "flushed between timed steps (256 MB write)",
+                       "pruner": "on (trained untimed on N=8/64/128 trajectories)" if prune else "off",
+                       "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
-            "time_to_all_components_s": statistics.median(step_ms) / 1e3,
+            "time_to_all_components_s": head["time_to_all_components_s"],
             "nominal_tflops": nominal_all / (total_ms_max / 1e3) / 1e12,
+            "headline": head, "unpruned": unpruned, "pruner_judge": judge, "pruner_training": train_report,
             "plain_fp32": plain,
-            "speedup_vs_plain_fp32": (plain["time_to_all_components_s"] / (statistics.median(step_ms) / 1e3))
+            "speedup_vs_plain_fp32": (plain["time_to_all_components_s"] / head["time_to_all_components_s"])
             if plain else None,
+            "speedup_vs_unpruned": (unpruned["time_to_all_components_s"] / head["time_to_all_components_s"])
+            if unpruned else None,
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": int(X_host.numel() * 4),
                     "d2h_bytes_per_step": int(K * N * 8 + K * 8), "time_s": statistics.median(e2e_ms) / 1e3},
             "clocks": clocks, "gpu_launches": int(launches),
-            "fused_kinds": kinds, "phase_ms_per_step": phases, "orthonormality": orth,
-            "pruned": pruned,
+            "fused_kinds": kinds, "phase_ms_per_step": phases, "orthonormality": orth, "certify": cert,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     ctx.close()
     return 0
-
 
 def run_kernel_step(args):
     """One fused BF16 update step (the iteration kernel plus the split combine), repeated."""

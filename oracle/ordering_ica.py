@@ -337,6 +337,57 @@ def order_fit(X: np.ndarray, M: int, n_components: int, iters: int, tol: float, 
 
 
 # --------------------------------------------------------------------------------------------
+# Certification of a fit's picks in FP64 (for fits too large for the full oracle)
+# --------------------------------------------------------------------------------------------
+
+@dataclass
+class PickCheck:
+    i: int                   # component (0-based)
+    ups_pick: float          # Upsilon (Eq. 1) of the refined pick
+    ups_best_other: float    # largest Upsilon among refined candidates distinct from the pick (-inf if none)
+    margin: float            # ups_pick - ups_best_other
+    pick_cos: float          # |cos| between the submitted pick and its FP64 refinement
+    alpha_pick: float        # Eq. 2 kurtosis of the refined pick
+    candidates: int          # non-zero candidate rows checked
+
+
+def certify_picks(Xw: np.ndarray, W: np.ndarray, cands: np.ndarray, K: int = 50, eps: float = 1e-10,
+                  components=None, distinct: float = 1.0 - 1e-3) -> list:
+    """FP64 re-check of the global pick of Algorithm 2 for each listed component i.
+
+    W (n x N) is a fit's output, row i its pick w_i; cands (n x k x N) holds, per component,
+    candidate directions in the whitened space from which that fit picked (zero rows unused).
+    With E = W[:i]^T W[:i] (the components found before, taken from the fit itself), the pick
+    and every candidate are refined by the FastICA run of Algorithm 1 (projected kurtosis fixed
+    point, FP64, to eps or K iterations); their kurtoses (Eq. 2) and objectives (Eq. 1) are then
+    compared as Algorithm 2's argmax compares them. Candidates within |cos| >= `distinct` of the
+    refined pick are the same direction and are not compared. A correct pick is a fixed point
+    (pick_cos ~ 1) with margin >= 0 up to the precision the fit ran in.
+    """
+    Xw = np.asarray(Xw, dtype=F64)
+    W = np.asarray(W, dtype=F64)
+    cands = np.asarray(cands, dtype=F64)
+    N = Xw.shape[0]
+    out = []
+    for i in (range(W.shape[0]) if components is None else components):
+        E = W[:i].T @ W[:i] if i > 0 else np.zeros((N, N))
+        wp, yp, _, _ = fastica_run(W[i], Xw, E, K, eps)
+        a_p = float(kurtosis_alpha(yp))
+        u_p = float(upsilon(a_p))
+        best, used = -np.inf, 0
+        for c in cands[i]:
+            if not np.any(c):
+                continue
+            used += 1
+            wc, yc, _, _ = fastica_run(c, Xw, E, K, eps)
+            if abs(wc @ wp) >= distinct:
+                continue
+            best = max(best, float(upsilon(kurtosis_alpha(yc))))
+        out.append(PickCheck(i, u_p, best, u_p - best, float(abs(wp @ W[i])), a_p, used))
+    return out
+
+
+# --------------------------------------------------------------------------------------------
 # Random initial restarts: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) + Box-Muller
 # --------------------------------------------------------------------------------------------
 

@@ -756,6 +756,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     CK(cudaEventRecord(fit_begin, s));
     const double dT = static_cast<double>(T);
     std::vector<int> comp_iters, comp_refine, comp_pruned, comp_fallback;
+    std::vector<double> comp_stage_ms;  // per component: stage (update) time, when profiling
     const bool prune_opt = o.prune_params != nullptr && o.precision != ICA_PLAIN_FP32;
     int* pruned = at<int>(c, L.pruned);
     float* uref = reinterpret_cast<float*>(counts + 12);  // pruner feature reference (one float)
@@ -1115,7 +1116,9 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         comp_hist.push_back(hist);
         if (o.profile) {
             CK(cudaStreamSynchronize(s));
+            const double before = c->kind_ms[K_ITER];
             harvest(c);
+            comp_stage_ms.push_back(c->kind_ms[K_ITER] - before);
             ev_cursor = 0;
         }
         found = i + 1;
@@ -1164,9 +1167,10 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         snprintf(buf, sizeof(buf),
                  "%s{\"i\": %d, \"iterations\": %d, \"winner\": %d, \"alpha\": %.12g, \"upsilon\": %.12g, "
                  "\"refine_iterations\": %d, \"rows_updated\": %lld, \"refine_rows\": %lld, \"pruned\": %d, "
-                 "\"fallback\": %d, \"active\": [",
+                 "\"fallback\": %d, \"stage_ms\": %.6f, \"active\": [",
                  i ? ", " : "", i + 1, comp_iters[i], static_cast<int>(p), a_p, u_p, comp_refine[i], rows_h[2 * i],
-                 rows_h[2 * i + 1], comp_pruned[i], comp_fallback[i]);
+                 rows_h[2 * i + 1], comp_pruned[i], comp_fallback[i],
+                 i < static_cast<int>(comp_stage_ms.size()) ? comp_stage_ms[i] : 0.0);
         js += buf;
         for (size_t h = 0; h < comp_hist[i].size(); ++h) {
             snprintf(buf, sizeof(buf), "%s%d", h ? ", " : "", comp_hist[i][h]);

@@ -135,6 +135,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     constexpr uint32_t kD2Cols = tc_d2_cols(TC);
     constexpr uint32_t kD1Col = G2S * kD2Cols;  // Z buffers after the G2S accumulators
     static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
+    constexpr uint32_t kALoCol = tc_alo_col(TC, NB);  // B's low term (tc_lo_in_tmem): n_pad / 2 columns
+    static_assert(!tc_lo_in_tmem(TC) || kALoCol + (TC == 128 ? 64u : 128u) <= 512, "B's low term must fit TMEM");
     static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
 
     // running counts of each role (mbarrier phases continue across the updates)
@@ -160,37 +162,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         const bool mom = t < kTrajLen;
 
         if (active && warp >= 2 && warp < 2 + kEpiWarps) {
-            // restart tile -> BF16, K-major, 128-byte swizzle (as the per-launch update kernel)
-            const int et = threadIdx.x - 64;
-            const int cpr = a.n_pad / 8;
-            for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
-                const int row = idx / cpr, ch = idx % cpr;
-                const int gm = m0 + row;
-                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                if (gm < M_act) {
-                    const int r = __ldcg(act + gm);
-                    const float4* src =
-                        reinterpret_cast<const float4*>(a.B32 + static_cast<int64_t>(r) * a.ldb + ch * 8);
-                    v0 = __ldcg(src);
-                    v1 = __ldcg(src + 1);
-                }
-                const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
-                const uint32_t h0 = pack_bf16x2(v0.x, v0.y), h1 = pack_bf16x2(v0.z, v0.w),
-                               h2 = pack_bf16x2(v1.x, v1.y), h3 = pack_bf16x2(v1.z, v1.w);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(h0), "r"(h1), "r"(h2),
-                             "r"(h3)
-                             : "memory");
-                if constexpr (tc_split_b(TC)) {  // residuals b - float(bf16(b)) in the second half
-                    auto lo = [](uint32_t hp, float x, float y) {
-                        return pack_bf16x2(x - __uint_as_float(hp << 16), y - __uint_as_float(hp & 0xFFFF0000u));
-                    };
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + (a.a_bytes >> 1)),
-                                 "r"(lo(h0, v0.x, v0.y)), "r"(lo(h1, v0.z, v0.w)), "r"(lo(h2, v1.x, v1.y)),
-                                 "r"(lo(h3, v1.z, v1.w))
-                                 : "memory");
-                }
-            }
-            fence_proxy_async_smem();
+            // restart tile -> BF16 hi (shared memory) and lo (beside it, or in tensor memory)
+            convert_restart_tile<tc_split_b(TC), tc_lo_in_tmem(TC)>(a.B32, a.ldb, act, m0, M_act, a.n_pad, sA,
+                                                                    a.a_bytes, tmem + kALoCol, true);
+            tc_fence_before();
         }
         // The restart tile is complete for the first-product issuer (warp 1) once the epilogue
         // warps pass this barrier; the TMA producer starts loading X~ without waiting for it.
@@ -239,7 +214,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
                             umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                         }
-                        if constexpr (tc_split_b(TC)) {
+                        if constexpr (tc_lo_in_tmem(TC)) {
+#pragma unroll
+                            for (int ks = 0; ks < 16; ++ks) {
+                                if (ks >= ksteps1) break;
+                                const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                                umma_bf16_tmem_a_acc(d1, tmem + kALoCol + static_cast<uint32_t>(ks) * 8u, b1s + b_off, id1);
+                            }
+                        } else if constexpr (tc_split_b(TC)) {
                             const uint64_t a1_lo = a1_desc + static_cast<uint64_t>((a.a_bytes >> 1) >> 4);
 #pragma unroll
                             for (int ks = 0; ks < 16; ++ks) {

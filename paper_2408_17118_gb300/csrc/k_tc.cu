@@ -114,37 +114,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
-    if (warp >= 2 && warp < 2 + kEpiWarps) {
-        // restart tile -> BF16, K-major, 128-byte swizzle: K-block kb (64 columns) at kb*16 KB
-        const int et = threadIdx.x - 64;
-        const int cpr = n_pad / 8;
-        for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
-            const int row = idx / cpr, ch = idx % cpr;
-            const int gm = m0 + row;
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-            if (gm < M_act) {
-                const int r = act_idx ? act_idx[gm] : gm;
-                const float4* src = reinterpret_cast<const float4*>(B32 + static_cast<int64_t>(r) * ldb + ch * 8);
-                v0 = src[0];
-                v1 = src[1];
-            }
-            const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
-            const uint32_t h0 = pack_bf16x2(v0.x, v0.y), h1 = pack_bf16x2(v0.z, v0.w), h2 = pack_bf16x2(v1.x, v1.y),
-                           h3 = pack_bf16x2(v1.z, v1.w);
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(h0), "r"(h1), "r"(h2), "r"(h3)
-                         : "memory");
-            if constexpr (tc_split_b(TC)) {  // residuals b - float(bf16(b)) in the second half
-                auto lo = [](uint32_t hp, float x, float y) {
-                    return pack_bf16x2(x - __uint_as_float(hp << 16), y - __uint_as_float(hp & 0xFFFF0000u));
-                };
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + (a_bytes >> 1)),
-                             "r"(lo(h0, v0.x, v0.y)), "r"(lo(h1, v0.z, v0.w)), "r"(lo(h2, v1.x, v1.y)),
-                             "r"(lo(h3, v1.z, v1.w))
-                             : "memory");
-            }
-        }
-        fence_proxy_async_smem();
-    }
+    constexpr bool kSplit = tc_split_b(TC), kLoTmem = tc_lo_in_tmem(TC);
+    if (!kLoTmem && warp >= 2 && warp < 2 + kEpiWarps)  // restart tile -> BF16 hi (+ lo) in shared memory
+        convert_restart_tile<kSplit, false>(B32, ldb, act_idx, m0, M_act, n_pad, sA, a_bytes, 0u, false);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -155,6 +127,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t kD1Col = G2S * kD2Cols;  // Z buffers after the G2S accumulators
     static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
     static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
+    constexpr uint32_t kALoCol = tc_alo_col(TC, NB);  // B's low term (kLoTmem): n_pad / 2 columns
+    static_assert(!kLoTmem || kALoCol + (TC == 128 ? 64u : 128u) <= 512, "B's low term must fit TMEM");
+    if constexpr (kLoTmem) {
+        // the low term goes to tensor memory, whose address is known only now: the epilogue warps
+        // convert the tile, then meet the first-product issuer (warp 1) at a named barrier
+        if (warp >= 2 && warp < 2 + kEpiWarps) {
+            convert_restart_tile<kSplit, true>(B32, ldb, act_idx, m0, M_act, n_pad, sA, a_bytes, tmem + kALoCol,
+                                               false);
+            tc_fence_before();
+        }
+        if (warp >= 1 && warp < 2 + kEpiWarps) named_bar_sync(10, 32 * (1 + kEpiWarps));
+        if (warp == 1) tc_fence_after();
+    }
 
     if (warp == 0) {
         // ------------------------------------------------------------------ TMA producer
@@ -211,7 +196,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                               : (static_cast<uint32_t>(ks) * 2048u) >> 4;
                     umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                 }
-                if constexpr (tc_split_b(TC)) {
+                if constexpr (kLoTmem) {
+#pragma unroll
+                    for (int ks = 0; ks < 16; ++ks) {
+                        if (ks >= ksteps1) break;
+                        const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
+                                                  : (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                        umma_bf16_tmem_a_acc(d1, tmem + kALoCol + static_cast<uint32_t>(ks) * 8u, b1s + b_off, id1);
+                    }
+                } else if constexpr (kSplit) {
                     const uint64_t a1_lo = a1_desc + static_cast<uint64_t>((a_bytes >> 1) >> 4);
 #pragma unroll
                     for (int ks = 0; ks < 16; ++ks) {

@@ -22,20 +22,32 @@ namespace ica {
 #ifndef ICA_TC_SMALL_NB
 #define ICA_TC_SMALL_NB 2
 #endif
-// Restart rows as two BF16 terms (hi = bf16(b), lo = bf16(b - hi)) in the first product, for the
-// 192-sample chunks (n_pad <= 64): Z = B_hi X~ + B_lo X~ carries b to about 16 bits instead of 8,
-// so that the BF16 stage's step distance can fall below its tolerance instead of stalling at the
-// rounding noise of b. Costs one more MMA per K step of the first product.
+// Restart rows as two BF16 terms (hi = bf16(b), lo = bf16(b - hi)) in the first product: Z =
+// B_hi X~ + B_lo X~ carries b to about 16 bits instead of 8, so that the BF16 stage's step
+// distance can fall below its tolerance instead of stalling at the rounding noise of b (without
+// it, at n_pad > 64 no restart of the EEG-like N = 128 and N = 256 workloads converged: every one
+// ran all iterations). Costs one more MMA per K step of the first product. Where the two tiles
+// fit shared memory (192-sample chunks, n_pad <= 64) lo sits beside hi there; for 128- and
+// 64-sample chunks lo goes to tensor memory (n_pad / 2 columns after the Z buffers) and the
+// first product reads it as a TMEM A operand.
 #ifndef ICA_TC_SPLIT_B
 #define ICA_TC_SPLIT_B 1
 #endif
-__host__ __device__ constexpr bool tc_split_b(int TC) { return ICA_TC_SPLIT_B && TC == 192; }
+__host__ __device__ constexpr bool tc_split_b(int TC) { return ICA_TC_SPLIT_B != 0; }
+__host__ __device__ constexpr bool tc_lo_in_tmem(int TC) { return ICA_TC_SPLIT_B != 0 && TC != 192; }
 // Second products issued by two threads (on different schedulers) into two accumulators, summed
 // when read out: measured on GB300, one thread sustained one M128 K16 MMA per 67 cycles at
 // N <= 64 and two threads one per 50 (N = 64) or 41 (N = 16) cycles. Both accumulators fit TMEM
-// next to the Z buffers for TC = 192 (n_pad <= 64) and TC = 128 (n_pad <= 128).
-__host__ __device__ constexpr int tc_g2_issuers(int TC) { return TC == 64 ? 1 : 2; }
+// next to the Z buffers for TC = 192 (n_pad <= 64); for TC = 128 only while B's low term does not
+// occupy TMEM (at N = 128 one issuing thread is close to the execution rate of the MMA).
+__host__ __device__ constexpr int tc_g2_issuers(int TC) {
+    return TC == 192 ? 2 : (TC == 128 && !tc_lo_in_tmem(128) ? 2 : 1);
+}
 __host__ __device__ constexpr uint32_t tc_d2_cols(int TC) { return TC == 192 ? 64u : (TC == 128 ? 128u : 256u); }
+// First TMEM column of B's low term (after the G2S accumulators and the NB Z buffers).
+__host__ __device__ constexpr uint32_t tc_alo_col(int TC, int NB) {
+    return static_cast<uint32_t>(tc_g2_issuers(TC)) * tc_d2_cols(TC) + static_cast<uint32_t>(NB * TC);
+}
 
 namespace {
 constexpr int kBars = 40;
@@ -55,7 +67,7 @@ struct TcLayout {
 // reserve: bytes of the 227 KB per-CTA shared memory left for the kernel's static shared memory
 TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, bool KT, uint32_t reserve = 0) {
     TcLayout L{};
-    L.a_bytes = static_cast<uint32_t>((n_pad + 63) / 64) * 16384u * (tc_split_b(TC) ? 2u : 1u);
+    L.a_bytes = static_cast<uint32_t>((n_pad + 63) / 64) * 16384u * (tc_split_b(TC) && !tc_lo_in_tmem(TC) ? 2u : 1u);
     L.xsub_bytes = static_cast<uint32_t>(n_pad) * 128u;
     L.xn_bytes = static_cast<uint32_t>(TC / 64) * L.xsub_bytes;  // X~ tile: n_pad rows x TC samples
     // + X~^T tile: ceil(n_pad / 64) K-blocks of TC rows x 128 bytes
@@ -90,6 +102,87 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* 
 
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Restart tile -> MMA A operands, by the kEpiWarps epilogue warps (warp index w = 2..).
+// hi = bf16(b) goes to shared memory (K-major, 128-byte swizzle, K-block kb of 64 columns at
+// kb * 16 KB); with the split, lo = bf16(b - hi) goes beside it (second half of the A region,
+// smem_lo) or to tensor memory (lo_tmem != 0: lane = row, K step ks at 8 columns from
+// lo_tmem + 8 ks; each warp writes its own lane quarter, as tcgen05.st requires). Rows at or
+// beyond M_act are zero. Row m of the tile is restart act[m0 + m] (or m0 + m when act is null).
+// ldcg: read B through L2 (rows written by other CTAs of a persistent launch).
+template <bool SPLIT, bool LO_TMEM>
+__device__ __forceinline__ void convert_restart_tile(const float* __restrict__ B32, int ldb, const int* act, int m0,
+                                                     int M_act, int n_pad, uint32_t sA, uint32_t a_bytes,
+                                                     uint32_t lo_tmem, bool ldcg) {
+    auto lo_of = [](uint32_t hp, float x, float y) {
+        return pack_bf16x2(x - __uint_as_float(hp << 16), y - __uint_as_float(hp & 0xFFFF0000u));
+    };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (LO_TMEM) {
+        // warp (lane quarter q, group h) takes row 32 q + lane and K steps h, h + 4, ...
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = q * 32 + lane, gm = m0 + row;
+        const bool live = gm < M_act;
+        const int r = live ? (act ? (ldcg ? __ldcg(act + gm) : act[gm]) : gm) : 0;
+        const float* src = B32 + static_cast<int64_t>(r) * ldb;
+        const int ksteps = n_pad / 16;
+        for (int ks = h; ks < ksteps; ks += kEpiWarps / 4) {
+            float4 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (live) {
+                    const float4* p = reinterpret_cast<const float4*>(src + ks * 16) + i;
+                    v[i] = ldcg ? __ldcg(p) : *p;
+                }
+            }
+            uint32_t hp[8], lp[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                hp[2 * i] = pack_bf16x2(v[i].x, v[i].y);
+                hp[2 * i + 1] = pack_bf16x2(v[i].z, v[i].w);
+                lp[2 * i] = lo_of(hp[2 * i], v[i].x, v[i].y);
+                lp[2 * i + 1] = lo_of(hp[2 * i + 1], v[i].z, v[i].w);
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {  // the two 8-element chunks of the K step
+                const int ch = ks * 2 + half;
+                const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(hp[4 * half]),
+                             "r"(hp[4 * half + 1]), "r"(hp[4 * half + 2]), "r"(hp[4 * half + 3])
+                             : "memory");
+            }
+            tmem_st8(lo_tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(ks * 8), lp);
+        }
+        tmem_st_wait();
+    } else {
+        const int et = threadIdx.x - 64;
+        const int cpr = n_pad / 8;
+        for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
+            const int row = idx / cpr, ch = idx % cpr;
+            const int gm = m0 + row;
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (gm < M_act) {
+                const int r = act ? (ldcg ? __ldcg(act + gm) : act[gm]) : gm;
+                const float4* src = reinterpret_cast<const float4*>(B32 + static_cast<int64_t>(r) * ldb + ch * 8);
+                v0 = ldcg ? __ldcg(src) : src[0];
+                v1 = ldcg ? __ldcg(src + 1) : src[1];
+            }
+            const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
+            const uint32_t h0 = pack_bf16x2(v0.x, v0.y), h1 = pack_bf16x2(v0.z, v0.w), h2 = pack_bf16x2(v1.x, v1.y),
+                           h3 = pack_bf16x2(v1.z, v1.w);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(h0), "r"(h1), "r"(h2), "r"(h3)
+                         : "memory");
+            if constexpr (SPLIT) {  // residuals b - float(bf16(b)) in the second half
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + (a_bytes >> 1)),
+                             "r"(lo_of(h0, v0.x, v0.y)), "r"(lo_of(h1, v0.z, v0.w)), "r"(lo_of(h2, v1.x, v1.y)),
+                             "r"(lo_of(h3, v1.z, v1.w))
+                             : "memory");
+            }
+        }
+    }
+    fence_proxy_async_smem();
 }
 
 }  // namespace ica

@@ -28,6 +28,16 @@ def collect(ctx: ica.Context, datasets, M: int, iters: int, tol: float, seed: in
     return torch.cat(Fs).contiguous(), torch.cat(ys).contiguous()
 
 
+def collect_sets(ctx: ica.Context, sets, iters: int, tol: float, seed: int, opts=None):
+    """As collect, for data sets with their own restart counts: sets = [(Xw, M), ...]."""
+    Fs, ys = [], []
+    for k, (Xw, M) in enumerate(sets):
+        F, y = collect(ctx, [Xw], M, iters, tol, seed + k, opts)
+        Fs.append(F)
+        ys.append(y)
+    return torch.cat(Fs).contiguous(), torch.cat(ys).contiguous()
+
+
 def train(ctx: ica.Context, F: torch.Tensor, y: torch.Tensor, steps: int = 300, lr: float = 3e-3, seed: int = 7,
           fp16: bool = True, recall: float = 0.999, tau_cap: float = 0.5):
     """Train from scratch; returns (params, tau, report). tau keeps at least `recall` of the

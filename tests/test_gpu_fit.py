@@ -218,3 +218,34 @@ def test_persistent_stage_equals_per_launch(ctx, case):
     for c0, c1 in zip(s0["components"], s1["components"]):
         assert c0["rows_updated"] == c1["rows_updated"] and c0["refine_rows"] == c1["refine_rows"]
         assert c0["iterations"] <= c1["iterations"] < c0["iterations"] + 4
+
+
+def test_certify_full_size_eeg_like(ctx):
+    """The bench configuration (EEG-like N=64, T=200,000, M=1024, BF16 with FP32 refinement) is
+    too large for the full FP64 oracle; its picks are certified in FP64 instead: for each of the
+    48 non-Gaussian components the library records its refined distinct candidates
+    (opts.record_cands), and oracle.certify_picks refines the pick and every candidate with the
+    FP64 FastICA run of Algorithm 1 (projected onto the complement of the fit's earlier
+    components) and compares their objectives as Algorithm 2's argmax does. Each pick must be
+    an FP64 fixed point (|cos| >= 1 - 1e-5 with its refinement) and no distinct candidate may
+    beat it by more than the FP32 error of Upsilon."""
+    from paper_2408_17118_gb300 import ica
+
+    w = synth.eeg64(0)
+    X = torch.from_numpy(w.X).cuda()
+    Xw, V, mean = ica.ica_whiten(ctx, X)
+    opts = ica.ica_default_opts(precision=ica.ICA_BF16)
+    cands = torch.zeros((w.n_components, opts.refine_topk, w.N), dtype=torch.float64, device="cuda")
+    W, kurt = ica.ica_order_fit(ctx, Xw, w.M, w.n_components, w.iters, w.tol, 11, opts, record_cands=cands)
+    W, kurt, cands = W.cpu().numpy(), kurt.cpu().numpy(), cands.cpu().numpy()
+    Xw64 = Xw.cpu().numpy().astype(np.float64)
+    assert np.abs(W @ W.T - np.eye(64)).max() < 1e-12
+    n_ng = 48  # 3/4 of the sources are non-Gaussian
+    for i in range(n_ng):  # the pick is one of the recorded candidates
+        assert np.max(np.abs(cands[i] @ W[i])) >= 1 - 1e-12, i
+    checks = oracle.certify_picks(Xw64, W, cands, K=30, eps=1e-9, components=range(n_ng))
+    for c in checks:
+        assert c.pick_cos >= 1 - 1e-5, c
+        assert c.margin >= -1e-4 * max(1.0, abs(c.ups_pick)), c
+        assert abs(kurt[c.i] - c.alpha_pick) <= 1e-4 * abs(c.alpha_pick), (c, kurt[c.i])
+    assert sum(c.candidates > 1 for c in checks) >= n_ng // 2  # most components compare >1 candidate

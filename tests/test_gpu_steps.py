@@ -191,12 +191,11 @@ STEP_SHAPES = [(1, 1, 64), (63, 5, 1000), (64, 16, 4097), (65, 17, 12345), (129,
 
 
 def b_operand(B, n_pad):
-    """The restart rows as the BF16 kernel feeds them to the tensor cores: for n_pad <= 64 (192-sample
-    chunks) as two BF16 terms hi = bf16(b), lo = bf16(b - hi); otherwise one BF16 value."""
+    """The restart rows as the BF16 kernel feeds them to the tensor cores: two BF16 terms
+    hi = bf16(b), lo = bf16(b - hi) (lo from shared memory for n_pad <= 64, from tensor memory
+    above), both multiplied by the same BF16 X~ and accumulated in FP32."""
     B = np.asarray(B, dtype=np.float32)
     hi = bf16(B).astype(np.float32)
-    if n_pad > 64:
-        return hi.astype(np.float64)
     lo = bf16((B - hi).astype(np.float32)).astype(np.float32)
     return hi.astype(np.float64) + lo.astype(np.float64)
 

@@ -321,3 +321,86 @@ def test_fluctuation_metric():
     b = np.array([[0, 1.0, 0], [1.0, 0, 0], [0, 0, 1.0]])
     f = oracle.fluctuation([a, b])
     assert np.allclose(f, [1.0, 1.0, 0.0])
+
+
+# ------------------------------------------------------------------ FP64 certification of picks
+def _distinct_top(trace, k, thresh=1.0 - 1e-3):
+    """The k best restarts of one oracle component by Upsilon, distinct directions only, mapped
+    to the whitened space (w = b G, Section 3.3)."""
+    order = np.argsort(-trace.upsilon, kind="stable")
+    picked = []
+    for r in order:
+        b = trace.B_final[r] / np.linalg.norm(trace.B_final[r])
+        if all(abs(b @ q) < thresh for q in picked):
+            picked.append(b)
+        if len(picked) == k:
+            break
+    rows = [b @ trace.G for b in picked]
+    return np.array([r / np.linalg.norm(r) for r in rows])
+
+
+def _cands_of(res, k):
+    N = res.W.shape[1]
+    C = np.zeros((len(res.traces), k, N))
+    for i, tr in enumerate(res.traces):
+        top = _distinct_top(tr, k)
+        C[i, : len(top)] = top
+    return C
+
+
+def test_certify_accepts_the_oracle_picks(small_oracle):
+    """Algorithm 2's own picks pass: each is an FP64 fixed point and no distinct candidate among
+    its component's best restarts has a larger Upsilon."""
+    w, B0, res, Xw, V, mean = small_oracle
+    checks = oracle.certify_picks(Xw, res.W, _cands_of(res, 4), K=200, eps=1e-12)
+    assert len(checks) == 8
+    for c in checks:
+        assert c.pick_cos >= 1 - 1e-12, c
+        assert c.margin >= -1e-9, c
+        assert c.ups_pick == pytest.approx(float(oracle.upsilon(res.alpha[c.i])), rel=1e-9, abs=1e-12)
+    assert sum(c.candidates > 1 for c in checks) >= 5  # the comparison is not vacuous
+
+
+def test_certify_flags_a_wrong_pick(small_oracle):
+    """A planted mistake: component 0's pick replaced by its runner-up (a distinct direction with
+    a smaller Upsilon). The check must report a negative margin for that component."""
+    w, B0, res, Xw, V, mean = small_oracle
+    C = _cands_of(res, 4)
+    W = res.W.copy()
+    W[0] = C[0, 1]
+    c = oracle.certify_picks(Xw, W, C, K=200, eps=1e-12, components=[0])[0]
+    assert c.margin < -1e-3, c
+
+
+def test_certify_two_dimensional_brute_force():
+    """N = 2: the pick at the brute-force maximum of Upsilon over the unit circle passes, its
+    refined objective equals the brute-force value, and a pick 0.3 rad away is flagged."""
+    T = 20_000
+    S = np.vstack([synth.standardise(synth.make_source("laplace", synth.rng_for(3, 0), T)),
+                   synth.standardise(synth.make_source("uniform", synth.rng_for(3, 1), T))])
+    X = (np.array([[1.0, 0.6], [-0.4, 1.3]]) @ S).astype(np.float32)
+    Xw, V, mean = oracle.whiten(X)
+    f = lambda t: float(oracle.upsilon(oracle.kurtosis_alpha(np.cos(t) * Xw[0] + np.sin(t) * Xw[1])))
+    th = np.linspace(0, math.pi, 20_000, endpoint=False)
+    vals = oracle.upsilon(oracle.kurtosis_alpha(np.outer(np.cos(th), Xw[0]) + np.outer(np.sin(th), Xw[1])))
+    t0 = th[int(np.argmax(vals))]
+    lo, hi = t0 - 2e-4, t0 + 2e-4
+    g = (math.sqrt(5) - 1) / 2
+    for _ in range(80):
+        a, b = hi - g * (hi - lo), lo + g * (hi - lo)
+        if f(a) > f(b):
+            hi = b
+        else:
+            lo = a
+    tb = (lo + hi) / 2
+    W = np.array([[math.cos(tb), math.sin(tb)], [-math.sin(tb), math.cos(tb)]])
+    ang = np.linspace(0, math.pi, 16, endpoint=False)
+    C = np.zeros((2, 16, 2))
+    C[0] = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    c = oracle.certify_picks(Xw, W, C, K=500, eps=1e-13, components=[0])[0]
+    assert c.pick_cos >= 1 - 1e-10 and c.margin >= -1e-9
+    assert c.ups_pick == pytest.approx(f(tb), rel=1e-9)
+    Wbad = np.array([[math.cos(tb + 0.3), math.sin(tb + 0.3)], [0.0, 0.0]])
+    bad = oracle.certify_picks(Xw, Wbad, C, K=500, eps=1e-13, components=[0])[0]
+    # refined, the bad pick either moves away (not a fixed point) or lands on a worse optimum
+    assert bad.pick_cos < 1 - 1e-5 or bad.margin < -1e-6
