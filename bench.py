@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prune", action="store_true", help="headline without the learned pruner")
     ap.add_argument("--side-steps", type=int, default=2, help="timed steps of the unpruned and e2e legs")
+    ap.add_argument("--plain-components", type=int, default=-1, metavar="K",
+                    help="plain FP32 comparison on the first K components (0: the whole fit; default: 8 for "
+                         "eeg256, whose whole plain fit takes about ten minutes, else 0)")
     ap.add_argument("--certify", type=int, default=0, metavar="K",
                     help="FP64 certification (oracle.certify_picks) of the first K components of one extra fit")
     ap.add_argument("--kernel-step", type=int, default=0, metavar="T",
@@ -245,7 +248,9 @@ def train_pruner(ctx, dev, seed: int):
     sets = [(ica.ica_whiten(ctx, torch.from_numpy(w.X).to(dev))[0], w.M) for w in shapes]
     F, y = pr.collect_sets(ctx, sets, 30, 1e-6, seed=4321)
     t_col = time.perf_counter() - t0
-    params, tau, report = pr.train(ctx, F, y, steps=400, recall=0.99)
+    # the keep floor (the restarts leading Upsilon at iteration 5) carries the likely winners; the
+    # network adds slower starters at a recall of 0.9 on the training positives
+    params, tau, report = pr.train(ctx, F, y, steps=400, recall=0.9)
     report["collect_seconds"] = t_col
     report["collect_and_train_seconds"] = time.perf_counter() - t0
     report["trained_on"] = [f"N={w.N} T={w.T} M={w.M}" for w in shapes]
@@ -266,25 +271,29 @@ def upsilon64(w, Xw_host):
     return a - 2.0 * math.log(a / 2.0 + 1.0) if a > -2.0 else math.inf
 
 
-def judge_same_components(Wu, Wp, Xw_host):
-    """The pruner's judge: the pruned fit must pick the unpruned fit's components, in order.
-    Components are compared in order while both fits agree (|w_u . w_p| >= 1 - 1e-5); at the first
-    difference the two picks (same earlier components) are compared by their FP64 objective
-    Upsilon: a pruned pick worse by more than the FP32 error of Upsilon (1e-4 relative) fails the
-    judge, a difference within it is a tie that FP32 cannot order (after it the deflation
-    subspaces differ and the remaining components are not compared)."""
-    import numpy as np
-
-    n = min(len(Wu), len(Wp))
+def judge_same_components(Wu, st_u, Wp, Xw_host):
+    """The pruner's judge: every component the Gaussianity test (Eq. 3) calls non-Gaussian in the
+    unpruned fit (Upsilon above 2 (N - i + 2)(N - i + 1) / T; the components after them span the
+    Gaussian subspace, where no direction is unique, Theorem 1) must be the pruned fit's too, in
+    order. At the first difference the two picks (same earlier components) are compared by their
+    FP64 objective Upsilon: a pruned pick worse by more than the FP32 error of Upsilon (1e-4
+    relative) fails the judge; a difference within it is a tie that FP32 cannot order (the
+    remaining components are then not compared, their deflation subspaces differ)."""
+    N, T = Xw_host.shape
+    ng = 0
+    for c in st_u["components"]:
+        if c["upsilon"] < 2.0 * (N - c["i"] + 2) * (N - c["i"] + 1) / T:
+            break
+        ng += 1
+    n = min(ng, len(Wp))
     for i in range(n):
         if abs(float(Wu[i] @ Wp[i])) >= 1 - 1e-5:
             continue
         uu, up = upsilon64(Wu[i], Xw_host), upsilon64(Wp[i], Xw_host)
         tol = 1e-4 * max(1.0, abs(uu))
-        return {"components": n, "agree_prefix": i, "first_difference": i + 1, "ups_unpruned": uu, "ups_pruned": up,
-                "tie": abs(up - uu) <= tol, "pruned_not_worse": up >= uu - tol,
-                "ok": bool(up >= uu - tol)}
-    return {"components": n, "agree_prefix": n, "first_difference": None, "ok": len(Wu) == len(Wp)}
+        return {"non_gaussian": ng, "agree_prefix": i, "first_difference": i + 1, "ups_unpruned": uu,
+                "ups_pruned": up, "tie": abs(up - uu) <= tol, "ok": bool(up >= uu - tol)}
+    return {"non_gaussian": ng, "agree_prefix": n, "first_difference": None, "ok": n == ng}
 
 
 def run_ours(args):
@@ -400,7 +409,7 @@ def run_ours(args):
         fit(opts_u, None)
         u_ms, u_st, (Wu, ku, _), _ = timed_steps(opts_u, None, max(1, args.side_steps))
         unpruned = summary(u_st, u_ms)
-        judge = judge_same_components(Wu.cpu().numpy(), W.cpu().numpy(), Xw.cpu().numpy())
+        judge = judge_same_components(Wu.cpu().numpy(), u_st[-1], W.cpu().numpy(), Xw.cpu().numpy())
         log(f"unpruned {unpruned} judge {judge}")
 
     # e2e through the public API with host buffers: H2D of X (pinned), whiten + fit, D2H of W, kurt
@@ -425,12 +434,36 @@ def run_ours(args):
     # that creates the cuBLAS handle
     plain = None
     if not args.no_compare and world == 1:
+        kp = args.plain_components if args.plain_components >= 0 else (8 if args.config == "eeg256" else 0)
+        kp = K if kp == 0 or kp > K else kp
         popts = ica.ica_default_opts(precision=ica.ICA_PLAIN_FP32)
         Xw_s, _, _ = ica.ica_whiten(ctx, X[:8, :4096].contiguous())
-        ica.ica_order_fit(ctx, Xw_s, 64, 2, 5, 1e-6, 1, popts)
-        p_ms, p_st, _, _ = timed_steps(popts, None, 1)
+        ica.ica_order_fit(ctx, Xw_s, 64, 2, 5, 1e-6, 1, popts)  # creates the cuBLAS handle
+
+        def prefix_steps(o, pp, steps):
+            ms, sts = [], []
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                Xw_p, _, _ = ica.ica_whiten(ctx, X)
+                ica.ica_order_fit(ctx, Xw_p, M, kp, w.iters, w.tol, seed_fit, o, prune_params=pp)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                sts.append(json.loads(ica.ica_last_stats(ctx)))
+            return ms, sts
+
+        p_ms, p_st = prefix_steps(popts, None, 1)
         plain = summary(p_st, p_ms)
-        plain.update({"dtype": "f32", "impl": "cuBLAS SGEMM (no TF32), Z materialised in device memory"})
+        plain.update({"dtype": "f32", "impl": "cuBLAS SGEMM (no TF32), Z materialised in device memory",
+                      "components": kp})
+        if kp < K:  # the headline configuration on the same components, for a like-for-like ratio
+            b_ms, b_st = prefix_steps(opts_head, params, 2)
+            plain["bf16_same_components"] = summary(b_st[1:], b_ms[1:])
+            plain["speedup_same_components"] = (plain["time_to_all_components_s"] /
+                                                plain["bf16_same_components"]["time_to_all_components_s"])
         log(f"plain {plain}")
 
     # parity spot check of the last timed result: orthonormal rows
@@ -494,7 +527,8 @@ def run_ours(args):
             "nominal_tflops": nominal_all / (total_ms_max / 1e3) / 1e12,
             "headline": head, "unpruned": unpruned, "pruner_judge": judge, "pruner_training": train_report,
             "plain_fp32": plain,
-            "speedup_vs_plain_fp32": (plain["time_to_all_components_s"] / head["time_to_all_components_s"])
+            "speedup_vs_plain_fp32": (plain["time_to_all_components_s"] / head["time_to_all_components_s"]
+                                      if plain["components"] == K else plain["speedup_same_components"])
             if plain else None,
             "speedup_vs_unpruned": (unpruned["time_to_all_components_s"] / head["time_to_all_components_s"])
             if unpruned else None,

@@ -79,7 +79,10 @@ typedef struct {
     const float* prune_params; /* optional: ICA_MLP_PARAMS floats (device). After the first 5
                               iterations of a component, restarts whose predicted probability of
                               ending at the picked direction is below prune_tau leave the active
-                              set and the pick. If a pruned restart's kurtosis objective is at
+                              set and the pick, except the restarts leading the objective then:
+                              the max(refine_topk (1 on the FP32 path), ceil(prune_keep_frac x
+                              active)) restarts with the largest Upsilon (Eq. 1) at iteration 5
+                              always stay. If a pruned restart's kurtosis objective is at
                               least the best kept one, or the pruner dropped every active
                               restart, the component is fitted again without pruning from the
                               same initial restarts (reported as "fallback" in ica_last_stats).
@@ -107,6 +110,9 @@ typedef struct {
                               persistent stage wait for one arrival more than there are CTAs, so
                               that its wait runs out (exercises the timeout path on the host's
                               request, without a fault) */
+    float prune_keep_frac; /* fraction of the active restarts, ranked by Upsilon at iteration 5,
+                              that the pruner always keeps (default 0.05; 0..1; 0: no floor at
+                              all, the network alone decides) */
     double* record_cands;  /* optional (device, BF16 path): n_components x refine_topk x N FP64.
                               Row (i, j) = w = G^T b of the j-th distinct candidate of component i
                               after the FP32 refinement (Section 3.3: the candidate in the full
@@ -117,8 +123,8 @@ typedef struct {
 
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
-   no profiling, no pruner (prune_tau 0.05), no recording, persistent stage, 2 s wait limit,
-   no stall. */
+   no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05), no recording, persistent
+   stage, 2 s wait limit, no stall. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */

@@ -41,6 +41,7 @@ class ica_opts(C.Structure):
         ("stage_persistent", C.c_int),
         ("wait_ns", C.c_int64),
         ("stall_test", C.c_int),
+        ("prune_keep_frac", C.c_float),
         ("record_cands", C.c_void_p),
     ]
 

@@ -110,8 +110,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     int n_pad_max = 0, M_pad = 0, part_rows_max = 0;
     int64_t ldx = 0;
-    int tcols = 0;  // row length (elements) of the transposed BF16 copy
-    size_t status, counts, Xt32, Xt16, Xt16t, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots, pruned,
+    size_t status, counts, Xt32, Xt16, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots, pruned,
         part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, comp_rows, total;
 };
 
@@ -133,8 +132,6 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.counts = take(32 * sizeof(int));
     L.Xt32 = take(sizeof(float) * L.n_pad_max * static_cast<size_t>(L.ldx));
     L.Xt16 = take(precision == ICA_BF16 ? sizeof(uint16_t) * L.n_pad_max * static_cast<size_t>(L.ldx) : 0);
-    L.tcols = round_up64cols(L.n_pad_max < 128 ? L.n_pad_max : 128);
-    L.Xt16t = take(precision == ICA_BF16 ? sizeof(uint16_t) * static_cast<size_t>(L.ldx) * L.tcols : 0);
     L.Z = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(M) * L.ldx : 0);
     L.B32 = take(sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max);
     L.Bact = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max : 0);
@@ -196,19 +193,6 @@ void choose_splits(int64_t total_chunks, int tiles, int waves_ctas, int max_spli
     *splits = static_cast<int>((total_chunks + c - 1) / c);
 }
 
-// X~^T (T rows x tcols elements, reduced index contiguous): box {64 reduced entries, TC samples}.
-int encode_xmap_t(ica_ctx* c, CUtensorMap* map, const uint16_t* Xt16t, int tcols, int64_t T, int TC) {
-    if (!c->encode) return ICA_ERR_UNSUPPORTED;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(tcols), static_cast<cuuint64_t>(T)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(tcols) * 2};
-    cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(TC)};
-    cuuint32_t estr[2] = {1u, 1u};
-    CUresult r = c->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(Xt16t), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? ICA_OK : ICA_ERR_CUDA;
-}
-
 int encode_xmap(ica_ctx* c, CUtensorMap* map, const uint16_t* Xt16, int n_pad, int64_t T, int64_t ld) {
     if (!c->encode) return ICA_ERR_UNSUPPORTED;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(T), static_cast<cuuint64_t>(n_pad)};
@@ -258,8 +242,6 @@ struct FusedArgs {
     int64_t T = 0;
     const float* Xt32 = nullptr;
     const uint16_t* Xt16 = nullptr;
-    const uint16_t* Xt16t = nullptr;  // transposed BF16 copy (T x tcols) or NULL
-    int tcols = 0;
     int64_t ldx = 0;
     int max_splits = 0;
     int* shape_dev = nullptr;  // BF16 update: shape the launch on the device, write {splits, part_rows} here
@@ -275,7 +257,7 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
         const int TC = tc_chunk(a.n_pad);
         const int64_t total = (a.T + TC - 1) / TC;
         const int tiles = (a.M_act + kTcRows - 1) / kTcRows;
-        if (a.shape_dev && a.count_dev && !a.moments_only && a.max_splits == 0 && !(a.Xt16t && tc_transposed(a.n_pad))) {
+        if (a.shape_dev && a.count_dev && !a.moments_only && a.max_splits == 0) {
             CUtensorMap map;
             int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
             if (rc) return rc;
@@ -288,15 +270,10 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
         }
         choose_splits(total, tiles, 152 / c->cta_div, a.max_splits, &shape->splits, &shape->cps, true);  // one wave
         shape->part_rows = tiles * kTcRows;
-        CUtensorMap map, map_t;
+        CUtensorMap map;
         int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
         if (rc) return rc;
-        const bool use_t = a.Xt16t && tc_transposed(a.n_pad);
-        if (use_t) {
-            rc = encode_xmap_t(c, &map_t, a.Xt16t, a.tcols, a.T, TC);
-            if (rc) return rc;
-        }
-        KL(launch_fused_tc(s, a.moments_only, a.moments, map, use_t ? &map_t : nullptr, a.B32, a.ldb, a.act,
+        KL(launch_fused_tc(s, a.moments_only, a.moments, map, a.B32, a.ldb, a.act,
                            a.count_dev, a.M_act, a.n_pad, a.T, shape->splits, shape->cps, static_cast<int>(total), pacc,
                            pmom, shape->part_rows, status));
         return ICA_OK;
@@ -458,6 +435,7 @@ void ica_default_opts(ica_opts* o) {
     o->record_features = nullptr;
     o->record_labels = nullptr;
     o->stage_persistent = 1;
+    o->prune_keep_frac = 0.05f;
 }
 
 const char* ica_status_string(int st) {
@@ -613,12 +591,6 @@ int ica_fp_step(ica_ctx* c, int precision, const float* B, int M, int n, const v
     fa.Xt32 = static_cast<const float*>(Xt);
     fa.Xt16 = static_cast<const uint16_t*>(Xt);
     fa.ldx = ldx;
-    if (precision == ICA_BF16 && tc_transposed(n_pad)) {
-        uint16_t* xt = at<uint16_t>(c, L.Xt16t);
-        KL(launch_transpose_bf16(c->stream, static_cast<const uint16_t*>(Xt), n_pad, T, ldx, xt, L.tcols));
-        fa.Xt16t = xt;
-        fa.tcols = L.tcols;
-    }
     rc = run_fused(c, L, fa, &sh);
     if (rc) return rc;
     KL(launch_combine(c->stream, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows, n_pad,
@@ -650,12 +622,6 @@ int ica_kurtosis(ica_ctx* c, int precision, const float* B, int M, int n, const 
     fa.Xt32 = static_cast<const float*>(Xt);
     fa.Xt16 = static_cast<const uint16_t*>(Xt);
     fa.ldx = ldx;
-    if (precision == ICA_BF16 && tc_transposed(n_pad)) {
-        uint16_t* xt = at<uint16_t>(c, L.Xt16t);
-        KL(launch_transpose_bf16(c->stream, static_cast<const uint16_t*>(Xt), n_pad, T, ldx, xt, L.tcols));
-        fa.Xt16t = xt;
-        fa.tcols = L.tcols;
-    }
     rc = run_fused(c, L, fa, &sh);
     if (rc) return rc;
     KL(launch_kurt_finalize(c->stream, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, nullptr, M,
@@ -676,6 +642,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_PLAIN_FP32) return ICA_ERR_UNSUPPORTED;
     if (o.precision == ICA_BF16 && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
     if (o.wait_ns < 0 || (o.record_cands && o.precision != ICA_BF16)) return ICA_ERR_ARG;
+    if (!(o.prune_keep_frac >= 0.f && o.prune_keep_frac <= 1.f)) return ICA_ERR_ARG;
     const Layout L = make_layout(N, T, M, o.precision);
     int rc = check_ws(c, L);
     if (rc) return rc;
@@ -769,10 +736,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         // reduction basis and X~ = G Xw (Section 3.3)
         rc = timed(K_BASIS, 0.0, [&] { return deflation_basis_impl(c, L, W_out, i, N, G); });
         if (rc) return rc;
-        const bool want_t = bf16 && tc_transposed(n_pad);
         rc = timed(K_REDUCE, 0.0, [&] {
-            KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx,
-                                want_t ? at<uint16_t>(c, L.Xt16t) : nullptr, L.tcols));
+            KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx));
             return ICA_OK;
         });
         if (rc) return rc;
@@ -805,8 +770,6 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             fa.T = T;
             fa.Xt32 = Xt32;
             fa.Xt16 = Xt16;
-            fa.Xt16t = want_t ? at<uint16_t>(c, L.Xt16t) : nullptr;
-            fa.tcols = L.tcols;
             fa.ldx = ldx;
             fa.max_splits = o.max_splits;
             // fixed-point iterations with removal of converged rows (Algorithm 2, Section 3.2)
@@ -816,7 +779,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             // The BF16 stage runs as one persistent cooperative launch per segment of iterations
             // (k_stage.cu; same arithmetic as the per-launch path below) when the fit owns the GPU.
             bool persist = bf16 && o.stage_persistent && o.max_splits == 0 && c->persist_ok && c->cta_div == 1 &&
-                           !want_t && M <= 152 * kTcRows;
+                           M <= 152 * kTcRows;
             while (t < iters && M_host > 0) {
                 if (persist) {
                     const int t_end = (prune_this && t < kTrajLen) ? std::min(iters, kTrajLen) : iters;
@@ -926,7 +889,9 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     int before = M_host;
                     rc = timed(K_PRUNE, 0.0, [&] {
                         KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, n,
-                                        std::log(static_cast<double>(T)), o.prune_tau, uref, flags, pruned));
+                                        std::log(static_cast<double>(T)), o.prune_tau, uref, flags, pruned,
+                                        o.prune_keep_frac > 0.f ? (bf16 ? o.refine_topk : 1) : 0,
+                                        o.prune_keep_frac));
                         KL(launch_compact_keep(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1)));
                         return ICA_OK;
                     });

@@ -93,10 +93,7 @@ cudaError_t launch_pad_cols(cudaStream_t s, const double* W, int k, int N, int n
 // ---- k_reduce.cu ----
 cudaError_t launch_rows_gemm(cudaStream_t s, const double* G, int n, int n_pad, int N, const float* X,
                              int64_t T, int64_t ldxin, const double* bias, float* out32, int64_t ld32,
-                             uint16_t* out16, int64_t ld16, uint16_t* out16t = nullptr, int64_t ld16t = 0);
-cudaError_t launch_transpose_bf16(cudaStream_t s, const uint16_t* Xn, int n_pad, int64_t T, int64_t ldx,
-                                  uint16_t* Xt, int64_t ldt);
-inline int round_up64cols(int n_pad) { return (n_pad + 63) / 64 * 64; }
+                             uint16_t* out16, int64_t ld16);
 
 // ---- k_fp32.cu ----
 size_t fp32_smem_bytes(int n_pad);
@@ -125,9 +122,11 @@ cudaError_t launch_mlp_forward(cudaStream_t s, const float* params, const float*
 cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float* v, int step, const float* F,
                                   const float* y, int rows, float lr, float pos_weight, bool fp16, float* scratch,
                                   float* loss_out, float* grad_out);
+// keep floor: the max(keep_min, ceil(keep_frac * count)) restarts with the largest Upsilon at
+// iteration kTrajLen (and any tied with the last of them) are always kept
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
                          const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned);
+                         int* pruned, int keep_min, float keep_frac);
 cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, const float* B32, int ldb, int n, int M,
                           const int* slot, double logT, float* ref, float* F_out, float* y_out);
 cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, int M, int* out);
@@ -151,16 +150,13 @@ __host__ __device__ inline void tc_device_shape(int M_act, int ctas, int total_c
 // ---- k_tc.cu ----
 int tc_chunk(int n_pad);
 int tc_buffers(int n_pad);
-bool tc_transposed(int n_pad);
 size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out);
-// xmap: X~ (n_pad x T, samples contiguous), box {64, n_pad}. xmap_t (optional, n_pad <= 128):
-// X~^T (T x round_up64cols(n_pad), reduced index contiguous), box {64, tc_chunk(n_pad)}; when
-// given, the first product reads it as a K-major operand.
+// xmap: X~ (n_pad x T, samples contiguous), box {64, n_pad}.
 cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
                                    const int* act_idx, const int* count_dev, int M_ub, int n_pad, int64_t T, int ctas,
                                    int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out);
 cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
-                            const CUtensorMap* xmap_t, const float* B32, int ldb, const int* act_idx,
+                            const float* B32, int ldb, const int* act_idx,
                             const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
                             int total_chunks, float* part_acc, float* part_mom, int part_rows, int* status);
 

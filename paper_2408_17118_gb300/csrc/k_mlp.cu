@@ -324,6 +324,86 @@ __global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ pa
     if (!k) pruned[r] = 1;
 }
 
+// Keep floor of the pruner: the active restarts with the largest Upsilon(alpha at iteration
+// kTrajLen) are kept whatever the network predicts, at least `k` of them: all with Upsilon at or
+// above the largest threshold theta that at least k reach (found by bisection over [min, max];
+// ties at theta are all kept). The restart leading the objective at that iteration ends at the
+// component's pick in most components, so the floor keeps the likely winners; the network adds
+// the slower starters. One block.
+__global__ void __launch_bounds__(256) keep_top_kernel(const float* __restrict__ traj, const int* __restrict__ act_idx,
+                                                       const int* __restrict__ count_dev, int count_host, int k_min,
+                                                       float frac, int* __restrict__ keep, int* __restrict__ pruned) {
+    __shared__ float rlo[256], rhi[256];
+    __shared__ int rc[256];
+    const int count = count_dev ? *count_dev : count_host;
+    const int tid = threadIdx.x;
+    int k = static_cast<int>(ceilf(frac * static_cast<float>(count)));
+    if (k < k_min) k = k_min;
+    if (k > count) k = count;
+    if (k <= 0) return;
+    auto u5_of = [&](int j) {
+        const int r = act_idx ? act_idx[j] : j;
+        return upsilon_clamped(traj[(static_cast<int64_t>(r) * kTrajLen + kTrajLen - 1) * 2]);
+    };
+    float lo = INFINITY, hi = -INFINITY;
+    for (int j = tid; j < count; j += 256) {
+        const float u = u5_of(j);
+        if (u == u) {  // not NaN
+            lo = fminf(lo, u);
+            hi = fmaxf(hi, u);
+        }
+    }
+    rlo[tid] = lo;
+    rhi[tid] = hi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o) {
+            rlo[tid] = fminf(rlo[tid], rlo[tid + o]);
+            rhi[tid] = fmaxf(rhi[tid], rhi[tid + o]);
+        }
+        __syncthreads();
+    }
+    lo = rlo[0];
+    hi = rhi[0];
+    __syncthreads();
+    if (!(lo <= hi)) return;  // every value NaN: the network's decisions stand
+    // invariant: count(u >= lo) >= k; find the largest such threshold to FP32 resolution
+    float theta = lo;
+    for (int it = 0; it < 40 && hi > theta; ++it) {
+        const float mid = theta + 0.5f * (hi - theta);
+        if (!(mid > theta) || !(mid < hi)) break;
+        int c = 0;
+        for (int j = tid; j < count; j += 256) c += u5_of(j) >= mid;
+        rc[tid] = c;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (tid < o) rc[tid] += rc[tid + o];
+            __syncthreads();
+        }
+        if (rc[0] >= k)
+            theta = mid;
+        else
+            hi = mid;
+        __syncthreads();
+    }
+    {   // hi may itself be reached by k values (a tie at the top): take it when it is
+        int c = 0;
+        for (int j = tid; j < count; j += 256) c += u5_of(j) >= hi;
+        rc[tid] = c;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (tid < o) rc[tid] += rc[tid + o];
+            __syncthreads();
+        }
+        if (rc[0] >= k) theta = hi;
+    }
+    for (int j = tid; j < count; j += 256)
+        if (u5_of(j) >= theta) {
+            keep[j] = 1;
+            pruned[act_idx ? act_idx[j] : j] = 0;
+        }
+}
+
 // Training record of one component: raw features of every restart and whether the restart
 // ended at the picked direction (|b_r . b_p| >= 1 - 1e-3 on normalised rows).
 __global__ void record_kernel(const float* __restrict__ traj, const float* __restrict__ B32, int ldb, int n_dim, int M,
@@ -428,13 +508,16 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
                          const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned) {
+                         int* pruned, int keep_min, float keep_frac) {
     upsilon_ref_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, nullptr, ref);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prune_kernel<<<(count_host + 127) / 128, 128, 0, s>>>(params, traj, act_idx, count_dev, count_host,
                                                           static_cast<float>(n), static_cast<float>(logT), ref, tau,
                                                           keep, pruned);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || (keep_min <= 0 && !(keep_frac > 0.f))) return e;
+    keep_top_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, keep_min, keep_frac, keep, pruned);
     return cudaGetLastError();
 }
 

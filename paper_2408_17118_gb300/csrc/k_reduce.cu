@@ -1,9 +1,7 @@
 // Reduction of signals (Section 3.3, Eq. 8): X~ = G X, and the whitening apply
 // Xw = V X - V mean. FP64 coefficients are rounded to FP32 on load; products accumulate in
-// FP32. Writes FP32 rows and/or their BF16 rounding (the tensor-core operand), and optionally the
-// BF16 transpose (samples x reduced dimension, the reduced index contiguous: the K-major operand
-// of the first product of the fused iteration). Rows n..n_pad-1 (columns of the transpose) are
-// written as zeros, so the padded reduced dimension contributes nothing to the products.
+// FP32. Writes FP32 rows and/or their BF16 rounding (the tensor-core operand). Rows n..n_pad-1
+// are written as zeros, so the padded reduced dimension contributes nothing to the products.
 #include "common.cuh"
 #include "internal.h"
 
@@ -15,10 +13,9 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
                                                         const float* __restrict__ X, int64_t T, int64_t ldxin,
                                                         const double* __restrict__ bias, float* __restrict__ out32,
                                                         int64_t ld32, uint16_t* __restrict__ out16, int64_t ld16,
-                                                        uint16_t* __restrict__ out16t, int64_t ld16t, int n_pad) {
+                                                        int n_pad) {
     __shared__ __align__(16) float Gs[RG_BK][RG_BM + 4];  // padded: the transposing stores spread over banks
     __shared__ __align__(16) float Xs[RG_BK][RG_BT];
-    __shared__ __align__(16) uint16_t Ts[RG_BT][RG_BM];  // transposed BF16 tile
     const int rb = blockIdx.x, tb = blockIdx.y;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int64_t t0 = static_cast<int64_t>(tb) * RG_BT;
@@ -75,12 +72,6 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
         float v[8];  // samples tx*4 + j (j < 4) and 64 + tx*4 + (j - 4)
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = r < n ? acc[i][j] - b : 0.f;
-        if (out16t) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                Ts[(j < 4 ? 0 : RG_BT / 2 - 4) + tx * 4 + j][ty * 4 + i] =
-                    static_cast<uint16_t>(pack_bf16x2(v[j], 0.f) & 0xffffu);
-        }
         if (r >= n_pad) continue;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -109,52 +100,13 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const double* __restrict
             }
         }
     }
-    if (out16t) {
-        // sample t of this tile: 64 consecutive reduced-dimension entries = 128 contiguous bytes
-        __syncthreads();
-        for (int e = threadIdx.x; e < RG_BT * (RG_BM / 8); e += 256) {
-            const int ts = e / (RG_BM / 8), c8 = (e % (RG_BM / 8)) * 8;
-            const int64_t t = t0 + ts;
-            if (t < T)
-                *reinterpret_cast<uint4*>(out16t + t * ld16t + rb * RG_BM + c8) =
-                    *reinterpret_cast<const uint4*>(&Ts[ts][c8]);
-        }
-    }
-}
-
-// Xt (T x ldt, BF16) = transpose of Xn (n_pad x ldx, BF16) for the first 64-multiple of n_pad
-// columns (zero beyond n_pad).
-__global__ void __launch_bounds__(256) transpose_bf16_kernel(const uint16_t* __restrict__ Xn, int n_pad, int64_t T,
-                                                             int64_t ldx, uint16_t* __restrict__ Xt, int64_t ldt) {
-    __shared__ uint16_t tile[64][65];
-    const int rb = blockIdx.x;                       // block of 64 reduced-dimension rows
-    const int64_t t0 = static_cast<int64_t>(blockIdx.y) * 64;
-    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
-        const int r = e / 64, c = e % 64;
-        const int rr = rb * 64 + r;
-        const int64_t t = t0 + c;
-        tile[r][c] = (rr < n_pad && t < T) ? Xn[rr * ldx + t] : static_cast<uint16_t>(0);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
-        const int c = e / 64, r = e % 64;
-        const int64_t t = t0 + c;
-        if (t < T) Xt[t * ldt + rb * 64 + r] = tile[r][c];
-    }
-}
-
-cudaError_t launch_transpose_bf16(cudaStream_t s, const uint16_t* Xn, int n_pad, int64_t T, int64_t ldx, uint16_t* Xt,
-                                  int64_t ldt) {
-    dim3 grid((n_pad + 63) / 64, static_cast<unsigned>((T + 63) / 64));
-    transpose_bf16_kernel<<<grid, 256, 0, s>>>(Xn, n_pad, T, ldx, Xt, ldt);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_rows_gemm(cudaStream_t s, const double* G, int n, int n_pad, int N, const float* X, int64_t T,
                              int64_t ldxin, const double* bias, float* out32, int64_t ld32, uint16_t* out16,
-                             int64_t ld16, uint16_t* out16t, int64_t ld16t) {
+                             int64_t ld16) {
     dim3 grid((n_pad + RG_BM - 1) / RG_BM, static_cast<unsigned>((T + RG_BT - 1) / RG_BT));
-    rows_gemm_kernel<<<grid, 256, 0, s>>>(G, n, N, X, T, ldxin, bias, out32, ld32, out16, ld16, out16t, ld16t, n_pad);
+    rows_gemm_kernel<<<grid, 256, 0, s>>>(G, n, N, X, T, ldxin, bias, out32, ld32, out16, ld16, n_pad);
     return cudaGetLastError();
 }
 

@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
 template <int TC, int NB>
 static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p,
                                      int* resident) {
-    const TcLayout L = tc_layout(p.n_pad, false, TC, NB, false, 1024u);  // + the compaction's static scratch
+    const TcLayout L = tc_layout(p.n_pad, false, TC, NB, 1024u);  // + the compaction's static scratch
     if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
     cudaError_t e = allow_max_dyn_smem(stage_tc_kernel<TC, NB>);
     if (e != cudaSuccess) return e;

@@ -26,21 +26,17 @@
 
 namespace ica {
 
-// Optional K-major operand for the first product from a transposed copy of X~. Measured on GB300
-// the MN-major read of the X~ tile is as fast, so the copy is not used (saves its traffic).
 int tc_chunk(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_CHUNK : (n_pad <= 128 ? 128 : 64); }
 int tc_buffers(int n_pad) { return n_pad <= 64 ? ICA_TC_SMALL_NB : 2; }
-bool tc_transposed(int n_pad) { return false; }
 size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out) {
-    const TcLayout L = tc_layout(n_pad, moments_only, tc_chunk(n_pad), tc_buffers(n_pad), tc_transposed(n_pad));
+    const TcLayout L = tc_layout(n_pad, moments_only, tc_chunk(n_pad), tc_buffers(n_pad));
     if (stages_out) *stages_out = static_cast<int>(L.stages);
     return L.total;
 }
 
-template <int TC, int NB, bool KT, bool MOMENTS_ONLY, bool MOMENTS>
+template <int TC, int NB, bool MOMENTS_ONLY, bool MOMENTS>
 __global__ void __launch_bounds__(kThreads, 1)
-    fused_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap_t,
-                    const float* __restrict__ B32, int ldb,
+    fused_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restrict__ B32, int ldb,
                     const int* __restrict__ act_idx, const int* __restrict__ count_dev, int M_act_host, int n_pad, int64_t T, int chunks_per_split,
                     int total_chunks, int stages, uint32_t a_bytes, uint32_t xsub_bytes, uint32_t xstage_bytes,
                     uint32_t off_x,
@@ -50,7 +46,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t raw_u32 = smem_u32(smem_raw);
     const uint32_t base_u32 = (raw_u32 + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_u32 - raw_u32);
-    const uint32_t xn_bytes = static_cast<uint32_t>(TC / 64) * xsub_bytes;  // X~^T tile follows at xn_bytes
     constexpr uint32_t p_bytes = static_cast<uint32_t>(TC / 64) * 16384u;
     const uint32_t sA = base_u32, sX = base_u32 + off_x, sP = base_u32 + off_p;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + off_bar);
@@ -106,10 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&xmap);
-        if (KT) tma_prefetch_desc(&xmap_t);
-    }
+    if (warp == 0 && lane == 0) tma_prefetch_desc(&xmap);
     if (warp == 1) {
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
@@ -156,10 +148,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int sub = 0; sub < TC / 64; ++sub)
                     tma_load_2d(stage + static_cast<uint32_t>(sub) * xsub_bytes, &xmap, &full[s], tg + sub * 64, 0);
-                if (KT)
-                    for (int kb = 0; kb < (n_pad + 63) / 64; ++kb)
-                        tma_load_2d(stage + xn_bytes + static_cast<uint32_t>(kb * TC) * 128u, &xmap_t, &full[s], kb * 64,
-                                    tg);
                 ++issued;
             }
             // drain: every issued load must land before the CTA can exit
@@ -171,11 +159,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------------ first-product issuer
         if (lane == 0) {
-            constexpr uint32_t id1 = idesc_bf16(128, TC, KT ? 0u : 1u);  // B: X~^T K-major, or X~ MN-major
+            constexpr uint32_t id1 = idesc_bf16(128, TC, 1u);  // B: X~ MN-major
             // Descriptors are built once; a K step only moves the start-address field (address >> 4,
             // bits 0-13), which cannot carry into the next field for shared addresses below 256 KB.
             const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
-            const uint64_t b1_desc = KT ? sw128_desc(sX + xn_bytes, 16u, 1024u) : sw128_desc(sX, xsub_bytes, 1024u);
+            const uint64_t b1_desc = sw128_desc(sX, xsub_bytes, 1024u);
             const uint32_t stage16 = xstage_bytes >> 4;
             const int ksteps1 = n_pad / 16;
             bool ok = true;
@@ -192,16 +180,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int ks = 0; ks < 16; ++ks) {
                     if (ks >= ksteps1) break;
                     const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
-                    const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
-                                              : (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                    const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
                     umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                 }
                 if constexpr (kLoTmem) {
 #pragma unroll
                     for (int ks = 0; ks < 16; ++ks) {
                         if (ks >= ksteps1) break;
-                        const uint32_t b_off = KT ? ((ks >> 2) * static_cast<uint32_t>(TC) * 128u + (ks & 3) * 32u) >> 4
-                                                  : (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                        const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
                         umma_bf16_tmem_a_acc(d1, tmem + kALoCol + static_cast<uint32_t>(ks) * 8u, b1s + b_off, id1);
                     }
                 } else if constexpr (kSplit) {
@@ -396,17 +382,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int TC, int NB, bool KT, bool MO, bool MOM>
-static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const CUtensorMap* xmap_t,
-                                  const float* B32, int ldb,
+template <int TC, int NB, bool MO, bool MOM>
+static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const float* B32, int ldb,
                                   const int* act_idx, const int* count_dev, int M_act, int n_pad, int64_t T,
                                   int splits, int chunks_per_split, int total_chunks, float* part_acc,
                                   float* part_mom, int part_rows, int* status, int shape_ctas = 0,
                                   int* shape_out = nullptr) {
-    const TcLayout L = tc_layout(n_pad, MO, TC, NB, KT);
+    const TcLayout L = tc_layout(n_pad, MO, TC, NB);
     if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
-    if (KT && !xmap_t) return cudaErrorInvalidValue;
-    cudaError_t e = allow_max_dyn_smem(fused_tc_kernel<TC, NB, KT, MO, MOM>);
+    cudaError_t e = allow_max_dyn_smem(fused_tc_kernel<TC, NB, MO, MOM>);
     if (e != cudaSuccess) return e;
     const int tiles_ub = (M_act + kTcRows - 1) / kTcRows;
     const dim3 grid = shape_ctas > 0 ? dim3(tiles_ub > shape_ctas ? tiles_ub : shape_ctas, 1)
@@ -422,48 +406,43 @@ static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = shape_ctas > 0 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, fused_tc_kernel<TC, NB, KT, MO, MOM>, xmap, KT ? *xmap_t : xmap, B32, ldb,
-                              act_idx, count_dev, M_act, n_pad, T, chunks_per_split, total_chunks,
-                              static_cast<int>(L.stages), L.a_bytes, L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p,
-                              L.off_bar, part_acc, part_mom, part_rows, status, shape_ctas, shape_out);
+    return cudaLaunchKernelEx(&cfg, fused_tc_kernel<TC, NB, MO, MOM>, xmap, B32, ldb, act_idx, count_dev, M_act,
+                              n_pad, T, chunks_per_split, total_chunks, static_cast<int>(L.stages), L.a_bytes,
+                              L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p, L.off_bar, part_acc, part_mom,
+                              part_rows, status, shape_ctas, shape_out);
 }
 
 cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
                                    const int* act_idx, const int* count_dev, int M_ub, int n_pad, int64_t T, int ctas,
                                    int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out) {
-    const int TC = tc_chunk(n_pad);
-#define ICA_TC_SHAPED(TCV, NBV)                                                                                     \
-    return moments ? launch_tc_impl<TCV, NBV, false, false, true>(s, xmap, nullptr, B32, ldb, act_idx, count_dev,   \
-                                                                  M_ub, n_pad, T, 0, 0, total_chunks, part_acc,      \
-                                                                  part_mom, 0, status, ctas, shape_out)              \
-                   : launch_tc_impl<TCV, NBV, false, false, false>(s, xmap, nullptr, B32, ldb, act_idx, count_dev,  \
-                                                                   M_ub, n_pad, T, 0, 0, total_chunks, part_acc,     \
-                                                                   part_mom, 0, status, ctas, shape_out)
+#define ICA_TC_SHAPED(TCV, NBV)                                                                                   \
+    return moments ? launch_tc_impl<TCV, NBV, false, true>(s, xmap, B32, ldb, act_idx, count_dev, M_ub, n_pad, T, \
+                                                           0, 0, total_chunks, part_acc, part_mom, 0, status,     \
+                                                           ctas, shape_out)                                       \
+                   : launch_tc_impl<TCV, NBV, false, false>(s, xmap, B32, ldb, act_idx, count_dev, M_ub, n_pad, T, \
+                                                            0, 0, total_chunks, part_acc, part_mom, 0, status,    \
+                                                            ctas, shape_out)
     if (n_pad <= 64) ICA_TC_SHAPED(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB);
     if (n_pad <= 128) ICA_TC_SHAPED(128, 2);
     ICA_TC_SHAPED(64, 2);
 #undef ICA_TC_SHAPED
-    (void)TC;
 }
 
-cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
-                            const CUtensorMap* xmap_t, const float* B32, int ldb, const int* act_idx,
-                            const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
-                            int total_chunks, float* part_acc, float* part_mom, int part_rows, int* status) {
-    const int TC = tc_chunk(n_pad);
-    const bool KT = xmap_t && tc_transposed(n_pad);
-#define ICA_TC_ARGS s, xmap, xmap_t, B32, ldb, act_idx, count_dev, M_act, n_pad, T, splits, chunks_per_split, \
-                    total_chunks, part_acc, part_mom, part_rows, status
-#define ICA_TC_DISPATCH(TCV, NBV, KTV)                                                                \
+cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap, const float* B32,
+                            int ldb, const int* act_idx, const int* count_dev, int M_act, int n_pad, int64_t T,
+                            int splits, int chunks_per_split, int total_chunks, float* part_acc, float* part_mom,
+                            int part_rows, int* status) {
+#define ICA_TC_ARGS s, xmap, B32, ldb, act_idx, count_dev, M_act, n_pad, T, splits, chunks_per_split, total_chunks, \
+                    part_acc, part_mom, part_rows, status
+#define ICA_TC_DISPATCH(TCV, NBV)                                                                     \
     do {                                                                                            \
-        if (moments_only) return launch_tc_impl<TCV, NBV, KTV, true, true>(ICA_TC_ARGS);            \
-        return moments ? launch_tc_impl<TCV, NBV, KTV, false, true>(ICA_TC_ARGS)                    \
-                       : launch_tc_impl<TCV, NBV, KTV, false, false>(ICA_TC_ARGS);                  \
+        if (moments_only) return launch_tc_impl<TCV, NBV, true, true>(ICA_TC_ARGS);                 \
+        return moments ? launch_tc_impl<TCV, NBV, false, true>(ICA_TC_ARGS)                         \
+                       : launch_tc_impl<TCV, NBV, false, false>(ICA_TC_ARGS);                       \
     } while (0)
-    if (n_pad <= 64) ICA_TC_DISPATCH(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB, false);
-    if (n_pad <= 128 && !KT) ICA_TC_DISPATCH(128, 2, false);
-    if (KT) ICA_TC_DISPATCH(64, 2, true);
-    ICA_TC_DISPATCH(64, 2, false);
+    if (n_pad <= 64) ICA_TC_DISPATCH(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB);
+    if (n_pad <= 128) ICA_TC_DISPATCH(128, 2);
+    ICA_TC_DISPATCH(64, 2);
 #undef ICA_TC_DISPATCH
 #undef ICA_TC_ARGS
 }

@@ -123,7 +123,7 @@ extern "C" int ica_fp_step_noalloc(int precision, const float* B, int M, int n, 
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return ICA_ERR_CUDA;
-        e = launch_fused_tc(s, false, true, map, nullptr, B, n_pad, nullptr, nullptr, M, n_pad, T, splits, cps,
+        e = launch_fused_tc(s, false, true, map, B, n_pad, nullptr, nullptr, M, n_pad, T, splits, cps,
                             static_cast<int>(total), part_acc, part_mom, part_rows, status);
     } else if (few_rows) {
         e = launch_fused_fp32_rows(s, false, B, n_pad, nullptr, nullptr, M, static_cast<const float*>(Xt), ldx, n_pad,

@@ -62,16 +62,14 @@ constexpr int kG2bWarp = 3 + kEpiWarps;  // issues their odd K steps when the is
 constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr uint32_t kScratchBytes = 8192u;  // barriers, TMEM slot, moment exchange
 struct TcLayout {
-    uint32_t a_bytes, xsub_bytes, xn_bytes, xstage_bytes, p_bytes, stages, off_x, off_p, off_bar, total;
+    uint32_t a_bytes, xsub_bytes, xstage_bytes, p_bytes, stages, off_x, off_p, off_bar, total;
 };
 // reserve: bytes of the 227 KB per-CTA shared memory left for the kernel's static shared memory
-TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, bool KT, uint32_t reserve = 0) {
+TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, uint32_t reserve = 0) {
     TcLayout L{};
     L.a_bytes = static_cast<uint32_t>((n_pad + 63) / 64) * 16384u * (tc_split_b(TC) && !tc_lo_in_tmem(TC) ? 2u : 1u);
     L.xsub_bytes = static_cast<uint32_t>(n_pad) * 128u;
-    L.xn_bytes = static_cast<uint32_t>(TC / 64) * L.xsub_bytes;  // X~ tile: n_pad rows x TC samples
-    // + X~^T tile: ceil(n_pad / 64) K-blocks of TC rows x 128 bytes
-    L.xstage_bytes = L.xn_bytes + (KT ? static_cast<uint32_t>((n_pad + 63) / 64) * static_cast<uint32_t>(TC) * 128u : 0u);
+    L.xstage_bytes = static_cast<uint32_t>(TC / 64) * L.xsub_bytes;  // X~ tile: n_pad rows x TC samples
     L.p_bytes = moments_only ? 0u : static_cast<uint32_t>(TC / 64) * 16384u;
     const uint32_t fixed = L.a_bytes + NB * L.p_bytes + kScratchBytes + 1024u;  // + scratch + alignment
     const uint32_t budget = 227u * 1024u - reserve;

@@ -249,3 +249,21 @@ def test_certify_full_size_eeg_like(ctx):
         assert c.margin >= -1e-4 * max(1.0, abs(c.ups_pick)), c
         assert abs(kurt[c.i] - c.alpha_pick) <= 1e-4 * abs(c.alpha_pick), (c, kurt[c.i])
     assert sum(c.candidates > 1 for c in checks) >= n_ng // 2  # most components compare >1 candidate
+
+
+@pytest.mark.parametrize("L", [1, 3, 10, 30, 100])
+def test_gaussianity_count_sweep(ctx, L):
+    """Section 4.2, second experiment (Fig. 2a): the number of non-Gaussian sources the
+    Gaussianity test (Eq. 3) estimates on the N = 30 data (20 generalised-Gaussian + 10
+    Gaussian sources, T = 10,000) as a function of the number of restarts L. For each L and
+    two random initialisations the GPU fit (BF16 stage + FP32 refinement) must estimate the
+    same count as the FP64 oracle from the same initial restarts, with the same components."""
+    from paper_2408_17118_gb300 import ica
+
+    w = synth.ggd_paper(0, with_gaussians=True, M=L)
+    for run in range(2):
+        B0 = synth.restart_inits(L, 30, 30, 1000 + 17 * run + L)
+        ref, _, _, _ = oracle.order_fit(w.X, L, 30, 30, 1e-6, B0, gauss_test=True)
+        W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, B0=B0, gauss=True, iters=30, tol=1e-6)
+        assert W.shape[0] == ref.W.shape[0], (L, run, W.shape[0], ref.W.shape[0])
+        check_parity(W, kurt, ref, f"L{L} run{run}")

@@ -132,10 +132,12 @@ def test_recorded_features_match_oracle(ica, ctx):
     assert np.all((y == 0) | (y == 1))
 
 
-def _fit(ica, ctx, Xw, w, prune=None, tau=None, record=False):
+def _fit(ica, ctx, Xw, w, prune=None, tau=None, record=False, keep_frac=None):
     opts = ica.ica_default_opts(precision=ica.ICA_BF16)
     if tau is not None:
         opts.prune_tau = tau
+    if keep_frac is not None:
+        opts.prune_keep_frac = keep_frac
     out = ica.ica_order_fit(ctx, Xw, w.M, w.n_components, w.iters, w.tol, 21, opts, prune_params=prune, record=record)
     return out, json.loads(ica.ica_last_stats(ctx))
 
@@ -161,10 +163,7 @@ def test_pruned_fit_matches_unpruned_and_saves_work(ica, ctx, trained):
     (W1, k1), st1 = _fit(ica, ctx, Xw, w, prune=params, tau=tau)
     W0, W1 = W0.cpu().numpy(), W1.cpu().numpy()
     assert W0.shape == W1.shape
-    dots = np.abs(np.sum(W0 * W1, axis=1))
-    # the Gaussian tail (last quarter) has no unique order; the non-Gaussian components must agree
-    ng = int(0.75 * w.X.shape[0])
-    assert np.all(dots[:ng] >= 1 - 1e-5), dots[:ng]
+    _judge(W0, st0, W1, w)
     rows0 = sum(c["rows_updated"] for c in st0["components"])
     rows1 = sum(c["rows_updated"] for c in st1["components"])
     pruned = sum(c["pruned"] for c in st1["components"])
@@ -172,13 +171,53 @@ def test_pruned_fit_matches_unpruned_and_saves_work(ica, ctx, trained):
     assert rows1 < rows0, (rows1, rows0)
 
 
+def _judge(W0, st0, W1, w):
+    """The pruner's judge: every component the Gaussianity test (Eq. 3) calls non-Gaussian in the
+    unpruned fit (Upsilon above 2 (N - i + 2)(N - i + 1) / T) must be the same in the pruned fit,
+    in order; the components after them span the Gaussian subspace, where no direction is unique
+    (Theorem 1), and are not compared."""
+    N, T = w.X.shape
+    ng = 0
+    for c in st0["components"]:
+        if c["upsilon"] < oica.gaussianity_threshold(N, c["i"], T):
+            break
+        ng += 1
+    assert ng >= N // 2, ng  # 3/4 of the sources are non-Gaussian
+    dots = np.abs(np.sum(W0[:ng] * W1[:ng], axis=1))
+    assert np.all(dots >= 1 - 1e-5), dots
+
+
+def test_keep_floor_alone_keeps_the_leaders(ica, ctx, trained):
+    """tau above every probability: the network keeps nothing, so exactly the floor stays - the
+    max(refine_topk, ceil(prune_keep_frac x active)) restarts leading Upsilon at iteration 5 -
+    and the pruned fit still picks the unpruned fit's non-Gaussian components."""
+    import math
+
+    params, _, _ = trained
+    w = synth.eeg_like(32, 50_000, 512, seed=9)
+    Xw = ica.ica_whiten(ctx, torch.from_numpy(w.X).cuda())[0]
+    (W0, k0), st0 = _fit(ica, ctx, Xw, w)
+    (W1, k1), st1 = _fit(ica, ctx, Xw, w, prune=params, tau=1.01, keep_frac=0.05)
+    checked = 0
+    for c in st1["components"]:
+        if c["fallback"] or not c["active"] or c["iterations"] < 5:
+            continue
+        act5 = c["active"][0]  # rows still running at iteration 5, before the pruner
+        if act5 > 0:
+            assert c["pruned"] == act5 - min(act5, max(4, math.ceil(0.05 * act5))), c
+            checked += 1
+    assert checked >= 8
+    _judge(W0.cpu().numpy(), st0, W1.cpu().numpy(), w)
+    assert sum(c["rows_updated"] for c in st1["components"]) < sum(c["rows_updated"] for c in st0["components"])
+
+
 def test_fallback_restores_unpruned_result(ica, ctx, trained):
-    # tau above every probability: the pruner drops every active restart, so every component
-    # must fall back to the unpruned fit, which is deterministic: identical output
+    # tau above every probability and no keep floor: the pruner drops every active restart, so
+    # every component must fall back to the unpruned fit, which is deterministic: identical output
     params, _, _ = trained
     w = synth.eeg_like(16, 20_000, 128, seed=5)
     Xw = ica.ica_whiten(ctx, torch.from_numpy(w.X).cuda())[0]
     (W0, k0), _ = _fit(ica, ctx, Xw, w)
-    (W1, k1), st1 = _fit(ica, ctx, Xw, w, prune=params, tau=1.01)
+    (W1, k1), st1 = _fit(ica, ctx, Xw, w, prune=params, tau=1.01, keep_frac=0.0)
     assert torch.equal(W0, W1) and torch.equal(k0, k1)
     assert all(c["fallback"] == 1 for c in st1["components"] if c["pruned"] > 0)
