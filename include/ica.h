@@ -79,7 +79,8 @@ typedef struct {
     const float* prune_params; /* optional: ICA_MLP_PARAMS floats (device). After the first 5
                               iterations of a component, restarts whose predicted probability of
                               ending at the picked direction is below prune_tau leave the active
-                              set and the pick, except the restarts leading the objective then:
+                              set and the pick (and so do restarts redundant with a leading
+                              one, prune_cos), except the restarts leading the objective then:
                               the max(refine_topk (1 on the FP32 path), ceil(prune_keep_frac x
                               active)) restarts with the largest Upsilon (Eq. 1) at iteration 5
                               always stay. If a pruned restart's kurtosis objective is at
@@ -112,7 +113,11 @@ typedef struct {
                               request, without a fault) */
     float prune_keep_frac; /* fraction of the active restarts, ranked by Upsilon at iteration 5,
                               that the pruner always keeps (default 0.05; 0..1; 0: no floor at
-                              all, the network alone decides) */
+                              all) */
+    float prune_cos;       /* the pruner also drops a restart when another one leading it in
+                              Upsilon at iteration 5 points the same way, |b . b'| >= prune_cos
+                              (it is heading to the same optimum); default 0.99, 0 disables.
+                              The keep floor (prune_keep_frac) overrides it. */
     double* record_cands;  /* optional (device, BF16 path): n_components x refine_topk x N FP64.
                               Row (i, j) = w = G^T b of the j-th distinct candidate of component i
                               after the FP32 refinement (Section 3.3: the candidate in the full
@@ -123,8 +128,8 @@ typedef struct {
 
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
-   no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05), no recording, persistent
-   stage, 2 s wait limit, no stall. */
+   no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05, prune_cos 0.99), no
+   recording, persistent stage, 2 s wait limit, no stall. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */

@@ -42,6 +42,7 @@ class ica_opts(C.Structure):
         ("wait_ns", C.c_int64),
         ("stall_test", C.c_int),
         ("prune_keep_frac", C.c_float),
+        ("prune_cos", C.c_float),
         ("record_cands", C.c_void_p),
     ]
 

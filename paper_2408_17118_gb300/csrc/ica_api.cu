@@ -110,6 +110,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     int n_pad_max = 0, M_pad = 0, part_rows_max = 0;
     int64_t ldx = 0;
+    size_t jscr;  // Jacobi scratch (mixed-precision solver above its shared-memory size)
     size_t status, counts, Xt32, Xt16, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots, pruned,
         part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, comp_rows, total;
 };
@@ -156,6 +157,7 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.t2 = take(sizeof(double) * nN);
     L.t3 = take(sizeof(double) * nN);
     L.t4 = take(sizeof(double) * nN);
+    L.jscr = take(jacobi_scratch_bytes(N));
     L.cov_part = take(sizeof(double) * nN * covariance_splits(N, T));
     L.comp_stats = take(sizeof(double) * 4 * (N + 1));
     L.comp_rows = take(sizeof(long long) * 2 * (N + 1));  // per component: rows updated (stage, refine)
@@ -361,7 +363,7 @@ int deflation_basis_impl(ica_ctx* c, const Layout& L, const double* W, int k, in
     if (k <= n) {
         KL(launch_gemm_f64(s, k, k, n, 1.0, W, N, 1, W, 1, N, 0.0, A, k));   // U U^T
         KL(launch_gemm_f64(s, k, k, n, 1.0, W, N, 1, W, 1, N, 0.0, T4, k));  // kept copy
-        KL(launch_jacobi(s, A, V, lam, k, status, 60));
+        KL(launch_jacobi(s, A, V, lam, k, status, 60, c->ws + L.jscr));
         KL(launch_scale_cols_fn(s, V, lam, k, 1, T1, status, 1e-10));      // Q f(mu)
         KL(launch_gemm_f64(s, k, k, k, 1.0, T1, k, 1, V, 1, k, 0.0, T2, k));  // H = Q f Q^T
         KL(launch_pad_cols(s, W, k, N, n, T3));                              // U~ = [U 0]
@@ -375,7 +377,7 @@ int deflation_basis_impl(ica_ctx* c, const Layout& L, const double* W, int k, in
     KL(launch_set_identity(s, T3, n, N, N, 1.0));
     KL(launch_gemm_f64(s, n, N, k, -1.0, W, 1, N, W, N, 1, 1.0, T3, N));  // F~ = E_n - U^T W
     KL(launch_gemm_f64(s, n, n, N, 1.0, T3, N, 1, T3, 1, N, 0.0, A, n));  // S = F~ F~^T (Gram form)
-    KL(launch_jacobi(s, A, V, lam, n, status, 60));
+    KL(launch_jacobi(s, A, V, lam, n, status, 60, c->ws + L.jscr));
     KL(launch_scale_cols_fn(s, V, lam, n, 0, T1, status, 1e-10));
     KL(launch_gemm_f64(s, n, n, n, 1.0, T1, n, 1, V, 1, n, 0.0, T2, n));  // S^(-1/2)
     KL(launch_gemm_f64(s, n, N, n, 1.0, T2, n, 1, T3, N, 1, 0.0, G, N));  // G = S^(-1/2) F~
@@ -436,6 +438,7 @@ void ica_default_opts(ica_opts* o) {
     o->record_labels = nullptr;
     o->stage_persistent = 1;
     o->prune_keep_frac = 0.05f;
+    o->prune_cos = 0.99f;
 }
 
 const char* ica_status_string(int st) {
@@ -529,7 +532,7 @@ int ica_whiten(ica_ctx* c, const float* X, int N, int64_t T, float* Xw, double* 
     KL(launch_covariance(s, X, mean, N, T, T, at<double>(c, L.cov_part), splits, A));
     ++c->launches;  // partial + reduce
     ++c->launches_total;
-    KL(launch_jacobi(s, A, E, lam, N, status, 60));
+    KL(launch_jacobi(s, A, E, lam, N, status, 60, c->ws + L.jscr));
     KL(launch_scale_cols_fn(s, E, lam, N, 0, T1, status, 1e-12));
     KL(launch_gemm_f64(s, N, N, N, 1.0, T1, N, 1, E, 1, N, 0.0, V, N));     // V = E diag(l^-1/2) E^T
     KL(launch_gemm_f64(s, N, 1, N, 1.0, V, N, 1, mean, 1, 1, 0.0, bias, 1));  // V mean
@@ -642,7 +645,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_PLAIN_FP32) return ICA_ERR_UNSUPPORTED;
     if (o.precision == ICA_BF16 && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
     if (o.wait_ns < 0 || (o.record_cands && o.precision != ICA_BF16)) return ICA_ERR_ARG;
-    if (!(o.prune_keep_frac >= 0.f && o.prune_keep_frac <= 1.f)) return ICA_ERR_ARG;
+    if (!(o.prune_keep_frac >= 0.f && o.prune_keep_frac <= 1.f) || !(o.prune_cos >= 0.f && o.prune_cos <= 1.f))
+        return ICA_ERR_ARG;
     const Layout L = make_layout(N, T, M, o.precision);
     int rc = check_ws(c, L);
     if (rc) return rc;
@@ -724,6 +728,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     const double dT = static_cast<double>(T);
     std::vector<int> comp_iters, comp_refine, comp_pruned, comp_fallback;
     std::vector<double> comp_stage_ms;  // per component: stage (update) time, when profiling
+    std::vector<int> comp_kurt_rows;    // per component: rows of the kurtosis pass
     const bool prune_opt = o.prune_params != nullptr && o.precision != ICA_PLAIN_FP32;
     int* pruned = at<int>(c, L.pruned);
     float* uref = reinterpret_cast<float*>(counts + 12);  // pruner feature reference (one float)
@@ -745,6 +750,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         // look at least as good as the kept ones (prune_check), the component is fitted again
         // without pruning from the same initial restarts (attempt 1).
         int t = 0, rt = 0, n_pruned = 0, fell_back = 0;
+        int kurt_rows = M;  // restarts whose kurtosis the component computed (all, or those the pruner kept)
         long long stage_rows_seen = 0;  // last value read of this component's stage row counter
         long long refine_rows_seen = 0;  // the same for its refinement row counter
         std::vector<int> hist;
@@ -891,7 +897,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                         KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, n,
                                         std::log(static_cast<double>(T)), o.prune_tau, uref, flags, pruned,
                                         o.prune_keep_frac > 0.f ? (bf16 ? o.refine_topk : 1) : 0,
-                                        o.prune_keep_frac));
+                                        o.prune_keep_frac, B32, n_pad, o.prune_cos));
                         KL(launch_compact_keep(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1)));
                         return ICA_OK;
                     });
@@ -909,20 +915,31 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             }
             fa.shape_dev = nullptr;
             // kurtosis of every candidate: converged rows plus rows still running after `iters`
+            // (after pruning: the restarts that stayed; the pruned ones leave the pick)
             {
                 StepShape sh;
-                fa.act = nullptr;
-                fa.count_dev = nullptr;
-                fa.M_act = M;
+                int* kept_list = pruned_now ? act[cur ^ 1] : nullptr;
+                int kept = M;
+                if (pruned_now) {  // the grid is sized for the exact count of restarts that stayed
+                    KL(launch_compact_keep(s, pruned, nullptr, nullptr, M, kept_list, counts + 6, true));
+                    rc = read_count(counts + 6, &kept);
+                    if (rc) return rc;
+                }
+                kurt_rows = kept;
+                fa.act = kept_list;
+                fa.count_dev = pruned_now ? counts + 6 : nullptr;
+                fa.M_act = kept > 0 ? kept : 1;
                 fa.moments_only = true;
-                rc = timed(K_KURT, 2.0 * n * M * dT, [&] { return run_fused(c, L, fa, &sh); });
-                if (rc) return rc;
-                KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, nullptr, nullptr, M, inv_T,
-                                        alpha, ups));
+                if (kept > 0) {
+                    rc = timed(K_KURT, 2.0 * n * kept * dT, [&] { return run_fused(c, L, fa, &sh); });
+                    if (rc) return rc;
+                    KL(launch_kurt_finalize(s, at<float>(c, L.part_mom), sh.splits, sh.part_rows, kept_list,
+                                            fa.count_dev, kept, inv_T, alpha, ups));
+                }
             }
             if (!pruned_now) break;
             int fb = 0;
-            KL(launch_prune_check(s, ups, pruned, M, counts + 4));
+            KL(launch_prune_check(s, ups, pruned, traj, M, counts + 4));
             rc = read_count(counts + 4, &fb);
             if (rc) return rc;
             if (!fb && !dropped_all) break;
@@ -1078,6 +1095,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         comp_refine.push_back(rt);
         comp_pruned.push_back(n_pruned);
         comp_fallback.push_back(fell_back);
+        comp_kurt_rows.push_back(kurt_rows);
         comp_hist.push_back(hist);
         if (o.profile) {
             CK(cudaStreamSynchronize(s));
@@ -1122,7 +1140,8 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     c->kind_flops[K_ITER] = it_flops;
     c->kind_flops[K_REFINE] = ref_flops;
     double kurt_flops = 0.0;
-    for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i) kurt_flops += 2.0 * (N - i) * static_cast<double>(M) * dT;
+    for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i)
+        kurt_flops += 2.0 * (N - i) * static_cast<double>(comp_kurt_rows[i]) * dT;
     c->kind_flops[K_KURT] = kurt_flops;
     std::string js = "{\"components\": [";
     for (int i = 0; i < found; ++i) {

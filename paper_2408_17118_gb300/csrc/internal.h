@@ -78,8 +78,12 @@ cudaError_t launch_row_mean(cudaStream_t s, const float* X, int N, int64_t T, in
 cudaError_t launch_covariance(cudaStream_t s, const float* X, const double* mean, int N, int64_t T,
                               int64_t ld, double* part, int splits, double* C);
 int covariance_splits(int N, int64_t T);
+// Symmetric eigendecomposition A = V diag(lam) V^T (cyclic Jacobi). scratch: device memory of
+// jacobi_scratch_bytes(m) for the mixed-precision solver at m above its shared-memory limit
+// (null: FP64 sweeps only there).
+size_t jacobi_scratch_bytes(int m);
 cudaError_t launch_jacobi(cudaStream_t s, double* A, double* V, double* lam, int m, int* status,
-                          int max_sweeps);
+                          int max_sweeps, void* scratch = nullptr);
 cudaError_t launch_gemm_f64(cudaStream_t s, int rows, int cols, int inner, double alpha, const double* A,
                             int64_t sar, int64_t sac, const double* B, int64_t sbr, int64_t sbc, double beta,
                             double* C, int64_t ldc);
@@ -122,16 +126,23 @@ cudaError_t launch_mlp_forward(cudaStream_t s, const float* params, const float*
 cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float* v, int step, const float* F,
                                   const float* y, int rows, float lr, float pos_weight, bool fp16, float* scratch,
                                   float* loss_out, float* grad_out);
-// keep floor: the max(keep_min, ceil(keep_frac * count)) restarts with the largest Upsilon at
-// iteration kTrajLen (and any tied with the last of them) are always kept
+// Keep set of the pruner after iteration kTrajLen: the network's keeps (p >= tau), minus the
+// restarts dominated by a similar (|cos| >= cos_min; 0 disables) restart leading them in
+// Upsilon, plus the keep floor: the max(keep_min, ceil(keep_frac * count)) restarts with the
+// largest Upsilon at iteration kTrajLen (and any tied with the last of them).
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
                          const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned, int keep_min, float keep_frac);
+                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, float cos_min);
 cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, const float* B32, int ldb, int n, int M,
                           const int* slot, double logT, float* ref, float* F_out, float* y_out);
-cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, int M, int* out);
+// 1 in *out when some pruned restart's Upsilon at iteration kTrajLen (its objective when it was
+// pruned) is at least the best final Upsilon of the restarts that stayed.
+cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, const float* traj, int M,
+                               int* out);
+// Stable compaction of an index list (act_in, or 0..count-1) to the slots whose keep flag is set
+// (invert: whose flag is clear).
 cudaError_t launch_compact_keep(cudaStream_t s, const int* keep, const int* act_in, const int* count_in_dev,
-                                int count_host, int* act_out, int* count_out_dev);
+                                int count_host, int* act_out, int* count_out_dev, bool invert = false);
 
 // Launch shape of a fused tcgen05 update from the device count of active rows (also evaluated
 // by the finalize): tiles of 128 rows, splits of the sample range so that tiles x splits <= ctas

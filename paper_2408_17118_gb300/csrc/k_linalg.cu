@@ -137,9 +137,10 @@ cudaError_t launch_covariance(cudaStream_t s, const float* X, const double* mean
 //      plain FP64 solver.
 // The result is an FP64 eigendecomposition (backward stable: V orthogonal to rounding, A = V
 // diag(lam) V^T to rounding) at about a third of the FP64 work of FP64 sweeps from the start.
-// Larger m runs FP64 sweeps only (matrices in shared memory when they fit, else in global
-// memory, L2 resident).
-constexpr int kJacMixedMin = 12, kJacMixedMax = 80;
+// The four m x m FP64 buffers live in shared memory up to m = kJacSmemMax; above, in a global
+// scratch (L2 resident), with the FP32 phase's two m x m matrices still in shared memory up to
+// m = kJacF32SmemMax. Smaller m, or calls without a scratch, run FP64 sweeps only.
+constexpr int kJacMixedMin = 12, kJacSmemMax = 80, kJacF32SmemMax = 128;
 
 // Pair a of round r in the circle ordering of me = m + (m odd) indices (p < q; q = m is the
 // dummy index of odd m). r, a < me - 1 and a <= (me - 1) / 2, so no modulo is needed.
@@ -420,23 +421,25 @@ __device__ __forceinline__ void jac_gemm(const double* X, const double* Y, doubl
     __syncthreads();
 }
 
-// Mixed-precision solver for kJacMixedMin <= m <= kJacMixedMax (see above). Shared memory:
-// four m x m FP64 buffers P0..P3; the FP32 phase keeps its A and V in P2 and P3.
+// Mixed-precision solver for m >= kJacMixedMin (see above). Four m x m FP64 buffers P0..P3: in
+// shared memory (gP null; the FP32 phase keeps its A and V in P2 and P3), or at gP (4 m^2
+// doubles) with the FP32 A and V in shared memory (f32_smem) or at gP32 (2 m^2 floats).
 __global__ void __launch_bounds__(1024) jacobi_mixed_kernel(double* Ag, double* Vg, double* lam, int m, int* status,
-                                                            int max_sweeps) {
+                                                            int max_sweeps, double* gP, float* gP32, int f32_smem) {
     extern __shared__ double jsm[];
-    __shared__ double rcd[kJacMixedMax / 2], rsd[kJacMixedMax / 2];
-    __shared__ float rcf[kJacMixedMax / 2], rsf[kJacMixedMax / 2];
+    __shared__ double rcd[kMaxN / 2], rsd[kMaxN / 2];
+    __shared__ float rcf[kMaxN / 2], rsf[kMaxN / 2];
     __shared__ double red[64];
     __shared__ int stop;
     const int mm = m * m;
     const int tid = threadIdx.x, nth = blockDim.x;
-    double* P0 = jsm;  // A (FP64, kept)
-    double* P1 = jsm + mm;
-    double* P2 = jsm + 2 * mm;
-    double* P3 = jsm + 3 * mm;
-    float* A32 = reinterpret_cast<float*>(P2);
-    float* V32 = reinterpret_cast<float*>(P3);
+    double* base = gP ? gP : jsm;
+    double* P0 = base;  // A (FP64, kept)
+    double* P1 = base + mm;
+    double* P2 = base + 2 * mm;
+    double* P3 = base + 3 * mm;
+    float* A32 = !gP ? reinterpret_cast<float*>(P2) : (f32_smem ? reinterpret_cast<float*>(jsm) : gP32);
+    float* V32 = !gP ? reinterpret_cast<float*>(P3) : (f32_smem ? reinterpret_cast<float*>(jsm) + mm : gP32 + mm);
     const double scale = jac_scale(Ag, mm, red), unscale = 1.0 / scale;  // powers of two: exact
     for (int i = tid; i < mm; i += nth) {
         const int r = i / m, c = i % m;
@@ -480,14 +483,23 @@ __global__ void __launch_bounds__(1024) jacobi_mixed_kernel(double* Ag, double* 
     }
 }
 
-cudaError_t launch_jacobi(cudaStream_t s, double* A, double* V, double* lam, int m, int* status, int max_sweeps) {
+size_t jacobi_scratch_bytes(int m) {
+    return m > kJacSmemMax ? 4ull * m * m * sizeof(double) + 2ull * m * m * sizeof(float) : 0;
+}
+
+cudaError_t launch_jacobi(cudaStream_t s, double* A, double* V, double* lam, int m, int* status, int max_sweeps,
+                          void* scratch) {
     int threads = m * m / 2;
     threads = threads < 128 ? 128 : (threads > 1024 ? 1024 : round_up(threads, 32));
-    if (m >= kJacMixedMin && m <= kJacMixedMax) {
-        const size_t smem = 4ull * m * m * sizeof(double);
+    if (m >= kJacMixedMin && (m <= kJacSmemMax || scratch)) {
+        const bool in_smem = m <= kJacSmemMax;
+        const bool f32_smem = !in_smem && m <= kJacF32SmemMax;
+        double* gP = in_smem ? nullptr : static_cast<double*>(scratch);
+        float* gP32 = in_smem || f32_smem ? nullptr : reinterpret_cast<float*>(gP + 4ull * m * m);
+        const size_t smem = in_smem ? 4ull * m * m * sizeof(double) : (f32_smem ? 2ull * m * m * sizeof(float) : 0);
         cudaError_t e = allow_max_dyn_smem(jacobi_mixed_kernel);
         if (e != cudaSuccess) return e;
-        jacobi_mixed_kernel<<<1, threads, smem, s>>>(A, V, lam, m, status, max_sweeps);
+        jacobi_mixed_kernel<<<1, threads, smem, s>>>(A, V, lam, m, status, max_sweeps, gP, gP32, f32_smem ? 1 : 0);
         return cudaGetLastError();
     }
     const size_t smem = 2ull * m * m * sizeof(double);

@@ -404,6 +404,89 @@ __global__ void __launch_bounds__(256) keep_top_kernel(const float* __restrict__
         }
 }
 
+// Redundant restarts: active slot j is dominated when another active restart that leads it in
+// Upsilon(alpha at iteration kTrajLen) (larger, or equal with a lower slot) points the same way,
+// |b_j . b_j'| >= cos_min (rows are unit vectors after each update). Distinct optima of the
+// objective are far apart (the sources' unmixing directions are orthogonal in the whitened space),
+// so a dominated restart is heading where a better-placed one already goes; the leader of every
+// such cluster is never dominated. Block: 32 slots j against all slots j' in tiles of 32, rows in
+// shared memory (stride n_pad + 1: conflict-free); stops scanning once all 32 are dominated.
+// Dominated slots leave the keep set (keep[j] = 0, pruned[r] = 1).
+constexpr int kDomTile = 32;
+__global__ void __launch_bounds__(256) dominated_kernel(const float* __restrict__ B32, int ldb, int n,
+                                                        const float* __restrict__ traj,
+                                                        const int* __restrict__ act_idx,
+                                                        const int* __restrict__ count_dev, int count_host,
+                                                        float cos_min, int* __restrict__ keep,
+                                                        int* __restrict__ pruned) {
+    extern __shared__ float dsm[];
+    const int count = count_dev ? *count_dev : count_host;
+    const int j0 = blockIdx.x * kDomTile;
+    if (j0 >= count) return;
+    const int stride = n + 1;
+    float* A = dsm;                          // [32][n + 1] rows of this block's slots
+    float* Bt = dsm + kDomTile * stride;     // [32][n + 1] rows of the scanned tile
+    float* uA = Bt + kDomTile * stride;      // [32] Upsilon of the block's slots
+    float* uB = uA + kDomTile;               // [32] Upsilon of the scanned slots
+    int* dom = reinterpret_cast<int*>(uB + kDomTile);  // [32]
+    __shared__ int all_dom;
+    const int tid = threadIdx.x;
+    auto row_of = [&](int j) { return act_idx ? act_idx[j] : j; };
+    auto u5 = [&](int r) { return upsilon_clamped(traj[(static_cast<int64_t>(r) * kTrajLen + kTrajLen - 1) * 2]); };
+    for (int e = tid; e < kDomTile * n; e += 256) {
+        const int jj = e / n, k = e % n, j = j0 + jj;
+        A[jj * stride + k] = j < count ? B32[static_cast<int64_t>(row_of(j)) * ldb + k] : 0.f;
+    }
+    if (tid < kDomTile) {
+        const int j = j0 + tid;
+        uA[tid] = j < count ? u5(row_of(j)) : -INFINITY;
+        dom[tid] = j < count ? 0 : 1;
+    }
+    // thread: slot jj = tid / 8 of the block, scanned slots (tid % 8) * 4 .. + 3
+    const int jj = tid >> 3, q0 = (tid & 7) * 4;
+    for (int t0 = 0; t0 < count; t0 += kDomTile) {
+        __syncthreads();
+        if (tid == 0) {
+            int a = 1;
+            for (int i = 0; i < kDomTile; ++i) a &= dom[i];
+            all_dom = a;
+        }
+        for (int e = tid; e < kDomTile * n; e += 256) {
+            const int ii = e / n, k = e % n, j = t0 + ii;
+            Bt[ii * stride + k] = j < count ? B32[static_cast<int64_t>(row_of(j)) * ldb + k] : 0.f;
+        }
+        if (tid < kDomTile) {
+            const int j = t0 + tid;
+            uB[tid] = j < count ? u5(row_of(j)) : -INFINITY;
+        }
+        __syncthreads();
+        if (all_dom) break;
+        const int j = j0 + jj;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < n; ++k) {
+            const float a = A[jj * stride + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = fmaf(a, Bt[(q0 + q) * stride + k], d[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jp = t0 + q0 + q;
+            if (j < count && jp < count && jp != j) {
+                const bool leads = uB[q0 + q] > uA[jj] || (uB[q0 + q] == uA[jj] && jp < j);
+                if (leads && fabsf(d[q]) >= cos_min) dom[jj] = 1;  // benign race: every writer stores 1
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < kDomTile) {
+        const int j = j0 + tid;
+        if (j < count && dom[tid]) {
+            keep[j] = 0;
+            pruned[row_of(j)] = 1;
+        }
+    }
+}
+
 // Training record of one component: raw features of every restart and whether the restart
 // ended at the picked direction (|b_r . b_p| >= 1 - 1e-3 on normalised rows).
 __global__ void record_kernel(const float* __restrict__ traj, const float* __restrict__ B32, int ldb, int n_dim, int M,
@@ -426,18 +509,20 @@ __global__ void record_kernel(const float* __restrict__ traj, const float* __res
     y_out[r] = fabsf(dot) >= (1.f - 1e-3f) * sqrtf(nr * np) ? 1.f : 0.f;
 }
 
-// Fallback test of a pruned component: 1 when some pruned restart has a kurtosis objective at
-// least as large as the best kept one (the network may have dropped the global optimum).
-__global__ void prune_check_kernel(const double* __restrict__ ups, const int* __restrict__ pruned, int M,
-                                   int* __restrict__ out) {
+// Fallback test of a pruned component: 1 when some pruned restart's objective when it was pruned
+// (Upsilon at iteration kTrajLen, Eq. 1 with alpha clamped at -1.999) is at least the best final
+// objective of the restarts that stayed (the pruner may have dropped the global optimum). The
+// kurtosis pass covers only the restarts that stayed, so ups holds nothing for the pruned ones.
+__global__ void prune_check_kernel(const double* __restrict__ ups, const int* __restrict__ pruned,
+                                   const float* __restrict__ traj, int M, int* __restrict__ out) {
     __shared__ double bp[256], bk[256];
     double mp = -INFINITY, mk = -INFINITY;
     for (int r = threadIdx.x; r < M; r += blockDim.x) {
-        const double u = ups[r];
         if (pruned[r])
-            mp = fmax(mp, u);
+            mp = fmax(mp, static_cast<double>(
+                              upsilon_clamped(traj[(static_cast<int64_t>(r) * kTrajLen + kTrajLen - 1) * 2])));
         else
-            mk = fmax(mk, u);
+            mk = fmax(mk, ups[r]);
     }
     bp[threadIdx.x] = mp;
     bk[threadIdx.x] = mk;
@@ -508,7 +593,7 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
                          const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned, int keep_min, float keep_frac) {
+                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, float cos_min) {
     upsilon_ref_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, nullptr, ref);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -516,6 +601,16 @@ cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj,
                                                           static_cast<float>(n), static_cast<float>(logT), ref, tau,
                                                           keep, pruned);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (cos_min > 0.f && B32) {
+        const size_t smem = sizeof(float) * (2 * kDomTile * static_cast<size_t>(n + 1) + 2 * kDomTile) +
+                            sizeof(int) * kDomTile;
+        e = allow_max_dyn_smem(dominated_kernel);
+        if (e != cudaSuccess) return e;
+        dominated_kernel<<<(count_host + kDomTile - 1) / kDomTile, 256, smem, s>>>(
+            B32, ldb, n, traj, act_idx, count_dev, count_host, cos_min, keep, pruned);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess || (keep_min <= 0 && !(keep_frac > 0.f))) return e;
     keep_top_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, keep_min, keep_frac, keep, pruned);
     return cudaGetLastError();
@@ -531,8 +626,9 @@ cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, int M, int* out) {
-    prune_check_kernel<<<1, 256, 0, s>>>(ups, pruned, M, out);
+cudaError_t launch_prune_check(cudaStream_t s, const double* ups, const int* pruned, const float* traj, int M,
+                               int* out) {
+    prune_check_kernel<<<1, 256, 0, s>>>(ups, pruned, traj, M, out);
     return cudaGetLastError();
 }
 

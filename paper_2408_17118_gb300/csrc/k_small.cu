@@ -294,14 +294,15 @@ cudaError_t launch_select_clear(cudaStream_t s, int* excluded, const int* init, 
 __global__ void __launch_bounds__(1024) compact_keep_kernel(const int* __restrict__ keep,
                                                             const int* __restrict__ act_in,
                                                             const int* __restrict__ count_in_dev, int count_host,
-                                                            int* __restrict__ act_out, int* count_out_dev) {
+                                                            int* __restrict__ act_out, int* count_out_dev,
+                                                            int invert) {
     __shared__ int warp_tot[32];
     const int count = count_in_dev ? *count_in_dev : count_host;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (count + 1023) / 1024;
     const int b = t * per, e = min(count, b + per);
     int local = 0;
-    for (int i = b; i < e; ++i) local += keep[i] != 0;
+    for (int i = b; i < e; ++i) local += (keep[i] != 0) != (invert != 0);
     int incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -314,12 +315,13 @@ __global__ void __launch_bounds__(1024) compact_keep_kernel(const int* __restric
     for (int ww = 0; ww < w; ++ww) before += warp_tot[ww];
     int pos = before + incl - local;
     for (int i = b; i < e; ++i)
-        if (keep[i]) act_out[pos++] = act_in ? act_in[i] : i;
+        if ((keep[i] != 0) != (invert != 0)) act_out[pos++] = act_in ? act_in[i] : i;
     if (t == 1023) *count_out_dev = before + incl;
 }
 cudaError_t launch_compact_keep(cudaStream_t s, const int* keep, const int* act_in, const int* count_in_dev,
-                                int count_host, int* act_out, int* count_out_dev) {
-    compact_keep_kernel<<<1, 1024, 0, s>>>(keep, act_in, count_in_dev, count_host, act_out, count_out_dev);
+                                int count_host, int* act_out, int* count_out_dev, bool invert) {
+    compact_keep_kernel<<<1, 1024, 0, s>>>(keep, act_in, count_in_dev, count_host, act_out, count_out_dev,
+                                           invert ? 1 : 0);
     return cudaGetLastError();
 }
 
