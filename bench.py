@@ -72,6 +72,13 @@ def parse_args():
     ap.add_argument("--side-steps", type=int, default=2, help="timed steps of the unpruned and e2e legs")
     ap.add_argument("--prune-recall", type=float, default=0.999,
                     help="recall of the training positives that sets the pruner's keep threshold")
+    ap.add_argument("--prune-train", choices=["n256", "c1c3"], default="n256",
+                    help="pruner training shapes: N = 8/64/128 plus a reduced N = 256 case, or N = 8/64/128 only")
+    ap.add_argument("--prune-tau", type=float, default=0.0,
+                    help="keep threshold of the headline's pruner network (0: the network keeps every restart, the "
+                         "keep floor and the redundancy rule prune; <0: the trained threshold)")
+    ap.add_argument("--no-network-leg", action="store_true",
+                    help="skip the leg that times and judges the pruner with the network's trained threshold")
     ap.add_argument("--prune-cos", type=float, default=0.99,
                     help="|cos| at iteration 5 above which a restart led by another one is redundant (0: off)")
     ap.add_argument("--plain-components", type=int, default=-1, metavar="K",
@@ -246,10 +253,11 @@ def log(msg: str):
     print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
-def train_pruner(ctx, dev, seed: int, recall: float = 0.999):
+def train_pruner(ctx, dev, seed: int, recall: float = 0.999, with_n256: bool = True):
     """The learned restart pruner, trained untimed on the method's own restart trajectories from
-    workloads shaped like the small N = 8 mixture and the EEG-like N = 64 and N = 128 cases
-    (seeds disjoint from the timed data). Returns (params, tau, report)."""
+    workloads shaped like the small N = 8 mixture and the EEG-like N = 64 and N = 128 cases, and
+    (with_n256) an EEG-like N = 256 case at reduced T and M (seeds disjoint from the timed data).
+    Returns (params, tau, report)."""
     import torch
 
     import synth
@@ -258,6 +266,8 @@ def train_pruner(ctx, dev, seed: int, recall: float = 0.999):
 
     t0 = time.perf_counter()
     shapes = [synth.small_mixture(seed + 101, iters=30, tol=1e-6), synth.eeg64(seed + 102), synth.eeg128(seed + 103)]
+    if with_n256:  # the N = 256 shape at a fifth of the samples and a quarter of the restarts
+        shapes.append(synth.eeg_like(256, 200_000, 2048, seed=seed + 104))
     sets = [(ica.ica_whiten(ctx, torch.from_numpy(w.X).to(dev))[0], w.M) for w in shapes]
     F, y = pr.collect_sets(ctx, sets, 30, 1e-6, seed=4321)
     t_col = time.perf_counter() - t0
@@ -318,14 +328,14 @@ def judge_same_components(Wu, st_u, Wp, Xw_host):
             if j != i:  # found at another position: a swap with the unpruned pick at position j
                 uj = comps[j]["upsilon"] if j < len(comps) else -math.inf
                 (swapped if abs(uj - comps[i]["upsilon"]) <= tol + upsilon_tie_tol(comps[min(j, len(comps) - 1)]["alpha"])
-                 else bad).append(i + 1)
+                 else bad).append((i + 1, j + 1, comps[i]["upsilon"], uj))
             continue
         # not found: the pruned fit's direction at position i must tie with it in FP64
         if i >= len(Wp):
-            bad.append(i + 1)
+            bad.append((i + 1, None, None, None))
             continue
         uu, up = upsilon64(Wu[i], Xw_host), upsilon64(Wp[i], Xw_host)
-        (replaced if up >= uu - tol else bad).append(i + 1)
+        (replaced if up >= uu - tol else bad).append((i + 1, None, uu, up))
     return {"non_gaussian": ng, "same_position": ng - len(swapped) - len(replaced) - len(bad),
             "swapped_ties": swapped, "replaced_ties": replaced, "failed": bad, "ok": not bad}
 
@@ -364,12 +374,15 @@ def run_ours(args):
     params, tau, train_report = None, None, None
     log(f"workload {w.name} ready")
     if prune:
-        params, tau, train_report = train_pruner(ctx, dev, args.seed, args.prune_recall)
+        params, tau, train_report = train_pruner(ctx, dev, args.seed, args.prune_recall, args.prune_train == "n256")
         log(f"pruner trained: {train_report}")
     # headline: BF16 (+ pruner); profile = 1 records CUDA events around each stage launch on the
     # library's stream inside the timed steps (the roofline's kernel time)
     opts_head = ica.ica_default_opts(precision=ica.ICA_BF16, profile=1)
+    tau_trained = tau
     if prune:
+        if args.prune_tau >= 0:
+            tau = args.prune_tau
         opts_head.prune_tau = tau
         opts_head.prune_cos = args.prune_cos
 
@@ -452,6 +465,18 @@ def run_ours(args):
         unpruned = summary(u_st, u_ms)
         judge = judge_same_components(Wu.cpu().numpy(), u_st[-1], W.cpu().numpy(), Xw.cpu().numpy())
         log(f"unpruned {unpruned} judge {judge}")
+
+    # the pruner with the network's trained threshold: timed once and judged like the headline
+    network = None
+    if prune and not args.no_network_leg and tau_trained is not None and tau_trained != tau:
+        opts_n = ica.ica_default_opts(precision=ica.ICA_BF16)
+        opts_n.prune_tau = tau_trained
+        opts_n.prune_cos = args.prune_cos
+        n_ms, n_st, (Wn, kn, _), _ = timed_steps(opts_n, params, 1)
+        network = summary(n_st, n_ms)
+        network["tau"] = tau_trained
+        network["judge"] = judge_same_components(Wu.cpu().numpy(), u_st[-1], Wn.cpu().numpy(), Xw.cpu().numpy())
+        log(f"network leg {network}")
 
     # e2e through the public API with host buffers: H2D of X (pinned), whiten + fit, D2H of W, kurt
     e2e_ms, e2e_flops = [], 0.0
@@ -562,12 +587,15 @@ def run_ours(args):
             "data": "synthetic (seeded generators, synth/; stands in for the paper's EEG recordings)",
             "config": {"workload": workload_desc(w), "components_fitted": K,
                        "precision": "bf16 tcgen05 + fp32 refinement",
-                       "pruner": "on (trained untimed on N=8/64/128 trajectories)" if prune else "off",
+                       "pruner": (f"on: keep floor {opts_head.prune_keep_frac:g} + redundancy |cos| >= "
+                                  f"{args.prune_cos:g}, network threshold {tau:g} (trained untimed; see "
+                                  f"pruner_network_leg for its trained threshold)") if prune else "off",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "time_to_all_components_s": head["time_to_all_components_s"],
             "nominal_tflops": nominal_all / (total_ms_max / 1e3) / 1e12,
             "headline": head, "unpruned": unpruned, "pruner_judge": judge, "pruner_training": train_report,
+            "pruner_network_leg": network,
             "plain_fp32": plain,
             "speedup_vs_plain_fp32": (plain["time_to_all_components_s"] / head["time_to_all_components_s"]
                                       if plain["components"] == K else plain["speedup_same_components"])

@@ -69,7 +69,8 @@ typedef struct {
     double refine_tol;     /* BF16: convergence tolerance of the FP32 refinement */
     double fp32_tol_floor; /* FP32 stages never use a tolerance below this (FP32 rounding) */
     const float* B0;       /* optional: n_components x M x N initial restarts (device, FP32);
-                              component i uses the first N-i entries of each row. NULL: draw
+                              component i uses the first N-i entries of each row (all N with
+                              algorithm 1). NULL: draw
                               them from Philox4x32-10 keyed by the seed (ica_init_restarts). */
     int max_splits;        /* 0: automatic split of the sample range; >0 caps it (tests) */
     int profile;           /* 1: time every fused launch with CUDA events on the context stream
@@ -118,6 +119,18 @@ typedef struct {
                               Upsilon at iteration 5 points the same way, |b . b'| >= prune_cos
                               (it is heading to the same optimum); default 0.99, 0 disables.
                               The keep floor (prune_keep_frac) overrides it. */
+    int algorithm;         /* 2 (default): Algorithm 2, each component on the reduced data X~ = G Xw
+                              (Section 3.3, n = N - i + 1 dimensions). 1: Algorithm 1's form (the
+                              "threads" ordering ICA, run here as one batch): every iteration on
+                              the full whitened data (n = N), each update projected onto the
+                              complement of the found components, w <- w - W^T (W w); the initial
+                              restarts are N-dimensional (B0 rows use all N entries) and projected
+                              the same way. Same fixed points, (N / n) times the work per
+                              iteration (the comparison variant of Section 4). */
+    int stage_lo_from;     /* BF16 stage: iterations t >= stage_lo_from (0-based) feed the restart
+                              rows to the first product as two BF16 terms (hi + lo, about 16
+                              bits: rows can converge to stage_tol); earlier ones as one BF16
+                              term, which is enough far from convergence (default 3) */
     double* record_cands;  /* optional (device, BF16 path): n_components x refine_topk x N FP64.
                               Row (i, j) = w = G^T b of the j-th distinct candidate of component i
                               after the FP32 refinement (Section 3.3: the candidate in the full
@@ -129,7 +142,7 @@ typedef struct {
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
    no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05, prune_cos 0.99), no
-   recording, persistent stage, 2 s wait limit, no stall. */
+   recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 3. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */

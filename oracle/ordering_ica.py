@@ -136,13 +136,16 @@ def canonical_sign(w: np.ndarray) -> np.ndarray:
 
 
 def ordering_ica_original(Xw: np.ndarray, L: int, K: int, eps: float, B0: np.ndarray,
-                          n_components: int | None = None, gauss_test: bool = False) -> FitResult:
+                          n_components: int | None = None, gauss_test: bool = False,
+                          full_init: bool = False) -> FitResult:
     """Algorithm 1 on whitened Xw with explicit initial restarts.
 
     B0[i] holds the initialisations for component i. For comparison with Algorithm 2 the
     initial vector of restart l is w = G^T b0 where b0 = B0[i, l, :N-i] and G is the reduction
     basis of Section 3.3 (at i = 0, G = I); that w lies in the complement of the found
-    components, so the projection in FastICA leaves it unchanged.
+    components, so the projection in FastICA leaves it unchanged. With full_init the initial
+    vector is the N-dimensional b0 = B0[i, l, :N] itself (Algorithm 1's random w), which the
+    FastICA run first projects onto the complement of the found components.
     """
     Xw = np.asarray(Xw, dtype=F64)
     N, T = Xw.shape
@@ -157,7 +160,7 @@ def ordering_ica_original(Xw: np.ndarray, L: int, K: int, eps: float, B0: np.nda
         ws, alpha, its = [], np.empty(L), np.empty(L, dtype=np.int64)
         n_conv = 0
         for l in range(L):
-            w0 = G.T @ np.asarray(B0[i - 1, l, :n], dtype=F64)
+            w0 = np.asarray(B0[i - 1, l, :N], dtype=F64) if full_init else G.T @ np.asarray(B0[i - 1, l, :n], dtype=F64)
             w, y, t, done = fastica_run(w0, Xw, E, K, eps)
             ws.append(w)
             alpha[l] = kurtosis_alpha(y)
@@ -328,11 +331,12 @@ def fast_ordering_ica(Xw: np.ndarray, L: int, K: int, eps: float, B0: np.ndarray
 
 
 def order_fit(X: np.ndarray, M: int, n_components: int, iters: int, tol: float, B0: np.ndarray,
-              gauss_test: bool = False, algorithm: int = 2, record: bool = False):
-    """Whiten raw X, then run Algorithm 2 (default) or Algorithm 1. Returns (result, Xw, V, mean)."""
+              gauss_test: bool = False, algorithm: int = 2, record: bool = False, full_init: bool = False):
+    """Whiten raw X, then run Algorithm 2 (default) or Algorithm 1 (full_init: N-dimensional
+    initial vectors). Returns (result, Xw, V, mean)."""
     Xw, V, mean = whiten(X)
     fit = fast_ordering_ica if algorithm == 2 else ordering_ica_original
-    kw = {"record": record} if algorithm == 2 else {}
+    kw = {"record": record} if algorithm == 2 else {"full_init": full_init}
     return fit(Xw, M, iters, tol, B0, n_components=n_components, gauss_test=gauss_test, **kw), Xw, V, mean
 
 

@@ -111,6 +111,7 @@ struct Layout {
     int n_pad_max = 0, M_pad = 0, part_rows_max = 0;
     int64_t ldx = 0;
     size_t jscr;  // Jacobi scratch (mixed-precision solver above its shared-memory size)
+    size_t W32;   // Algorithm 1: FP32 copy of the found components (N x n_pad_max)
     size_t status, counts, Xt32, Xt16, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots, pruned,
         part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, comp_rows, total;
 };
@@ -158,6 +159,7 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.t3 = take(sizeof(double) * nN);
     L.t4 = take(sizeof(double) * nN);
     L.jscr = take(jacobi_scratch_bytes(N));
+    L.W32 = take(sizeof(float) * static_cast<size_t>(N) * L.n_pad_max);
     L.cov_part = take(sizeof(double) * nN * covariance_splits(N, T));
     L.comp_stats = take(sizeof(double) * 4 * (N + 1));
     L.comp_rows = take(sizeof(long long) * 2 * (N + 1));  // per component: rows updated (stage, refine)
@@ -247,6 +249,7 @@ struct FusedArgs {
     int64_t ldx = 0;
     int max_splits = 0;
     int* shape_dev = nullptr;  // BF16 update: shape the launch on the device, write {splits, part_rows} here
+    bool use_lo = true;        // BF16 update: the restart rows' low BF16 term enters the first product
     bool pdl = false;          // FP32 few-row update: programmatic dependent launch after the previous kernel
 };
 
@@ -264,7 +267,8 @@ int run_fused(ica_ctx* c, const Layout& L, const FusedArgs& a, StepShape* shape)
             int rc = encode_xmap(c, &map, a.Xt16, a.n_pad, a.T, a.ldx);
             if (rc) return rc;
             KL(launch_fused_tc_shaped(s, a.moments, map, a.B32, a.ldb, a.act, a.count_dev, a.M_act, a.n_pad, a.T,
-                                      152 / c->cta_div, static_cast<int>(total), pacc, pmom, status, a.shape_dev));
+                                      152 / c->cta_div, static_cast<int>(total), pacc, pmom, status, a.shape_dev,
+                                      a.use_lo));
             shape->splits = -1;  // on the device (a.shape_dev)
             shape->cps = -1;
             shape->part_rows = -1;
@@ -439,6 +443,8 @@ void ica_default_opts(ica_opts* o) {
     o->stage_persistent = 1;
     o->prune_keep_frac = 0.05f;
     o->prune_cos = 0.99f;
+    o->algorithm = 2;
+    o->stage_lo_from = 3;
 }
 
 const char* ica_status_string(int st) {
@@ -645,6 +651,9 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_PLAIN_FP32) return ICA_ERR_UNSUPPORTED;
     if (o.precision == ICA_BF16 && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
     if (o.wait_ns < 0 || (o.record_cands && o.precision != ICA_BF16)) return ICA_ERR_ARG;
+    if (o.algorithm != 1 && o.algorithm != 2) return ICA_ERR_ARG;
+    if (o.stage_lo_from < 0) return ICA_ERR_ARG;
+    const bool alg1 = o.algorithm == 1;
     if (!(o.prune_keep_frac >= 0.f && o.prune_keep_frac <= 1.f) || !(o.prune_cos >= 0.f && o.prune_cos <= 1.f))
         return ICA_ERR_ARG;
     const Layout L = make_layout(N, T, M, o.precision);
@@ -673,6 +682,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     int* cand_list = at<int>(c, L.slots) + 32;
     int* slots = at<int>(c, L.slots);
     double* G = at<double>(c, L.G);
+    float* W32 = at<float>(c, L.W32);
     double* cstats = at<double>(c, L.comp_stats);
     long long* crows = at<long long>(c, L.comp_rows);
     const int64_t ldx = L.ldx;
@@ -736,16 +746,22 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     long long persist_launches = 0;  // persistent BF16 stage launches of this fit
     int found = 0;
     for (int i = 0; i < n_components; ++i) {
-        const int n = N - i;
+        // Algorithm 2: reduced dimension n = N - i. Algorithm 1: every iteration on the full
+        // whitened data (n = N, G = I, X~ = Xw, formed once), the found components projected out
+        // of every update (Wp, the FP32 copy of W).
+        const int n = alg1 ? N : N - i;
         const int n_pad = round_up(n, 16);
-        // reduction basis and X~ = G Xw (Section 3.3)
-        rc = timed(K_BASIS, 0.0, [&] { return deflation_basis_impl(c, L, W_out, i, N, G); });
-        if (rc) return rc;
-        rc = timed(K_REDUCE, 0.0, [&] {
-            KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx));
-            return ICA_OK;
-        });
-        if (rc) return rc;
+        const float* Wp = alg1 && i > 0 ? W32 : nullptr;
+        if (!alg1 || i == 0) {
+            // reduction basis and X~ = G Xw (Section 3.3)
+            rc = timed(K_BASIS, 0.0, [&] { return deflation_basis_impl(c, L, W_out, i, N, G); });
+            if (rc) return rc;
+            rc = timed(K_REDUCE, 0.0, [&] {
+                KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx));
+                return ICA_OK;
+            });
+            if (rc) return rc;
+        }
         // Attempt 0 may run the learned pruner after kTrajLen iterations; when the pruned restarts
         // look at least as good as the kept ones (prune_check), the component is fitted again
         // without pruning from the same initial restarts (attempt 1).
@@ -765,6 +781,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             // initial restarts
             KL(launch_init_restarts(s, seed, i, M, n, n_pad, o.B0 ? o.B0 + static_cast<int64_t>(i) * M * N : nullptr, N,
                                     B32));
+            if (Wp) KL(launch_project_rows(s, B32, n_pad, M, n, Wp, i, n_pad));
             CK(cudaMemsetAsync(itc, 0, sizeof(int) * M, s));
             CK(cudaMemsetAsync(traj, 0, sizeof(float) * M * kTrajLen * 2, s));
             KL(launch_iota(s, act[0], M, counts + 0));
@@ -819,6 +836,10 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     sl.tol = tol_iter;
                     sl.wait_ns = static_cast<uint64_t>(o.wait_ns);
                     sl.stall = o.stall_test != 0;
+                    sl.Wp = Wp;
+                    sl.nw = i;
+                    sl.ldw = n_pad;
+                    sl.lo_from = o.stage_lo_from;
                     CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
                     cudaError_t le = cudaSuccess;
                     int resident = 0;
@@ -867,6 +888,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     fa.M_act = M_host;
                     fa.moments_only = false;
                     fa.moments = t < kTrajLen;
+                    fa.use_lo = t >= o.stage_lo_from;
                     rc = timed(K_ITER, 4.0 * n * M_host * dT, [&] { return run_fused(c, L, fa, &sh); });
                     if (rc) return rc;
                     rc = timed(K_FINALIZE, 0.0, [&] {
@@ -878,7 +900,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                                            // the persistent stage's summation order when this
                                            // context may run it (identical results either way),
                                            // else four virtual warps per row
-                                           fa.shape_dev && c->cta_div == 1 ? 152 : 0));
+                                           fa.shape_dev && c->cta_div == 1 ? 152 : 0, Wp, i, n_pad));
                         return ICA_OK;
                     });
                     if (rc) return rc;
@@ -894,10 +916,10 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     // learned pruner on the first kTrajLen iterations' trajectories
                     int before = M_host;
                     rc = timed(K_PRUNE, 0.0, [&] {
-                        KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, n,
+                        KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, N - i,
                                         std::log(static_cast<double>(T)), o.prune_tau, uref, flags, pruned,
                                         o.prune_keep_frac > 0.f ? (bf16 ? o.refine_topk : 1) : 0,
-                                        o.prune_keep_frac, B32, n_pad, o.prune_cos));
+                                        o.prune_keep_frac, B32, n_pad, n, o.prune_cos, excl));
                         KL(launch_compact_keep(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1)));
                         return ICA_OK;
                     });
@@ -914,6 +936,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                 }
             }
             fa.shape_dev = nullptr;
+            fa.use_lo = true;
             // kurtosis of every candidate: converged rows plus rows still running after `iters`
             // (after pruning: the restarts that stayed; the pruned ones leave the pick)
             {
@@ -999,6 +1022,9 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                 rl.t_end = refine_iters;
                 rl.inv_T = static_cast<float>(inv_T);
                 rl.tol = static_cast<float>(tol_ref);
+                rl.Wp = Wp;
+                rl.nw = i;
+                rl.ldw = n_pad;
                 rl.wait_ns = static_cast<uint64_t>(o.wait_ns);
                 CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
                 cudaError_t le = cudaSuccess;
@@ -1054,7 +1080,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     KL(launch_finalize(s, at<float>(c, L.part_acc), at<float>(c, L.part_mom), sh.splits, sh.part_rows,
                                        n_pad, n, act[rcur], counts + rcur, R_host, B32, n_pad, inv_T, tol_ref, flags,
                                        itc, nullptr, kTrajLen, status, act[rcur ^ 1], counts + (rcur ^ 1),
-                                       crows + 2 * i + 1, done_ctr, nullptr, true));
+                                       crows + 2 * i + 1, done_ctr, nullptr, true, 0, Wp, i, n_pad));
                     return ICA_OK;
                 });
                 if (rc) return rc;
@@ -1088,6 +1114,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
         // w_i = b_p G appended to W (Algorithm 2)
         rc = timed(K_APPEND, 0.0, [&] {
             KL(launch_append(s, G, n, N, B32, n_pad, slots, alpha, ups, W_out, i, kurt_out + i, cstats + 4 * i));
+            if (alg1) KL(launch_w_to_f32(s, W_out, i, N, W32, n_pad));
             return ICA_OK;
         });
         if (rc) return rc;
@@ -1134,14 +1161,14 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     // algorithmic FLOPs from the exact per-component counts of updated rows (4 n rows T)
     double it_flops = 0.0, ref_flops = 0.0;
     for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i) {
-        it_flops += 4.0 * (N - i) * static_cast<double>(rows_h[2 * i]) * dT;
-        ref_flops += 4.0 * (N - i) * static_cast<double>(rows_h[2 * i + 1]) * dT;
+        it_flops += 4.0 * (alg1 ? N : N - i) * static_cast<double>(rows_h[2 * i]) * dT;
+        ref_flops += 4.0 * (alg1 ? N : N - i) * static_cast<double>(rows_h[2 * i + 1]) * dT;
     }
     c->kind_flops[K_ITER] = it_flops;
     c->kind_flops[K_REFINE] = ref_flops;
     double kurt_flops = 0.0;
     for (int i = 0; i < static_cast<int>(comp_iters.size()); ++i)
-        kurt_flops += 2.0 * (N - i) * static_cast<double>(comp_kurt_rows[i]) * dT;
+        kurt_flops += 2.0 * (alg1 ? N : N - i) * static_cast<double>(comp_kurt_rows[i]) * dT;
     c->kind_flops[K_KURT] = kurt_flops;
     std::string js = "{\"components\": [";
     for (int i = 0; i < found; ++i) {

@@ -44,7 +44,7 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
                             unsigned int* done_ctr, const int* shape_dev = nullptr, bool pdl = false,
-                            int vw_ctas = 0);
+                            int vw_ctas = 0, const float* Wp = nullptr, int nw = 0, int ldw = 0);
 // Order of the compensated sums over split partials in the BF16 stage's row completion: the
 // number of virtual warps V per row (split s goes to virtual warp s mod V; the V sums are added
 // in order). More virtual warps when few rows share the GPU, so that the persistent stage kernel
@@ -69,6 +69,10 @@ cudaError_t launch_exclude(cudaStream_t s, const float* B32, int ldb, int n, int
 cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
                           const int* p_slot, const double* alpha, const double* ups, double* W, int i,
                           double* kurt_out, double* comp_stats);
+// Algorithm 1 helpers: rows of B (M x ldb, first n entries) projected onto the complement of the
+// nw FP32 rows of W32 (ld ldw) and normalised; row i of the FP64 W (ld N) converted to FP32 (ld ldw).
+cudaError_t launch_project_rows(cudaStream_t s, float* B32, int ldb, int M, int n, const float* W32, int nw, int ldw);
+cudaError_t launch_w_to_f32(cudaStream_t s, const double* W, int i, int N, float* W32, int ldw);
 cudaError_t launch_record_cands(cudaStream_t s, const double* G, int n, int N, const float* B32, int ldb,
                                 const int* cand, int k, double* out);
 
@@ -132,7 +136,8 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 // largest Upsilon at iteration kTrajLen (and any tied with the last of them).
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
                          const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, float cos_min);
+                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, int row_n,
+                         float cos_min, int* order);  // order: scratch of count ints (sorted test)
 cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, const float* B32, int ldb, int n, int M,
                           const int* slot, double logT, float* ref, float* F_out, float* y_out);
 // 1 in *out when some pruned restart's Upsilon at iteration kTrajLen (its objective when it was
@@ -163,9 +168,11 @@ int tc_chunk(int n_pad);
 int tc_buffers(int n_pad);
 size_t tc_smem_bytes(int n_pad, bool moments_only, int* stages_out);
 // xmap: X~ (n_pad x T, samples contiguous), box {64, n_pad}.
+// use_lo = false: the restart rows enter the first product as one BF16 term (their high term).
 cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
                                    const int* act_idx, const int* count_dev, int M_ub, int n_pad, int64_t T, int ctas,
-                                   int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out);
+                                   int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out,
+                                   bool use_lo = true);
 cudaError_t launch_fused_tc(cudaStream_t s, bool moments_only, bool moments, const CUtensorMap& xmap,
                             const float* B32, int ldb, const int* act_idx,
                             const int* count_dev, int M_act, int n_pad, int64_t T, int splits, int chunks_per_split,
@@ -198,6 +205,9 @@ struct StageLaunch {
     double inv_T, tol;
     uint64_t wait_ns;  // limit of the kernel's waits (0: ICA_WAIT_NS); its teardown drains keep ICA_WAIT_NS
     int stall;         // test hook: 1 makes the first grid barrier wait for an arrival that never comes
+    const float* Wp;   // Algorithm 1: found components (nw rows, ld ldw, FP32) projected out of each update
+    int nw, ldw;
+    int lo_from;       // iterations t >= lo_from add the restart rows' low BF16 term (0: every iteration)
 };
 // resident (optional) receives the number of CTAs of the kernel that fit the GPU at once.
 cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident = nullptr);
@@ -231,6 +241,8 @@ struct RefineLaunch {
     int t_begin, t_end;
     float inv_T, tol;
     uint64_t wait_ns;  // limit of the grid barriers (0: ICA_WAIT_NS)
+    const float* Wp;   // Algorithm 1: found components (nw rows, ld ldw, FP32) projected out of each update
+    int nw, ldw;
 };
 cudaError_t launch_refine_fp32(cudaStream_t s, const RefineLaunch& p, int* resident = nullptr);
 

@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(256, 2) refine_fp32_kernel(RefineLaunch a, int
                 float accv[8], e2, e4;
                 row_combine(rsm, 32, a.n_pad, a.n, false, accv, &e2, &e4);
                 finish_row_loaded(accv, b, nq, a.n, r, j, a.B32, a.ldb, a.inv_T, a.tol, a.flags, a.iters, nullptr,
-                                  kTrajLen, false, 0.f, 0.f, a.status);
+                                  kTrajLen, false, 0.f, 0.f, a.status, RowProj{a.Wp, a.Wp ? a.nw : 0, a.ldw});
             }
         }
         target += static_cast<unsigned int>(G);

@@ -487,6 +487,118 @@ __global__ void __launch_bounds__(256) dominated_kernel(const float* __restrict_
     }
 }
 
+// The same test in leading order: the active slots sorted by Upsilon(alpha at iteration kTrajLen),
+// descending (ties to the lower slot), by one block (bitonic sort of 64-bit keys in shared
+// memory, count <= kDomSortMax). Block b then takes the sorted positions 32 b .. 32 b + 31 and
+// scans only the positions before them, tile by tile from the top, stopping once all 32 are
+// dominated: a dominated restart usually meets its leader early, and no pair is tested twice.
+constexpr int kDomSortMax = 16384;
+__device__ __forceinline__ uint32_t desc_key(float u) {
+    // order-preserving map of u to an unsigned key, complemented so that larger u sort first;
+    // NaN sorts last
+    if (u != u) return 0xffffffffu;
+    const uint32_t b = __float_as_uint(u);
+    const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return ~asc;
+}
+__global__ void __launch_bounds__(1024) lead_sort_kernel(const float* __restrict__ traj, const int* __restrict__ act_idx,
+                                                         const int* __restrict__ count_dev, int count_host,
+                                                         int* __restrict__ order) {
+    extern __shared__ unsigned long long keys[];
+    const int count = count_dev ? *count_dev : count_host;
+    if (count > kDomSortMax) return;
+    int P = 1;
+    while (P < count) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        if (i < count) {
+            const int r = act_idx ? act_idx[i] : i;
+            const float u = upsilon_clamped(traj[(static_cast<int64_t>(r) * kTrajLen + kTrajLen - 1) * 2]);
+            keys[i] = (static_cast<unsigned long long>(desc_key(u)) << 32) | static_cast<uint32_t>(i);
+        } else {
+            keys[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int jb = k >> 1; jb > 0; jb >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int l = i ^ jb;
+                if (l > i) {
+                    const unsigned long long a = keys[i], b = keys[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < count; i += blockDim.x) order[i] = static_cast<int>(keys[i] & 0xffffffffu);
+}
+__global__ void __launch_bounds__(256) dominated_sorted_kernel(const float* __restrict__ B32, int ldb, int n,
+                                                               const int* __restrict__ order,
+                                                               const int* __restrict__ act_idx,
+                                                               const int* __restrict__ count_dev, int count_host,
+                                                               float cos_min, int* __restrict__ keep,
+                                                               int* __restrict__ pruned) {
+    extern __shared__ float dsm[];
+    const int count = count_dev ? *count_dev : count_host;
+    const int p0 = blockIdx.x * kDomTile;
+    if (p0 >= count || count > kDomSortMax) return;
+    const int stride = n + 1;
+    float* A = dsm;
+    float* Bt = dsm + kDomTile * stride;
+    int* dom = reinterpret_cast<int*>(Bt + kDomTile * stride);
+    __shared__ int all_dom;
+    const int tid = threadIdx.x;
+    auto row_at = [&](int pos) {
+        const int j = order[pos];
+        return act_idx ? act_idx[j] : j;
+    };
+    for (int e = tid; e < kDomTile * n; e += 256) {
+        const int jj = e / n, k = e % n, pos = p0 + jj;
+        A[jj * stride + k] = pos < count ? B32[static_cast<int64_t>(row_at(pos)) * ldb + k] : 0.f;
+    }
+    if (tid < kDomTile) dom[tid] = p0 + tid < count ? 0 : 1;
+    const int jj = tid >> 3, q0 = (tid & 7) * 4;
+    for (int t0 = 0; t0 <= p0; t0 += kDomTile) {  // positions before the block's, and its own tile
+        __syncthreads();
+        if (tid == 0) {
+            int a = 1;
+            for (int i = 0; i < kDomTile; ++i) a &= dom[i];
+            all_dom = a;
+        }
+        for (int e = tid; e < kDomTile * n; e += 256) {
+            const int ii = e / n, k = e % n, pos = t0 + ii;
+            Bt[ii * stride + k] = pos < count ? B32[static_cast<int64_t>(row_at(pos)) * ldb + k] : 0.f;
+        }
+        __syncthreads();
+        if (all_dom) break;
+        const int pos = p0 + jj;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < n; ++k) {
+            const float a = A[jj * stride + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = fmaf(a, Bt[(q0 + q) * stride + k], d[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int pp = t0 + q0 + q;  // leads pos when it comes first in the order
+            if (pos < count && pp < pos && fabsf(d[q]) >= cos_min) dom[jj] = 1;
+        }
+    }
+    __syncthreads();
+    if (tid < kDomTile) {
+        const int pos = p0 + tid;
+        if (pos < count && dom[tid]) {
+            const int j = order[pos];
+            keep[j] = 0;
+            pruned[act_idx ? act_idx[j] : j] = 1;
+        }
+    }
+}
+
 // Training record of one component: raw features of every restart and whether the restart
 // ended at the picked direction (|b_r . b_p| >= 1 - 1e-3 on normalised rows).
 __global__ void record_kernel(const float* __restrict__ traj, const float* __restrict__ B32, int ldb, int n_dim, int M,
@@ -593,7 +705,8 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
                          const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, float cos_min) {
+                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, int row_n,
+                         float cos_min, int* order) {
     upsilon_ref_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, nullptr, ref);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -603,12 +716,28 @@ cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cos_min > 0.f && B32) {
-        const size_t smem = sizeof(float) * (2 * kDomTile * static_cast<size_t>(n + 1) + 2 * kDomTile) +
+        const size_t smem = sizeof(float) * (2 * kDomTile * static_cast<size_t>(row_n + 1) + 2 * kDomTile) +
                             sizeof(int) * kDomTile;
         e = allow_max_dyn_smem(dominated_kernel);
         if (e != cudaSuccess) return e;
-        dominated_kernel<<<(count_host + kDomTile - 1) / kDomTile, 256, smem, s>>>(
-            B32, ldb, n, traj, act_idx, count_dev, count_host, cos_min, keep, pruned);
+        if (count_host <= kDomSortMax && order) {
+            // count_host bounds the device count: the sorted form runs whenever it is in range
+            int P = 1;
+            while (P < count_host) P <<= 1;
+            e = allow_max_dyn_smem(lead_sort_kernel);
+            if (e != cudaSuccess) return e;
+            lead_sort_kernel<<<1, 1024, sizeof(unsigned long long) * P, s>>>(traj, act_idx, count_dev, count_host,
+                                                                              order);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            e = allow_max_dyn_smem(dominated_sorted_kernel);
+            if (e != cudaSuccess) return e;
+            dominated_sorted_kernel<<<(count_host + kDomTile - 1) / kDomTile, 256, smem, s>>>(
+                B32, ldb, row_n, order, act_idx, count_dev, count_host, cos_min, keep, pruned);
+        } else {
+            dominated_kernel<<<(count_host + kDomTile - 1) / kDomTile, 256, smem, s>>>(
+                B32, ldb, row_n, traj, act_idx, count_dev, count_host, cos_min, keep, pruned);
+        }
         e = cudaGetLastError();
     }
     if (e != cudaSuccess || (keep_min <= 0 && !(keep_frac > 0.f))) return e;

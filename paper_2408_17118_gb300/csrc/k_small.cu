@@ -95,7 +95,7 @@ __device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc,
                                              const int* __restrict__ act_idx, int j, float* __restrict__ B32,
                                              int ldb, float inv_T, float tol, int* __restrict__ flags,
                                              int* __restrict__ iters, float* __restrict__ traj, int t_iter,
-                                             int* status, int V, float* red) {
+                                             int* status, int V, float* red, RowProj proj) {
     const int w = threadIdx.x >> 5;
     const bool want_traj = traj && t_iter < kTrajLen;
     const int nq = (n_pad + 31) >> 5;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void finalize_row(const float* __restrict__ part_acc,
     float accv[8], e2, e4;
     row_combine(red, V, n_pad, n, want_traj, accv, &e2, &e4);
     finish_row_loaded(accv, b, nq, n, r, j, B32, ldb, inv_T, tol, flags, iters, traj, t_iter, want_traj, e2, e4,
-                      status);
+                      status, proj);
 }
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restrict__ part_acc,
@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
                                                            float* __restrict__ traj, int t_iter, int* status,
                                                            int* __restrict__ act_out, int* count_out,
                                                            long long* rows_accum, unsigned int* done_ctr,
-                                                           const int* __restrict__ shape_dev, int vw_ctas) {
+                                                           const int* __restrict__ shape_dev, int vw_ctas,
+                                                           RowProj proj) {
     extern __shared__ float fin_red[];  // [V][n_pad] sums, [V][n_pad] compensations, [V][4] moments
     pdl_wait();  // the update grid wrote the partials and the shape
     pdl_trigger();
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(NW * 32) finalize_kernel(const float* __restri
     // kernel's order for this active count, so that both give identical rows
     const int V = vw_ctas > 0 ? fin_vwarps(M_act, vw_ctas) : NW;
     finalize_row<NW>(part_acc, part_mom, splits, part_rows, n_pad, n, act_idx, j, B32, ldb, inv_T, tol, flags, iters,
-                     traj, t_iter, status, V, fin_red);
+                     traj, t_iter, status, V, fin_red, proj);
     compact_tail<NW>(flags, act_idx, M_act, act_out, count_out, rows_accum, done_ctr, M_act);
 }
 
@@ -153,8 +154,10 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
                             int part_rows, int n_pad, int n, const int* act_idx, const int* count_dev, int M_act,
                             float* B32, int ldb, double inv_T, double tol, int* flags, int* iters, float* traj,
                             int t_iter, int* status, int* act_out, int* count_out, long long* rows_accum,
-                            unsigned int* done_ctr, const int* shape_dev, bool pdl, int vw_ctas) {
+                            unsigned int* done_ctr, const int* shape_dev, bool pdl, int vw_ctas, const float* Wp,
+                            int nw, int ldw) {
     const float fT = static_cast<float>(inv_T), ftol = static_cast<float>(tol);
+    const RowProj proj{Wp, Wp ? nw : 0, ldw};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -170,13 +173,13 @@ cudaError_t launch_finalize(cudaStream_t s, const float* part_acc, const float* 
         cfg.dynamicSmemBytes = sizeof(float) * 32 * (2 * n_pad + 4);
         return cudaLaunchKernelEx(&cfg, finalize_kernel<32>, part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                                   count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj, t_iter, status, act_out,
-                                  count_out, rows_accum, done_ctr, shape_dev, 0);
+                                  count_out, rows_accum, done_ctr, shape_dev, 0, proj);
     }
     cfg.blockDim = dim3(128, 1, 1);
     cfg.dynamicSmemBytes = sizeof(float) * (vw_ctas > 0 ? kFinMaxVWarps : 4) * (2 * n_pad + 4);
     return cudaLaunchKernelEx(&cfg, finalize_kernel<4>, part_acc, part_mom, splits, part_rows, n_pad, n, act_idx,
                               count_dev, M_act, B32, ldb, fT, ftol, flags, iters, traj, t_iter, status, act_out,
-                              count_out, rows_accum, done_ctr, shape_dev, vw_ctas);
+                              count_out, rows_accum, done_ctr, shape_dev, vw_ctas, proj);
 }
 
 // Un-normalised update (step entry point): Bnew = acc / T - 3 B and moments / T.
@@ -527,6 +530,60 @@ cudaError_t launch_append(cudaStream_t s, const double* G, int n, int N, const f
                           const double* alpha, const double* ups, double* W, int i, double* kurt_out,
                           double* comp_stats) {
     append_kernel<<<1, 256, 0, s>>>(G, n, N, B32, ldb, p_slot, alpha, ups, W, i, kurt_out, comp_stats);
+    return cudaGetLastError();
+}
+
+// Algorithm 1 (FastICA with projection deflation, Section 2.2): initial restarts are random
+// vectors in the full whitened space, projected onto the complement of the components found so
+// far (w <- w - W^T (W w)) and normalised. One warp per row.
+__global__ void __launch_bounds__(256) project_rows_kernel(float* __restrict__ B32, int ldb, int M, int n,
+                                                           const float* __restrict__ W32, int nw, int ldw) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= M) return;
+    float* b = B32 + static_cast<int64_t>(row) * ldb;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        v[q] = k < n ? b[k] : 0.f;
+    }
+    for (int i = 0; i < nw; ++i) {
+        const float* wi = W32 + static_cast<int64_t>(i) * ldw;
+        float d = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (k < n) d = fmaf(wi[k], v[q], d);
+        }
+        d = warp_sumf(d);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (k < n) v[q] = fmaf(-d, wi[k], v[q]);
+        }
+    }
+    float ss = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ss = fmaf(v[q], v[q], ss);
+    ss = warp_sumf(ss);
+    const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k = lane + 32 * q;
+        if (k < n) b[k] = v[q] * inv;
+    }
+}
+cudaError_t launch_project_rows(cudaStream_t s, float* B32, int ldb, int M, int n, const float* W32, int nw, int ldw) {
+    project_rows_kernel<<<(M + 7) / 8, 256, 0, s>>>(B32, ldb, M, n, W32, nw, ldw);
+    return cudaGetLastError();
+}
+
+__global__ void w_to_f32_kernel(const double* __restrict__ W, int i, int N, float* __restrict__ W32, int ldw) {
+    for (int k = threadIdx.x; k < ldw; k += blockDim.x)
+        W32[static_cast<int64_t>(i) * ldw + k] = k < N ? static_cast<float>(W[static_cast<int64_t>(i) * N + k]) : 0.f;
+}
+cudaError_t launch_w_to_f32(cudaStream_t s, const double* W, int i, int N, float* W32, int ldw) {
+    w_to_f32_kernel<<<1, 256, 0, s>>>(W, i, N, W32, ldw);
     return cudaGetLastError();
 }
 

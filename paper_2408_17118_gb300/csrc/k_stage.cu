@@ -51,6 +51,8 @@ struct StageArgs {
     float inv_T, tol;
     uint64_t wait_ns;  // limit of every wait except the teardown drains
     unsigned int stall;  // test hook: arrivals the grid barriers expect beyond the CTAs (0)
+    RowProj proj;        // Algorithm 1: found components projected out of each update (none: nw = 0)
+    int lo_from;         // iterations t >= lo_from add the restart rows' low BF16 term to the first product
     int stages;
     uint32_t a_bytes, xsub_bytes, xstage_bytes, off_x, off_p, off_bar;
 };
@@ -75,7 +77,7 @@ __device__ __forceinline__ void group_finish_row(const StageArgs& a, const int* 
         float accv[8], e2, e4;
         row_combine(red, R, a.n_pad, a.n, want_traj, accv, &e2, &e4);
         finish_row_loaded(accv, b, nq, a.n, r, j, a.B32, a.ldb, a.inv_T, a.tol, a.flags, a.iters, a.traj, t,
-                          want_traj, e2, e4, a.status);
+                          want_traj, e2, e4, a.status, a.proj);
     }
     named_bar_sync(bar_id, 32 * R);  // the scratch is reused by the group's next row
 }
@@ -160,11 +162,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         const int nch = active ? min(a.total_chunks, c_begin + cps) - c_begin : 0;
         const int part_rows = tiles * kTcRows;
         const bool mom = t < kTrajLen;
+        const bool use_lo = t >= a.lo_from;
 
         if (active && warp >= 2 && warp < 2 + kEpiWarps) {
             // restart tile -> BF16 hi (shared memory) and lo (beside it, or in tensor memory)
             convert_restart_tile<tc_split_b(TC), tc_lo_in_tmem(TC)>(a.B32, a.ldb, act, m0, M_act, a.n_pad, sA,
-                                                                    a.a_bytes, tmem + kALoCol, true);
+                                                                    a.a_bytes, tmem + kALoCol, true, use_lo);
             tc_fence_before();
         }
         // The restart tile is complete for the first-product issuer (warp 1) once the epilogue
@@ -214,7 +217,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
                             umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                         }
-                        if constexpr (tc_lo_in_tmem(TC)) {
+                        if (!use_lo) {
+                        } else if constexpr (tc_lo_in_tmem(TC)) {
 #pragma unroll
                             for (int ks = 0; ks < 16; ++ks) {
                                 if (ks >= ksteps1) break;
@@ -498,6 +502,8 @@ static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, co
     a.tol = static_cast<float>(p.tol);
     a.wait_ns = p.wait_ns ? p.wait_ns : ICA_WAIT_NS;
     a.stall = p.stall ? 1u : 0u;
+    a.proj = RowProj{p.Wp, p.Wp ? p.nw : 0, p.ldw};
+    a.lo_from = p.lo_from;
     a.stages = static_cast<int>(L.stages);
     a.a_bytes = L.a_bytes;
     a.xsub_bytes = L.xsub_bytes;

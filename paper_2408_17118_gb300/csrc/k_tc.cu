@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int total_chunks, int stages, uint32_t a_bytes, uint32_t xsub_bytes, uint32_t xstage_bytes,
                     uint32_t off_x,
                     uint32_t off_p, uint32_t off_bar, float* __restrict__ part_acc, float* __restrict__ part_mom,
-                    int part_rows, int* status, int shape_ctas, int* shape_out) {
+                    int part_rows, int* status, int shape_ctas, int* shape_out, int use_lo) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_u32 = smem_u32(smem_raw);
     const uint32_t base_u32 = (raw_u32 + 1023u) & ~1023u;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     constexpr bool kSplit = tc_split_b(TC), kLoTmem = tc_lo_in_tmem(TC);
     if (!kLoTmem && warp >= 2 && warp < 2 + kEpiWarps)  // restart tile -> BF16 hi (+ lo) in shared memory
-        convert_restart_tile<kSplit, false>(B32, ldb, act_idx, m0, M_act, n_pad, sA, a_bytes, 0u, false);
+        convert_restart_tile<kSplit, false>(B32, ldb, act_idx, m0, M_act, n_pad, sA, a_bytes, 0u, false, use_lo != 0);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // convert the tile, then meet the first-product issuer (warp 1) at a named barrier
         if (warp >= 2 && warp < 2 + kEpiWarps) {
             convert_restart_tile<kSplit, true>(B32, ldb, act_idx, m0, M_act, n_pad, sA, a_bytes, tmem + kALoCol,
-                                               false);
+                                               false, use_lo != 0);
             tc_fence_before();
         }
         if (warp >= 1 && warp < 2 + kEpiWarps) named_bar_sync(10, 32 * (1 + kEpiWarps));
@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
                     umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                 }
-                if constexpr (kLoTmem) {
+                if (!use_lo) {
+                } else if constexpr (kLoTmem) {
 #pragma unroll
                     for (int ks = 0; ks < 16; ++ks) {
                         if (ks >= ksteps1) break;
@@ -387,7 +388,7 @@ static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const
                                   const int* act_idx, const int* count_dev, int M_act, int n_pad, int64_t T,
                                   int splits, int chunks_per_split, int total_chunks, float* part_acc,
                                   float* part_mom, int part_rows, int* status, int shape_ctas = 0,
-                                  int* shape_out = nullptr) {
+                                  int* shape_out = nullptr, bool use_lo = true) {
     const TcLayout L = tc_layout(n_pad, MO, TC, NB);
     if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
     cudaError_t e = allow_max_dyn_smem(fused_tc_kernel<TC, NB, MO, MOM>);
@@ -409,19 +410,20 @@ static cudaError_t launch_tc_impl(cudaStream_t s, const CUtensorMap& xmap, const
     return cudaLaunchKernelEx(&cfg, fused_tc_kernel<TC, NB, MO, MOM>, xmap, B32, ldb, act_idx, count_dev, M_act,
                               n_pad, T, chunks_per_split, total_chunks, static_cast<int>(L.stages), L.a_bytes,
                               L.xsub_bytes, L.xstage_bytes, L.off_x, L.off_p, L.off_bar, part_acc, part_mom,
-                              part_rows, status, shape_ctas, shape_out);
+                              part_rows, status, shape_ctas, shape_out, use_lo ? 1 : 0);
 }
 
 cudaError_t launch_fused_tc_shaped(cudaStream_t s, bool moments, const CUtensorMap& xmap, const float* B32, int ldb,
                                    const int* act_idx, const int* count_dev, int M_ub, int n_pad, int64_t T, int ctas,
-                                   int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out) {
+                                   int total_chunks, float* part_acc, float* part_mom, int* status, int* shape_out,
+                                   bool use_lo) {
 #define ICA_TC_SHAPED(TCV, NBV)                                                                                   \
     return moments ? launch_tc_impl<TCV, NBV, false, true>(s, xmap, B32, ldb, act_idx, count_dev, M_ub, n_pad, T, \
                                                            0, 0, total_chunks, part_acc, part_mom, 0, status,     \
-                                                           ctas, shape_out)                                       \
+                                                           ctas, shape_out, use_lo)                               \
                    : launch_tc_impl<TCV, NBV, false, false>(s, xmap, B32, ldb, act_idx, count_dev, M_ub, n_pad, T, \
                                                             0, 0, total_chunks, part_acc, part_mom, 0, status,    \
-                                                            ctas, shape_out)
+                                                            ctas, shape_out, use_lo)
     if (n_pad <= 64) ICA_TC_SHAPED(ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB);
     if (n_pad <= 128) ICA_TC_SHAPED(128, 2);
     ICA_TC_SHAPED(64, 2);

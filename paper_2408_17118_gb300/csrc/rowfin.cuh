@@ -29,25 +29,47 @@ __device__ __forceinline__ void load_row(const float* __restrict__ B32, int ldb,
     }
 }
 
+// Projection of Algorithm 1 (FastICA with deflation on the full whitened data): the found
+// components W (nw rows of ld floats, FP32 copy) are projected out of each update,
+// w <- w - W^T (W w). nw = 0 for Algorithm 2, whose reduced rows need no projection.
+struct RowProj {
+    const float* W;
+    int nw, ld;
+};
+
 // One warp finishes active row j (restart r, current entries b) from the summed update u*T
-// (acc): b' = acc / T - 3 b, normalisation, distance, flag, iteration count and trajectory.
+// (acc): b' = acc / T - 3 b (Algorithm 1: then projected, RowProj), normalisation, distance,
+// flag, iteration count and trajectory.
 __device__ __forceinline__ void finish_row_loaded(const float (&accv)[8], const float (&b)[8], int nq, int n, int r,
                                                   int j, float* __restrict__ B32, int ldb, float inv_T, float tol,
                                                   int* __restrict__ flags, int* __restrict__ iters,
                                                   float* __restrict__ traj, int t_iter, bool want_traj, float e2sum,
-                                                  float e4sum, int* status) {
+                                                  float e4sum, int* status, RowProj proj = RowProj{nullptr, 0, 0}) {
     const int lane = threadIdx.x & 31;
     float u[8];
-    float ss = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int k = lane + 32 * q;
-        u[q] = 0.f;
-        if (q < nq && k < n) {
-            u[q] = accv[q] * inv_T - 3.f * b[q];
-            ss = fmaf(u[q], u[q], ss);
+        u[q] = (q < nq && k < n) ? accv[q] * inv_T - 3.f * b[q] : 0.f;
+    }
+    for (int i = 0; i < proj.nw; ++i) {  // u -= w_i (w_i . u), w_i in turn (modified Gram-Schmidt)
+        const float* wi = proj.W + static_cast<int64_t>(i) * proj.ld;
+        float d = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (q < nq && k < n) d = fmaf(__ldcg(wi + k), u[q], d);
+        }
+        d = warp_sumf(d);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = lane + 32 * q;
+            if (q < nq && k < n) u[q] = fmaf(-d, __ldcg(wi + k), u[q]);
         }
     }
+    float ss = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ss = fmaf(u[q], u[q], ss);
     ss = warp_sumf(ss);
     const bool bad = !(ss > 0.f) || !isfinite(ss);
     float dm = 0.f, dp = 0.f;

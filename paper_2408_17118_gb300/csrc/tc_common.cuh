@@ -109,10 +109,11 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
 // lo_tmem + 8 ks; each warp writes its own lane quarter, as tcgen05.st requires). Rows at or
 // beyond M_act are zero. Row m of the tile is restart act[m0 + m] (or m0 + m when act is null).
 // ldcg: read B through L2 (rows written by other CTAs of a persistent launch).
+// with_lo = false: the low term is not written (iterations that use the high term alone).
 template <bool SPLIT, bool LO_TMEM>
 __device__ __forceinline__ void convert_restart_tile(const float* __restrict__ B32, int ldb, const int* act, int m0,
                                                      int M_act, int n_pad, uint32_t sA, uint32_t a_bytes,
-                                                     uint32_t lo_tmem, bool ldcg) {
+                                                     uint32_t lo_tmem, bool ldcg, bool with_lo = true) {
     auto lo_of = [](uint32_t hp, float x, float y) {
         return pack_bf16x2(x - __uint_as_float(hp << 16), y - __uint_as_float(hp & 0xFFFF0000u));
     };
@@ -151,7 +152,7 @@ __device__ __forceinline__ void convert_restart_tile(const float* __restrict__ B
                              "r"(hp[4 * half + 1]), "r"(hp[4 * half + 2]), "r"(hp[4 * half + 3])
                              : "memory");
             }
-            tmem_st8(lo_tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(ks * 8), lp);
+            if (with_lo) tmem_st8(lo_tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(ks * 8), lp);
         }
         tmem_st_wait();
     } else {
@@ -172,7 +173,7 @@ __device__ __forceinline__ void convert_restart_tile(const float* __restrict__ B
                            h3 = pack_bf16x2(v1.z, v1.w);
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(h0), "r"(h1), "r"(h2), "r"(h3)
                          : "memory");
-            if constexpr (SPLIT) {  // residuals b - float(bf16(b)) in the second half
+            if (SPLIT && with_lo) {  // residuals b - float(bf16(b)) in the second half
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + (a_bytes >> 1)),
                              "r"(lo_of(h0, v0.x, v0.y)), "r"(lo_of(h1, v0.z, v0.w)), "r"(lo_of(h2, v1.x, v1.y)),
                              "r"(lo_of(h3, v1.z, v1.w))

@@ -268,6 +268,26 @@ def ica_fp_step_noalloc(precision: int, B: torch.Tensor, n: int, Xt: torch.Tenso
     return Bnew, mom
 
 
+def fluctuation(Ws) -> "np.ndarray":
+    """Run-to-run fluctuation of the components of several fits (Section 4.3, an analysis of the
+    outputs, no device work): for component i, the mean over ordered pairs of runs (t != u) of
+    1 - |cos(w_i^t, w_i^u)|. Ws: list of (n x N) arrays or tensors; the shortest fit bounds i."""
+    import numpy as np
+
+    Ws = [np.asarray(w.cpu() if hasattr(w, "cpu") else w, dtype=np.float64) for w in Ws]
+    R = len(Ws)
+    if R < 2:
+        raise ValueError("fluctuation needs at least two runs")
+    n = min(w.shape[0] for w in Ws)
+    unit = [w[:n] / np.linalg.norm(w[:n], axis=1, keepdims=True) for w in Ws]
+    acc = np.zeros(n)
+    for t in range(R):
+        for u in range(R):
+            if t != u:
+                acc += 1.0 - np.abs(np.sum(unit[t] * unit[u], axis=1))
+    return acc / (R * (R - 1))
+
+
 # ------------------------------------------------------------------ learned restart pruner
 def ica_mlp_init(ctx: Context, seed: int, params: torch.Tensor | None = None) -> torch.Tensor:
     params = torch.empty(ICA_MLP_PARAMS, dtype=torch.float32, device=f"cuda:{ctx.device}") if params is None else params

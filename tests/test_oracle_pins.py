@@ -404,3 +404,24 @@ def test_certify_two_dimensional_brute_force():
     bad = oracle.certify_picks(Xw, Wbad, C, K=500, eps=1e-13, components=[0])[0]
     # refined, the bad pick either moves away (not a fixed point) or lands on a worse optimum
     assert bad.pick_cos < 1 - 1e-5 or bad.margin < -1e-6
+
+
+def test_algorithm1_full_init_reaches_the_same_components(small_oracle):
+    """Algorithm 1 from N-dimensional random initial vectors (projected by FastICA itself) finds
+    the same ordered components as Algorithm 2 on the N=8 mixture (each non-Gaussian optimum is
+    reached by many of the 64 restarts either way)."""
+    w, B0, res, Xw, V, mean = small_oracle
+    r1 = oracle.ordering_ica_original(Xw, w.M, 60, 1e-10, B0, full_init=True)
+    cos = np.abs(np.sum(r1.W * res.W, axis=1))
+    assert np.all(cos[:7] >= 1 - 1e-8), cos
+    assert np.allclose(r1.alpha[:7], res.alpha[:7], rtol=1e-8)
+
+
+def test_package_fluctuation_matches_the_oracle():
+    from paper_2408_17118_gb300 import ica
+
+    rng = np.random.default_rng(4)
+    Ws = [rng.standard_normal((6, 9)) for _ in range(4)]
+    assert np.allclose(ica.fluctuation(Ws), oracle.fluctuation(Ws), atol=1e-15)
+    a = np.eye(3)
+    assert np.allclose(ica.fluctuation([a, -a, 2 * a]), 0.0)
