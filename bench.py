@@ -456,6 +456,8 @@ def run_ours(args):
 
     head = summary(stats, step_ms)
     log(f"headline {head}")
+    if K <= 8:  # per-component iterations of the last timed step (profile captures need them)
+        log("components " + str([(c["i"], c["iterations"], c["rows_updated"]) for c in stats[-1]["components"]]))
     # the same fits without the pruner (the pruner's fallback and judge)
     unpruned, judge = None, None
     if prune:
@@ -542,13 +544,16 @@ def run_ours(args):
     it = kinds.get("iteration", {"launches": 0, "ms": 0.0, "flops": 0.0})
     achieved = it["flops"] / (it["ms"] / 1e3) / 1e12 if it["ms"] > 0 else 0.0
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    xt_bytes = sum((N - c["i"] + 1 + 15) // 16 * 16 * T * 2.0 for c in stats[-1]["components"])
+    # X~ bytes the stage reads per launch: one pass per iteration (X~ larger than L2 at N = 256)
+    xt_iter_bytes = sum(c["iterations"] * ((N - c["i"] + 1 + 15) // 16 * 16) * T * 2.0
+                        for c in stats[-1]["components"])
     ratio = STAGE_TRAFFIC_RATIO.get(args.config)
-    traffic = ratio * xt_bytes / len(stats[-1]["components"]) if ratio else None
+    traffic = ratio * xt_iter_bytes / max(1, it["launches"] / max(1, args.steps)) if ratio else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": ("ncu dram read+write of a stage launch / its X~ bytes, times the fit's mean X~ bytes "
-                                 "per launch" if ratio else "no ncu capture of the current stage kernel at this workload"),
+                "traffic_note": ("ncu dram read+write of a captured stage launch / (its iterations x n_pad T 2 B), "
+                                 "times the fit's iterations x X~ bytes per launch" if ratio else
+                                 "no ncu capture of the current stage kernel at this workload"),
                 "kernel": "stage_tc_kernel (persistent BF16 stage: tcgen05 update, row completion, removal of "
                           "converged rows)",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",

@@ -119,6 +119,10 @@ typedef struct {
                               Upsilon at iteration 5 points the same way, |b . b'| >= prune_cos
                               (it is heading to the same optimum); default 0.99, 0 disables.
                               The keep floor (prune_keep_frac) overrides it. */
+    int prune_gauss;       /* pruner: 1 (default) - when no running restart's Upsilon at iteration 5
+                              reaches the Gaussianity threshold of Eq. 3 for the component, the
+                              component is in the Gaussian subspace (no unique direction,
+                              Theorem 1) and only the keep floor stays; 0: the network decides */
     int algorithm;         /* 2 (default): Algorithm 2, each component on the reduced data X~ = G Xw
                               (Section 3.3, n = N - i + 1 dimensions). 1: Algorithm 1's form (the
                               "threads" ordering ICA, run here as one batch): every iteration on
@@ -142,7 +146,8 @@ typedef struct {
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
    no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05, prune_cos 0.99), no
-   recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 3. */
+   recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 3,
+   prune_gauss 1. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */

@@ -43,6 +43,7 @@ class ica_opts(C.Structure):
         ("stall_test", C.c_int),
         ("prune_keep_frac", C.c_float),
         ("prune_cos", C.c_float),
+        ("prune_gauss", C.c_int),
         ("algorithm", C.c_int),
         ("stage_lo_from", C.c_int),
         ("record_cands", C.c_void_p),

@@ -445,6 +445,7 @@ void ica_default_opts(ica_opts* o) {
     o->prune_cos = 0.99f;
     o->algorithm = 2;
     o->stage_lo_from = 3;
+    o->prune_gauss = 1;
 }
 
 const char* ica_status_string(int st) {
@@ -916,8 +917,12 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     // learned pruner on the first kTrajLen iterations' trajectories
                     int before = M_host;
                     rc = timed(K_PRUNE, 0.0, [&] {
+                        // Eq. 3 for component i + 1: Upsilon below 2 (N - i + 1)(N - i) / T
+                        const float gthr = o.prune_gauss
+                                               ? static_cast<float>(2.0 * (N - i + 1) * (N - i) / static_cast<double>(T))
+                                               : 0.f;
                         KL(launch_prune(s, o.prune_params, traj, act[cur], counts + cur, M_host, N - i,
-                                        std::log(static_cast<double>(T)), o.prune_tau, uref, flags, pruned,
+                                        std::log(static_cast<double>(T)), o.prune_tau, gthr, uref, flags, pruned,
                                         o.prune_keep_frac > 0.f ? (bf16 ? o.refine_topk : 1) : 0,
                                         o.prune_keep_frac, B32, n_pad, n, o.prune_cos, excl));
                         KL(launch_compact_keep(s, flags, act[cur], counts + cur, M_host, act[cur ^ 1], counts + (cur ^ 1)));

@@ -134,10 +134,12 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 // restarts dominated by a similar (|cos| >= cos_min; 0 disables) restart leading them in
 // Upsilon, plus the keep floor: the max(keep_min, ceil(keep_frac * count)) restarts with the
 // largest Upsilon at iteration kTrajLen (and any tied with the last of them).
+// gauss_thr > 0: when no running restart's Upsilon reaches it (the Gaussianity threshold of
+// Eq. 3), the network keeps nothing and only the keep floor stays.
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
-                         const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, int row_n,
-                         float cos_min, int* order);  // order: scratch of count ints (sorted test)
+                         const int* count_dev, int count_host, int n, double logT, float tau, float gauss_thr,
+                         float* ref, int* keep, int* pruned, int keep_min, float keep_frac, const float* B32, int ldb,
+                         int row_n, float cos_min, int* order);  // order: scratch of count ints (sorted test)
 cudaError_t launch_record(cudaStream_t s, const float* traj, const int* iters, const float* B32, int ldb, int n, int M,
                           const int* slot, double logT, float* ref, float* F_out, float* y_out);
 // 1 in *out when some pruned restart's Upsilon at iteration kTrajLen (its objective when it was

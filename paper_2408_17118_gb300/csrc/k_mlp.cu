@@ -308,7 +308,7 @@ __global__ void upsilon_ref_kernel(const float* __restrict__ traj, const int* __
 __global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ params, const float* __restrict__ traj,
                                                     const int* __restrict__ act_idx, const int* __restrict__ count_dev,
                                                     int count_host, float n, float logT,
-                                                    const float* __restrict__ ref, float tau,
+                                                    const float* __restrict__ ref, float tau, float gauss_thr,
                                                     int* __restrict__ keep, int* __restrict__ pruned) {
     __shared__ SmemNet s;
     load_net<true>(params, s);
@@ -319,7 +319,10 @@ __global__ void __launch_bounds__(128) prune_kernel(const float* __restrict__ pa
     float x[IN];
     restart_features(traj, r, n, logT, *ref, x);
     const float p = sigmoidf(forward_one<true>(s, x, nullptr, nullptr));
-    const int k = p >= tau ? 1 : 0;
+    // Gaussian regime: no running restart reaches the Gaussianity threshold (Eq. 3), so no
+    // direction of this component is unique; the network keeps nothing (the keep floor decides)
+    const bool gaussian = *ref < gauss_thr;
+    const int k = (p >= tau && !gaussian) ? 1 : 0;
     keep[j] = k;
     if (!k) pruned[r] = 1;
 }
@@ -536,60 +539,68 @@ __global__ void __launch_bounds__(1024) lead_sort_kernel(const float* __restrict
         }
     for (int i = threadIdx.x; i < count; i += blockDim.x) order[i] = static_cast<int>(keys[i] & 0xffffffffu);
 }
+constexpr int kDomSortTile = 64, kDomStride = kDomSortTile + 4;  // k-major tiles, 16-byte aligned rows
 __global__ void __launch_bounds__(256) dominated_sorted_kernel(const float* __restrict__ B32, int ldb, int n,
                                                                const int* __restrict__ order,
                                                                const int* __restrict__ act_idx,
                                                                const int* __restrict__ count_dev, int count_host,
                                                                float cos_min, int* __restrict__ keep,
                                                                int* __restrict__ pruned) {
-    extern __shared__ float dsm[];
+    extern __shared__ __align__(16) float dsm[];
     const int count = count_dev ? *count_dev : count_host;
-    const int p0 = blockIdx.x * kDomTile;
+    const int p0 = blockIdx.x * kDomSortTile;
     if (p0 >= count || count > kDomSortMax) return;
-    const int stride = n + 1;
-    float* A = dsm;
-    float* Bt = dsm + kDomTile * stride;
-    int* dom = reinterpret_cast<int*>(Bt + kDomTile * stride);
+    float* At = dsm;                         // [n][kDomStride]: the block's 64 rows, k-major
+    float* Bt = dsm + n * kDomStride;        // [n][kDomStride]: the scanned 64 rows
+    __shared__ int dom[kDomSortTile];
     __shared__ int all_dom;
     const int tid = threadIdx.x;
     auto row_at = [&](int pos) {
         const int j = order[pos];
         return act_idx ? act_idx[j] : j;
     };
-    for (int e = tid; e < kDomTile * n; e += 256) {
-        const int jj = e / n, k = e % n, pos = p0 + jj;
-        A[jj * stride + k] = pos < count ? B32[static_cast<int64_t>(row_at(pos)) * ldb + k] : 0.f;
+    for (int e = tid; e < kDomSortTile * n; e += 256) {
+        const int rr = e / n, k = e % n, pos = p0 + rr;
+        At[k * kDomStride + rr] = pos < count ? B32[static_cast<int64_t>(row_at(pos)) * ldb + k] : 0.f;
     }
-    if (tid < kDomTile) dom[tid] = p0 + tid < count ? 0 : 1;
-    const int jj = tid >> 3, q0 = (tid & 7) * 4;
-    for (int t0 = 0; t0 <= p0; t0 += kDomTile) {  // positions before the block's, and its own tile
+    if (tid < kDomSortTile) dom[tid] = p0 + tid < count ? 0 : 1;
+    // thread: rows 4 ty .. 4 ty + 3 of the block against scanned rows 4 tx .. 4 tx + 3
+    const int ty = tid >> 4, tx = tid & 15;
+    for (int t0 = 0; t0 <= p0; t0 += kDomSortTile) {  // positions before the block's, and its own tile
         __syncthreads();
         if (tid == 0) {
             int a = 1;
-            for (int i = 0; i < kDomTile; ++i) a &= dom[i];
+            for (int i = 0; i < kDomSortTile; ++i) a &= dom[i];
             all_dom = a;
         }
-        for (int e = tid; e < kDomTile * n; e += 256) {
-            const int ii = e / n, k = e % n, pos = t0 + ii;
-            Bt[ii * stride + k] = pos < count ? B32[static_cast<int64_t>(row_at(pos)) * ldb + k] : 0.f;
+        for (int e = tid; e < kDomSortTile * n; e += 256) {
+            const int rr = e / n, k = e % n, pos = t0 + rr;
+            Bt[k * kDomStride + rr] = pos < count ? B32[static_cast<int64_t>(row_at(pos)) * ldb + k] : 0.f;
         }
         __syncthreads();
         if (all_dom) break;
-        const int pos = p0 + jj;
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        float acc[4][4] = {};
         for (int k = 0; k < n; ++k) {
-            const float a = A[jj * stride + k];
+            const float4 av = *reinterpret_cast<const float4*>(At + k * kDomStride + 4 * ty);
+            const float4 bv = *reinterpret_cast<const float4*>(Bt + k * kDomStride + 4 * tx);
+            const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d[q] = fmaf(a, Bt[(q0 + q) * stride + k], d[q]);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int pp = t0 + q0 + q;  // leads pos when it comes first in the order
-            if (pos < count && pp < pos && fabsf(d[q]) >= cos_min) dom[jj] = 1;
+        for (int i = 0; i < 4; ++i) {
+            const int pos = p0 + 4 * ty + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int pp = t0 + 4 * tx + j;  // leads pos when it comes first in the order
+                if (pos < count && pp < pos && fabsf(acc[i][j]) >= cos_min) dom[4 * ty + i] = 1;
+            }
         }
     }
     __syncthreads();
-    if (tid < kDomTile) {
+    if (tid < kDomSortTile) {
         const int pos = p0 + tid;
         if (pos < count && dom[tid]) {
             const int j = order[pos];
@@ -704,15 +715,15 @@ cudaError_t launch_mlp_train_step(cudaStream_t s, float* params, float* m, float
 }
 
 cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj, const int* act_idx,
-                         const int* count_dev, int count_host, int n, double logT, float tau, float* ref, int* keep,
-                         int* pruned, int keep_min, float keep_frac, const float* B32, int ldb, int row_n,
-                         float cos_min, int* order) {
+                         const int* count_dev, int count_host, int n, double logT, float tau, float gauss_thr,
+                         float* ref, int* keep, int* pruned, int keep_min, float keep_frac, const float* B32, int ldb,
+                         int row_n, float cos_min, int* order) {
     upsilon_ref_kernel<<<1, 256, 0, s>>>(traj, act_idx, count_dev, count_host, nullptr, ref);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prune_kernel<<<(count_host + 127) / 128, 128, 0, s>>>(params, traj, act_idx, count_dev, count_host,
                                                           static_cast<float>(n), static_cast<float>(logT), ref, tau,
-                                                          keep, pruned);
+                                                          gauss_thr, keep, pruned);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cos_min > 0.f && B32) {
@@ -732,7 +743,8 @@ cudaError_t launch_prune(cudaStream_t s, const float* params, const float* traj,
             if (e != cudaSuccess) return e;
             e = allow_max_dyn_smem(dominated_sorted_kernel);
             if (e != cudaSuccess) return e;
-            dominated_sorted_kernel<<<(count_host + kDomTile - 1) / kDomTile, 256, smem, s>>>(
+            const size_t smem_sorted = sizeof(float) * 2 * static_cast<size_t>(row_n) * kDomStride;
+            dominated_sorted_kernel<<<(count_host + kDomSortTile - 1) / kDomSortTile, 256, smem_sorted, s>>>(
                 B32, ldb, row_n, order, act_idx, count_dev, count_host, cos_min, keep, pruned);
         } else {
             dominated_kernel<<<(count_host + kDomTile - 1) / kDomTile, 256, smem, s>>>(
