@@ -60,8 +60,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["small", "eeg64", "eeg128", "eeg256", "eeg128_small", "eeg256_small", "batch"],
                     default="eeg256",
-                    help="workload (eeg128_small / eeg256_small: N = 128 / 256, T = 400,000, M = 2048, for ncu "
-                         "captures that must stay a few GB)")
+                    help="workload (eeg128_small / eeg256_small: N = 128 / 256, T = 400,000, M = 4096 / 8192, for "
+                         "ncu captures that must stay a few GB)")
     ap.add_argument("--components", type=int, default=0, metavar="K",
                     help="fit only the first K components (ncu captures of the widest stage launches)")
     ap.add_argument("--workers", type=int, default=8, help="concurrent fits of --config batch")
@@ -97,8 +97,9 @@ def parse_args():
 def workload(name: str, seed: int):
     import synth
 
-    if name.endswith("_small"):
-        return synth.eeg_like(int(name[3:6]), 400_000, 2048, seed=seed)
+    if name.endswith("_small"):  # the N = 256 / 128 cases at T = 400,000 (restarts as at full size)
+        N = int(name[3:6])
+        return synth.eeg_like(N, 400_000, 8192 if N == 256 else 4096, seed=seed)
     return {"small": synth.small_mixture, "eeg64": synth.eeg64, "eeg128": synth.eeg128, "eeg256": synth.eeg256}[name](seed)
 
 

@@ -16,7 +16,8 @@
  *     that stream a few times per component: once after each persistent BF16 stage and FP32
  *     refinement launch (opts.stage_persistent), otherwise on a sparse schedule of iterations
  *     (it reads the active-restart count every fourth iteration on the BF16 path; every
- *     iteration at first, then every second and every fourth on the FP32 path); ica_whiten,
+ *     iteration at first, then every second and every fourth on the FP32 path; with the
+ *     restart pruner also when it runs and before the kurtosis pass); ica_whiten,
  *     ica_deflation_basis, ica_fp_step and ica_kurtosis synchronise once at the end to read
  *     the device status word; ica_init_restarts and ica_reduce only enqueue.
  *   - The return value is an ica_status. Nothing is thrown across the ABI. After an error the
@@ -135,6 +136,11 @@ typedef struct {
                               rows to the first product as two BF16 terms (hi + lo, about 16
                               bits: rows can converge to stage_tol); earlier ones as one BF16
                               term, which is enough far from convergence (default 3) */
+    int stage_streamk;     /* persistent BF16 stage: 1 (default) - when the one-wave shape (restart
+                              tiles x sample splits) would leave more than a sixteenth of the SMs
+                              idle, every CTA takes an equal share of the (tile x chunk) work
+                              instead (results then differ from the per-launch path by FP32
+                              summation order); 0: always the one-wave shape */
     double* record_cands;  /* optional (device, BF16 path): n_components x refine_topk x N FP64.
                               Row (i, j) = w = G^T b of the j-th distinct candidate of component i
                               after the FP32 refinement (Section 3.3: the candidate in the full
@@ -147,7 +153,7 @@ typedef struct {
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
    no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05, prune_cos 0.99), no
    recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 3,
-   prune_gauss 1. */
+   prune_gauss 1, stage_streamk 1. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */

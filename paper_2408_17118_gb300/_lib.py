@@ -46,6 +46,7 @@ class ica_opts(C.Structure):
         ("prune_gauss", C.c_int),
         ("algorithm", C.c_int),
         ("stage_lo_from", C.c_int),
+        ("stage_streamk", C.c_int),
         ("record_cands", C.c_void_p),
     ]
 

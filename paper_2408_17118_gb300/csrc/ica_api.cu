@@ -446,6 +446,7 @@ void ica_default_opts(ica_opts* o) {
     o->algorithm = 2;
     o->stage_lo_from = 3;
     o->prune_gauss = 1;
+    o->stage_streamk = 1;
 }
 
 const char* ica_status_string(int st) {
@@ -841,6 +842,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     sl.nw = i;
                     sl.ldw = n_pad;
                     sl.lo_from = o.stage_lo_from;
+                    sl.streamk = o.stage_streamk;
                     CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
                     cudaError_t le = cudaSuccess;
                     int resident = 0;
@@ -1199,6 +1201,14 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     json_kv(js, "launches", static_cast<double>(c->launches));
     json_kv(js, "launches_total", static_cast<double>(c->launches_total));
     json_kv(js, "stage_persistent_launches", static_cast<double>(persist_launches));
+    {   // the persistent stage's first iteration (all M restarts) in equal work shares
+        int tl = 0, sp0 = 0, cps0 = 0;
+        const int tc0 = tc_chunk(round_up(N, 16));
+        const int tot0 = static_cast<int>((T + tc0 - 1) / tc0);
+        tc_device_shape(M, 152, tot0, &tl, &sp0, &cps0);
+        const bool sk0 = o.stage_streamk && tl * sp0 < (152 * 15) / 16 && static_cast<int64_t>(tl) * tot0 >= 152;
+        json_kv(js, "stage_streamk_first_iteration", (persist_launches > 0 && sk0) ? 1.0 : 0.0);
+    }
     js += "\"stage_persistent_note\": \"" + c->persist_note + "\", ";
     js += "\"fused\": {";
     for (int k = 0; k < 4; ++k) {

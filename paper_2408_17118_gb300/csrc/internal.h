@@ -210,6 +210,7 @@ struct StageLaunch {
     const float* Wp;   // Algorithm 1: found components (nw rows, ld ldw, FP32) projected out of each update
     int nw, ldw;
     int lo_from;       // iterations t >= lo_from add the restart rows' low BF16 term (0: every iteration)
+    int streamk;       // 1: equal shares of the (tile x chunk) work when the one-wave shape leaves SMs idle
 };
 // resident (optional) receives the number of CTAs of the kernel that fit the GPU at once.
 cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident = nullptr);

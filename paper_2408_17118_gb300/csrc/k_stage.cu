@@ -53,6 +53,7 @@ struct StageArgs {
     unsigned int stall;  // test hook: arrivals the grid barriers expect beyond the CTAs (0)
     RowProj proj;        // Algorithm 1: found components projected out of each update (none: nw = 0)
     int lo_from;         // iterations t >= lo_from add the restart rows' low BF16 term to the first product
+    int streamk;         // 1: equal shares of the (tile x chunk) work when the one-wave shape leaves SMs idle
     int stages;
     uint32_t a_bytes, xsub_bytes, xstage_bytes, off_x, off_p, off_bar;
 };
@@ -61,8 +62,11 @@ struct StageArgs {
 // the split partials summed in the virtual-warp order of row_partials with V = R, the row
 // completed by the group's first warp (which loads the restart row while the sums run).
 // red: the group's scratch, [R][n_pad] sums, [R][n_pad] compensations, [R][4].
+// Wsk > 0: the update ran in equal shares of Wsk = tiles x chunks work (see the update): row j's
+// partials come from the CTAs whose shares meet its tile, in CTA order, each at row j mod 128 of
+// its slot for that tile (2 k, or 2 k + 1 when its share began in the tile before).
 __device__ __forceinline__ void group_finish_row(const StageArgs& a, const int* act, int j, int splits, int part_rows,
-                                                 int t, float* red, int R, int gw, int bar_id) {
+                                                 int64_t Wsk, int t, float* red, int R, int gw, int bar_id) {
     const bool want_traj = a.traj && t < kTrajLen;
     const int nq = (a.n_pad + 31) >> 5;
     int r = 0;
@@ -71,7 +75,27 @@ __device__ __forceinline__ void group_finish_row(const StageArgs& a, const int* 
         r = __ldcg(act + j);
         load_row(a.B32, a.ldb, r, nq, a.n, b);
     }
-    row_partials(a.part_acc, a.part_mom, splits, part_rows, a.n_pad, j, want_traj, R, R, gw, red);
+    if (Wsk > 0) {
+        const int G = static_cast<int>(gridDim.x);
+        const int64_t tot = a.total_chunks;
+        const int tile = j / kTcRows, rr = j % kTcRows;
+        auto w0 = [&](int k) { return static_cast<int64_t>(k) * Wsk / G; };
+        const int64_t first = static_cast<int64_t>(tile) * tot, last = first + tot - 1;
+        int kf = static_cast<int>(first * G / Wsk), kl = static_cast<int>(last * G / Wsk);
+        while (kf + 1 < G && w0(kf + 1) <= first) ++kf;
+        while (kf > 0 && w0(kf) > first) --kf;
+        while (kl + 1 < G && w0(kl + 1) <= last) ++kl;
+        while (kl > 0 && w0(kl) > last) --kl;
+        row_partials_at(a.part_acc, a.part_mom, kl - kf + 1,
+                        [=](int s) {
+                            const int k = kf + s;
+                            const int seg = w0(k) / tot == tile ? 0 : 1;
+                            return static_cast<int64_t>(2 * k + seg) * kTcRows + rr;
+                        },
+                        a.n_pad, want_traj, R, R, gw, red);
+    } else {
+        row_partials(a.part_acc, a.part_mom, splits, part_rows, a.n_pad, j, want_traj, R, R, gw, red);
+    }
     named_bar_sync(bar_id, 32 * R);
     if (gw == 0) {
         float accv[8], e2, e4;
@@ -155,16 +179,43 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         const int* act = cur ? a.act[1] : a.act[0];
         int tiles, sp, cps;
         tc_device_shape(M_act, a.shape_ctas, a.total_chunks, &tiles, &sp, &cps);
-        const bool active = bid < tiles * sp;
-        const int tile = bid / sp, split = bid % sp;
-        const int m0 = tile * kTcRows;
-        const int c_begin = split * cps;
-        const int nch = active ? min(a.total_chunks, c_begin + cps) - c_begin : 0;
         const int part_rows = tiles * kTcRows;
         const bool mom = t < kTrajLen;
         const bool use_lo = t >= a.lo_from;
+        // Work of this CTA: one (restart tile, sample split) of the one-wave shape, or, when that
+        // shape leaves more than a sixteenth of the CTAs idle, an equal share of the (tile x
+        // chunk) work in tile-major order (at most two segments: the end of one tile's chunk
+        // range and the start of the next; partials per segment in slot 2 bid + segment).
+        const int64_t Wsk = static_cast<int64_t>(tiles) * a.total_chunks;
+        const bool sk = a.streamk && tiles * sp < (G * 15) / 16 && Wsk >= G;
+        int nseg = 0, seg_tile[2] = {0, 0}, seg_c0[2] = {0, 0}, seg_nch[2] = {0, 0};
+        if (!sk) {
+            if (bid < tiles * sp) {
+                nseg = 1;
+                seg_tile[0] = bid / sp;
+                seg_c0[0] = (bid % sp) * cps;
+                seg_nch[0] = min(a.total_chunks, seg_c0[0] + cps) - seg_c0[0];
+            }
+        } else {
+            const int64_t w1 = (static_cast<int64_t>(bid) + 1) * Wsk / G;
+            for (int64_t w = static_cast<int64_t>(bid) * Wsk / G; w < w1 && nseg < 2;) {
+                const int tl = static_cast<int>(w / a.total_chunks);
+                const int64_t e = min(w1, static_cast<int64_t>(tl + 1) * a.total_chunks);
+                seg_tile[nseg] = tl;
+                seg_c0[nseg] = static_cast<int>(w - static_cast<int64_t>(tl) * a.total_chunks);
+                seg_nch[nseg] = static_cast<int>(e - w);
+                ++nseg;
+                w = e;
+            }
+        }
 
-        if (active && warp >= 2 && warp < 2 + kEpiWarps) {
+        for (int seg = 0; seg < nseg; ++seg) {
+        const int m0 = seg_tile[seg] * kTcRows;
+        const int c_begin = seg_c0[seg];
+        const int nch = seg_nch[seg];
+        const int64_t prow0 = sk ? static_cast<int64_t>(2 * bid + seg) * kTcRows
+                                 : static_cast<int64_t>(bid % sp) * part_rows + m0;
+        if (warp >= 2 && warp < 2 + kEpiWarps) {
             // restart tile -> BF16 hi (shared memory) and lo (beside it, or in tensor memory)
             convert_restart_tile<tc_split_b(TC), tc_lo_in_tmem(TC)>(a.B32, a.ldb, act, m0, M_act, a.n_pad, sA,
                                                                     a.a_bytes, tmem + kALoCol, true, use_lo);
@@ -172,9 +223,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         }
         // The restart tile is complete for the first-product issuer (warp 1) once the epilogue
         // warps pass this barrier; the TMA producer starts loading X~ without waiting for it.
-        if (active && warp >= 1 && warp < 2 + kEpiWarps) named_bar_sync(10, 32 * (1 + kEpiWarps));
+        if (warp >= 1 && warp < 2 + kEpiWarps) named_bar_sync(10, 32 * (1 + kEpiWarps));
 
-        if (active) {
+        {
             if (warp == 0) {
                 // -------------------------------------------------------------- TMA producer
                 if (lane == 0) {
@@ -359,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 }
                 ec += static_cast<uint32_t>(nch);
                 const int grow = m0 + row;
-                const int64_t prow = static_cast<int64_t>(split) * part_rows + grow;
+                const int64_t prow = prow0 + row;
                 if (ok && h < 2) {  // accumulator read-out: two warps per lane quarter
                     ok = __all_sync(0xffffffffu, mbar_wait(d2_full, d2n & 1u, abort_flag, a.status, a.wait_ns));
                     if (ok) {
@@ -410,6 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 }
             }
         }
+        }  // segments
         // ---------------------------------------------------------------- finish the rows
         tc_fence_before();
         bar_target += static_cast<unsigned int>(G);
@@ -420,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             const int grp = warp / R, gw = warp % R;
             float* red = fin_scratch + grp * R * (2 * a.n_pad + 4);
             for (int j = bid * ngrp + grp; j < M_act; j += G * ngrp)
-                group_finish_row(a, act, j, sp, part_rows, t, red, R, gw, 2 + grp);
+                group_finish_row(a, act, j, sp, part_rows, sk ? Wsk : 0, t, red, R, gw, 2 + grp);
         }
         bar_target += static_cast<unsigned int>(G);
         if (!grid_barrier(a.bar_ctr, bar_target + a.stall, abort_flag, a.status, a.wait_ns)) break;
@@ -504,6 +556,7 @@ static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, co
     a.stall = p.stall ? 1u : 0u;
     a.proj = RowProj{p.Wp, p.Wp ? p.nw : 0, p.ldw};
     a.lo_from = p.lo_from;
+    a.streamk = p.streamk;
     a.stages = static_cast<int>(L.stages);
     a.a_bytes = L.a_bytes;
     a.xsub_bytes = L.xsub_bytes;

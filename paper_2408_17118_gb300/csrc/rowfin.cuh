@@ -108,9 +108,11 @@ __device__ __forceinline__ void finish_row_loaded(const float (&accv)[8], const 
 // and sum z^4); the V partial sums are then combined in the order v = 0, 1, ..., V - 1
 // (row_combine). A group of R real warps (warp w of the group) computes virtual warps w,
 // w + R, ... into red: [V][n_pad] sums, [V][n_pad] compensations, [V][4] moment sums.
-__device__ __forceinline__ void row_partials(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
-                                             int splits, int part_rows, int n_pad, int j, bool want_mom, int V,
-                                             int R, int w, float* red) {
+// General form: partial s of the row sits at row index prow_of(s) of part_acc / part_mom.
+template <typename RowOf>
+__device__ __forceinline__ void row_partials_at(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
+                                                int splits, RowOf prow_of, int n_pad, bool want_mom, int V, int R,
+                                                int w, float* red) {
     const int lane = threadIdx.x & 31;
     const int nq = (n_pad + 31) >> 5;
     float* red_s = red;
@@ -121,7 +123,8 @@ __device__ __forceinline__ void row_partials(const float* __restrict__ part_acc,
         CompSum m2, m4;
 #pragma unroll 8
         for (int sp = v; sp < splits; sp += V) {
-            const float* p = part_acc + (static_cast<int64_t>(sp) * part_rows + j) * n_pad;
+            const int64_t prow = prow_of(sp);
+            const float* p = part_acc + prow * n_pad;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (q >= nq) break;
@@ -129,8 +132,8 @@ __device__ __forceinline__ void row_partials(const float* __restrict__ part_acc,
                 if (k < n_pad) acc[q].add(__ldcg(p + k));
             }
             if (want_mom && lane == 0) {
-                m2.add(__ldcg(part_mom + (static_cast<int64_t>(sp) * part_rows + j) * 4 + 0));
-                m4.add(__ldcg(part_mom + (static_cast<int64_t>(sp) * part_rows + j) * 4 + 1));
+                m2.add(__ldcg(part_mom + prow * 4 + 0));
+                m4.add(__ldcg(part_mom + prow * 4 + 1));
             }
         }
 #pragma unroll
@@ -149,6 +152,15 @@ __device__ __forceinline__ void row_partials(const float* __restrict__ part_acc,
             redm[4 * v + 3] = m4.c;
         }
     }
+}
+
+// Split layout: partial s of active row j at row s * part_rows + j.
+__device__ __forceinline__ void row_partials(const float* __restrict__ part_acc, const float* __restrict__ part_mom,
+                                             int splits, int part_rows, int n_pad, int j, bool want_mom, int V,
+                                             int R, int w, float* red) {
+    row_partials_at(part_acc, part_mom, splits,
+                    [=](int sp) { return static_cast<int64_t>(sp) * part_rows + j; }, n_pad, want_mom, V, R, w,
+                    red);
 }
 
 // One warp combines the V virtual-warp sums of row_partials (after a barrier of the group).

@@ -208,8 +208,8 @@ def test_persistent_stage_equals_per_launch(ctx, case):
     else:  # n_pad 208: 64-sample chunks, one issuer, 256-column accumulator
         w = synth.eeg_like(200, 12_000, 200, seed=7, n_components=4)
     out = []
-    for persistent in (1, 0):
-        W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, seed=7, stage_persistent=persistent)
+    for persistent in (1, 0):  # (equal work shares off: the per-launch path's split of the samples)
+        W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, seed=7, stage_persistent=persistent, stage_streamk=0)
         st = json.loads(ica.ica_last_stats(ctx))
         out.append((W, kurt, st))
     (W0, k0, s0), (W1, k1, s1) = out
@@ -315,3 +315,25 @@ def test_fluctuation_of_algorithms_1_and_2(ctx):
     assert np.sum(f1[:8] < 1e-5) >= 6 and np.sum(f2[:8] < 1e-5) >= 6, (f1, f2)
     cross = np.max(np.abs(runs[1][0][:8] @ runs[2][0][:8].T), axis=1)  # same directions, any order
     assert np.all(cross >= 1 - 1e-5), cross
+
+
+@pytest.mark.parametrize("N,M", [(48, 2560), (200, 8192)])
+def test_stage_equal_work_shares(ctx, N, M):
+    """M restarts = 20 or 64 restart tiles: the one-wave shape (2 sample splits per tile at 64
+    tiles, 7 at 20) leaves 24 and 12 of the 152 SMs idle, so the persistent stage hands every CTA
+    an equal share of the (tile x chunk) work instead. Same fixed points as the one-wave shape:
+    the same components (|cos| >= 1 - 1e-5) and kurtoses (relative 1e-5), summation order aside."""
+    import json
+
+    from paper_2408_17118_gb300 import ica
+
+    w = synth.eeg_like(N, 20_000, M, seed=N + 1, n_components=4)
+    res = []
+    for sk in (1, 0):
+        W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_BF16, seed=3, stage_streamk=sk)
+        st = json.loads(ica.ica_last_stats(ctx))
+        res.append((W, kurt, st))
+    (W1, k1, s1), (W0, k0, s0) = res
+    assert s1["stage_streamk_first_iteration"] == 1 and s0["stage_streamk_first_iteration"] == 0
+    assert np.all(np.abs(np.sum(W1 * W0, axis=1)) >= 1 - 1e-5)
+    assert np.all(np.abs(k1 - k0) <= 1e-5 * np.abs(k0))
