@@ -79,6 +79,9 @@ def parse_args():
                          "keep floor and the redundancy rule prune; <0: the trained threshold)")
     ap.add_argument("--no-network-leg", action="store_true",
                     help="skip the leg that times and judges the pruner with the network's trained threshold")
+    ap.add_argument("--no-fp8-leg", action="store_true",
+                    help="skip the leg that times and judges the FP8 form (iterations 1..3 of each stage on E4M3 "
+                         "operands) with the headline's pruner")
     ap.add_argument("--prune-cos", type=float, default=0.99,
                     help="|cos| at iteration 5 above which a restart led by another one is redundant (0: off)")
     ap.add_argument("--plain-components", type=int, default=-1, metavar="K",
@@ -481,6 +484,24 @@ def run_ours(args):
         network["judge"] = judge_same_components(Wu.cpu().numpy(), u_st[-1], Wn.cpu().numpy(), Xw.cpu().numpy())
         log(f"network leg {network}")
 
+    # the FP8 form with the headline's pruner: timed (side steps) and judged like the headline,
+    # against the unpruned BF16 fit (or, without the pruner, against the headline's BF16 fit)
+    fp8 = None
+    if not args.no_fp8_leg:
+        opts_8 = ica.ica_default_opts(precision=ica.ICA_FP8, profile=1)
+        if prune:
+            opts_8.prune_tau = tau
+            opts_8.prune_cos = args.prune_cos
+        fit(opts_8, params)
+        f_ms, f_st, (W8, k8, _), _ = timed_steps(opts_8, params, max(1, args.side_steps))
+        fp8 = summary(f_st, f_ms)
+        fp8["stage_fp8_launches"] = f_st[-1].get("stage_fp8_launches")
+        fp8["stage_ms"] = sum(x["fused"]["iteration"]["ms"] for x in f_st) / len(f_st)
+        ref_W, ref_st = (Wu, u_st[-1]) if prune else (W, stats[-1])
+        fp8["judge"] = judge_same_components(ref_W.cpu().numpy(), ref_st, W8.cpu().numpy(), Xw.cpu().numpy())
+        fp8["judged_against"] = "unpruned BF16 fit" if prune else "headline BF16 fit"
+        log(f"fp8 leg {fp8}")
+
     # e2e through the public API with host buffers: H2D of X (pinned), whiten + fit, D2H of W, kurt
     e2e_ms, e2e_flops = [], 0.0
     W_host = torch.empty((K, N), dtype=torch.float64).pin_memory()
@@ -602,6 +623,7 @@ def run_ours(args):
             "nominal_tflops": nominal_all / (total_ms_max / 1e3) / 1e12,
             "headline": head, "unpruned": unpruned, "pruner_judge": judge, "pruner_training": train_report,
             "pruner_network_leg": network,
+            "fp8_leg": fp8,
             "plain_fp32": plain,
             "speedup_vs_plain_fp32": (plain["time_to_all_components_s"] / head["time_to_all_components_s"]
                                       if plain["components"] == K else plain["speedup_same_components"])

@@ -19,7 +19,7 @@
  *     iteration at first, then every second and every fourth on the FP32 path; with the
  *     restart pruner also when it runs and before the kurtosis pass); ica_whiten,
  *     ica_deflation_basis, ica_fp_step and ica_kurtosis synchronise once at the end to read
- *     the device status word; ica_init_restarts and ica_reduce only enqueue.
+ *     the device status word; ica_init_restarts, ica_reduce and ica_quantize_e4m3 only enqueue.
  *   - The return value is an ica_status. Nothing is thrown across the ABI. After an error the
  *     outputs are unspecified and the context stays usable.
  *   - The paper writes samples as M and restarts as L; this interface writes samples as T
@@ -52,6 +52,14 @@ typedef enum {
     ICA_FP32 = 0,        /* fused FP32 CUDA-core iteration (Z never stored) */
     ICA_BF16 = 1,        /* fused tcgen05 iteration, BF16 operands, FP32 accumulate and cube,
                             followed by FP32 refinement of the top distinct candidates */
+    ICA_FP8 = 2,         /* as ICA_BF16, with iterations 1..fp8_iters of each component's stage
+                            on E4M3 operands (tcgen05 kind::f8f6f4, FP32 accumulate and cube):
+                            X~ with one power-of-two scale per row, the restart rows with a
+                            power-of-two scale per column of X~, P = Z o Z o Z with one
+                            power-of-two scale per restart row set from the row's largest |z| of
+                            the previous iteration (Section 3.1's update, same fixed points; the
+                            later BF16 iterations and the FP32 refinement set the accuracy). The
+                            FP8 iterations need the persistent stage; otherwise they run in BF16. */
     ICA_PLAIN_FP32 = 3   /* Algorithm 2 written literally: Z = B X~ materialised in device
                             memory, cube, second product (cuBLAS SGEMM, no TF32). The
                             comparison baseline, not the fast path. */
@@ -141,19 +149,22 @@ typedef struct {
                               idle, every CTA takes an equal share of the (tile x chunk) work
                               instead (results then differ from the per-launch path by FP32
                               summation order); 0: always the one-wave shape */
-    double* record_cands;  /* optional (device, BF16 path): n_components x refine_topk x N FP64.
-                              Row (i, j) = w = G^T b of the j-th distinct candidate of component i
-                              after the FP32 refinement (Section 3.3: the candidate in the full
-                              whitened space), normalised; zero rows where fewer candidates
-                              were distinct. The pick of component i is among them. For an FP64
-                              re-check of the pick outside the library. */
+    double* record_cands;  /* optional (device, BF16 / FP8 path): n_components x refine_topk x N
+                              FP64. Row (i, j) = w = G^T b of the j-th distinct candidate of
+                              component i after the FP32 refinement (Section 3.3: the candidate in
+                              the full whitened space), normalised; zero rows where fewer
+                              candidates were distinct. The pick of component i is among them. For
+                              an FP64 re-check of the pick outside the library. */
+    int fp8_iters;         /* ICA_FP8: stage iterations 1..fp8_iters (0-based) on E4M3 operands
+                              (default 3, so that iteration 4, the last before the pruner, is BF16
+                              again; 0: none) */
 } ica_opts;
 
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
    no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05, prune_cos 0.99), no
    recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 3,
-   prune_gauss 1, stage_streamk 1. */
+   prune_gauss 1, stage_streamk 1, fp8_iters 3. */
 void ica_default_opts(ica_opts* opts);
 
 /* Human-readable name of a status code (static string). */
@@ -221,7 +232,7 @@ int ica_init_restarts(ica_ctx* ctx, uint64_t seed, int component, int M, int n, 
 
 /* Reduction basis (Section 3.3, Eq. 6-7): W k x N FP64 with orthonormal rows (ld = N),
    0 <= k < N. Output G: (N-k) x N FP64 (ld = N), G = (F~F~^T)^(-1/2) F~, F~ = first N-k rows
-   of I - W^T W. ICA_ERR_ILLCOND if F~F~^T has an eigenvalue <= 1e-10. */
+   of I - W^T W. ICA_ERR_ILLCOND if F~F~^T has an eigenvalue <= 1e-14. */
 int ica_deflation_basis(ica_ctx* ctx, const double* W, int k, int N, double* G);
 
 /* Reduction of signals (Eq. 8): X~ = G Xw. G: n x N FP64 (ld = N); Xw: N x T FP32 (ld = T).
@@ -230,6 +241,16 @@ int ica_deflation_basis(ica_ctx* ctx, const double* W, int k, int N, double* G);
    multiples of 8. */
 int ica_reduce(ica_ctx* ctx, const double* G, int n, int N, const float* Xw, int64_t T,
                float* Xt32, int64_t ldx32, uint16_t* Xt16, int64_t ldx16);
+
+/* E4M3 operand of the FP8 iterations (ICA_FP8, Section 3.1's update on 8-bit operands): the
+   FP32 reduced data Xt32 (n x ldx32, ld a multiple of 8) -> X8 (n8 rows of ld8 bytes, n8 = n
+   rounded up to 32, ld8 >= T and a multiple of 16), row k stored as e4m3(x 2^e_k) (round to
+   nearest even, saturating; byte 0x7e = 448), e_k the largest integer with max_t |x_kt| 2^e_k
+   <= 448 (0 for a zero row); rows n..n8-1 and samples T..ld8-1 zero. scales (3 n8 + 1 floats):
+   2^e_k, 2^(c - e_k) (the factor applied to column k of a restart row), 2^-e_k, and last 2^-c,
+   c = 8 + min_{k<n} e_k. Needs a workspace of ica_workspace_bytes(n, T, 1, ICA_FP8 opts). */
+int ica_quantize_e4m3(ica_ctx* ctx, const float* Xt32, int n, int64_t T, int64_t ldx32, uint8_t* X8, int64_t ld8,
+                      float* scales);
 
 /* One matrix-form update (Eq. 4-5 as written in Algorithm 2) for M rows without
    normalisation: Bnew = (Z o Z o Z) X~^T / T - 3 B with Z = B X~.

@@ -195,7 +195,11 @@ def deflation_basis(W: np.ndarray, N: int) -> np.ndarray:
     Ft = F[:n, :]
     S = Ft @ Ft.T
     lam, U = np.linalg.eigh(S)
-    if lam.min() <= 1e-10:
+    # Eq. 7 keeps the first n rows of F; F~ F~^T is then nearly singular when the found rows nearly
+    # contain a unit vector of the first n coordinates (eigenvalues of 1e-11 occur near n = k = N/2
+    # in generic data). FP64 eigenpairs keep G accurate to about 1 % in length and 1e-9 in
+    # direction down to 1e-14; below that the basis is refused.
+    if lam.min() <= 1e-14:
         raise np.linalg.LinAlgError(f"F~ F~^T is singular (lambda_min = {lam.min():.3e})")
     S_inv_half = (U * (1.0 / np.sqrt(lam))) @ U.T
     return S_inv_half @ Ft

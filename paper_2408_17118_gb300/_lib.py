@@ -19,6 +19,7 @@ ICA_ERR_UNSUPPORTED = 7
 # ica_precision
 ICA_FP32 = 0
 ICA_BF16 = 1
+ICA_FP8 = 2
 ICA_PLAIN_FP32 = 3
 
 
@@ -48,6 +49,7 @@ class ica_opts(C.Structure):
         ("stage_lo_from", C.c_int),
         ("stage_streamk", C.c_int),
         ("record_cands", C.c_void_p),
+        ("fp8_iters", C.c_int),
     ]
 
 
@@ -87,6 +89,7 @@ SIGNATURES = {
     "ica_init_restarts": (i32, [vp, u64, i32, i32, i32, vp, i32]),
     "ica_deflation_basis": (i32, [vp, vp, i32, i32, vp]),
     "ica_reduce": (i32, [vp, vp, i32, i32, vp, i64, vp, i64, vp, i64]),
+    "ica_quantize_e4m3": (i32, [vp, vp, i32, i64, i64, vp, i64, vp]),
     "ica_fp_step": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_kurtosis": (i32, [vp, i32, vp, i32, i32, vp, i64, i64, vp, vp]),
     "ica_fp_step_noalloc": (i32, [i32, vp, i32, i32, vp, i64, i64, vp, vp, vp]),

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #ifndef ICA_WAIT_NS
@@ -252,6 +253,42 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uin
 // Instruction descriptor, kind::f16: FP32 D, BF16 A and B, A K-major, B K- or MN-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N, uint32_t b_mn_major) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (b_mn_major << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f8f6f4: FP32 D, E4M3 A and B (format code 0), A K-major, B K- or
+// MN-major. One MMA covers K = 32 (32 bytes of each operand row).
+__host__ __device__ constexpr uint32_t idesc_e4m3(uint32_t M, uint32_t N, uint32_t b_mn_major) {
+    return (1u << 4) | (b_mn_major << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+// D[tmem] (+)= A[smem desc] * B[smem desc], kind::f8f6f4 (E4M3 inputs, FP32 accumulate).
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Four floats -> four E4M3 bytes (round to nearest even, saturating at +-448), x0 in the lowest byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float x0, float x1, float x2, float x3) {
+    uint32_t out;
+    asm("{\n\t.reg .b16 lo, hi;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f32 lo, %2, %1;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f32 hi, %4, %3;\n\t"
+        "mov.b32 %0, {lo, hi};\n\t}"
+        : "=r"(out)
+        : "f"(x0), "f"(x1), "f"(x2), "f"(x3));
+    return out;
+}
+// Largest e with m * 2^e <= lim (m > 0 finite, lim > 0): the exponent of a power-of-two scale that
+// maps magnitudes up to m into [-lim, lim]. ldexpf is exact, so the result is exact.
+__host__ __device__ inline int pow2_fit_exponent(float m, float lim) {
+    if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
+    int e = ilogbf(lim) - ilogbf(m);
+    while (e > -126 && ldexpf(m, e) > lim) --e;
+    while (e < 126 && ldexpf(m, e + 1) <= lim) ++e;
+    return e;
 }
 
 // Byte offset of the 16-byte chunk `c` (0..7) of row `r` inside a 128-byte-swizzled tile whose

@@ -112,6 +112,8 @@ struct Layout {
     int64_t ldx = 0;
     size_t jscr;  // Jacobi scratch (mixed-precision solver above its shared-memory size)
     size_t W32;   // Algorithm 1: FP32 copy of the found components (N x n_pad_max)
+    int64_t ld8 = 0;  // FP8: bytes per row of the E4M3 copy of X~
+    size_t X8, fp8sc, rmax, zmax;  // FP8: E4M3 X~ (256 rows), its scales, row maxima, per-restart |z| maxima
     size_t status, counts, Xt32, Xt16, Z, B32, Bact, act0, act1, cand, flags, iters, traj, alpha, ups, excl, slots, pruned,
         part_acc, part_mom, G, jA, jV, lam, t1, t2, t3, t4, cov_part, comp_stats, comp_rows, total;
 };
@@ -133,7 +135,15 @@ Layout make_layout(int N, int64_t T, int M, int precision) {
     L.status = take(16 * sizeof(int));
     L.counts = take(32 * sizeof(int));
     L.Xt32 = take(sizeof(float) * L.n_pad_max * static_cast<size_t>(L.ldx));
-    L.Xt16 = take(precision == ICA_BF16 ? sizeof(uint16_t) * L.n_pad_max * static_cast<size_t>(L.ldx) : 0);
+    const bool tc = precision == ICA_BF16 || precision == ICA_FP8;
+    L.Xt16 = take(tc ? sizeof(uint16_t) * L.n_pad_max * static_cast<size_t>(L.ldx) : 0);
+    const bool f8 = precision == ICA_FP8;
+    L.ld8 = round_up64(T, 16);
+    const int n8_max = (N + 31) / 32 * 32;
+    L.X8 = take(f8 ? static_cast<size_t>(n8_max) * static_cast<size_t>(L.ld8) : 0);
+    L.fp8sc = take(f8 ? sizeof(float) * (3 * 256 + 1) : 0);
+    L.rmax = take(f8 ? sizeof(unsigned) * 256 : 0);
+    L.zmax = take(f8 ? sizeof(float) * L.M_pad : 0);
     L.Z = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(M) * L.ldx : 0);
     L.B32 = take(sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max);
     L.Bact = take(precision == ICA_PLAIN_FP32 ? sizeof(float) * static_cast<size_t>(L.M_pad) * L.n_pad_max : 0);
@@ -205,6 +215,19 @@ int encode_xmap(ica_ctx* c, CUtensorMap* map, const uint16_t* Xt16, int n_pad, i
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = c->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(Xt16), dims, strides, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ICA_OK : ICA_ERR_CUDA;
+}
+
+// E4M3 copy of X~ (n8 rows of ld bytes): boxes of 128 samples x n8 rows, 128-byte swizzle.
+int encode_xmap8(ica_ctx* c, CUtensorMap* map, const uint8_t* X8, int n8, int64_t T, int64_t ld) {
+    if (!c->encode) return ICA_ERR_UNSUPPORTED;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(T), static_cast<cuuint64_t>(n8)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld)};
+    cuuint32_t box[2] = {128u, static_cast<cuuint32_t>(n8)};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = c->encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(X8), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? ICA_OK : ICA_ERR_CUDA;
 }
@@ -354,6 +377,14 @@ int read_status(ica_ctx* c, const Layout& L) {
 //           G = F~ + U^T H U F~ = E_n + U^T (H (U~ - U U^T W) - W), U~ = [U 0];
 //   k >  n: S = F~ F~^T = Q diag(l) Q^T (n x n, formed from the computed F~ so that G G^T = I
 //           holds to rounding), G = Q diag(l^(-1/2)) Q^T F~.
+// Smallest eigenvalue of F~F~^T (Eq. 7) accepted for the deflation basis. Keeping the first n
+// rows of F makes F~F~^T = I - W_{:,:n}^T W_{:,:n} nearly singular when the found components
+// nearly contain a unit vector of the first n coordinates; where the two subspaces have about equal
+// dimension (i near N / 2) eigenvalues of 1e-11 occur in generic data. With FP64 eigenpairs
+// (absolute error about 1e-16) an eigenvalue of 1e-14 still sets G's length along its eigenvector
+// to within 1 % and its direction to within 1e-9, so only eigenvalues below that are an error.
+constexpr double kBasisIllCond = 1e-14;
+
 int deflation_basis_impl(ica_ctx* c, const Layout& L, const double* W, int k, int N, double* G) {
     cudaStream_t s = c->stream;
     const int n = N - k;
@@ -368,7 +399,7 @@ int deflation_basis_impl(ica_ctx* c, const Layout& L, const double* W, int k, in
         KL(launch_gemm_f64(s, k, k, n, 1.0, W, N, 1, W, 1, N, 0.0, A, k));   // U U^T
         KL(launch_gemm_f64(s, k, k, n, 1.0, W, N, 1, W, 1, N, 0.0, T4, k));  // kept copy
         KL(launch_jacobi(s, A, V, lam, k, status, 60, c->ws + L.jscr));
-        KL(launch_scale_cols_fn(s, V, lam, k, 1, T1, status, 1e-10));      // Q f(mu)
+        KL(launch_scale_cols_fn(s, V, lam, k, 1, T1, status, kBasisIllCond));  // Q f(mu)
         KL(launch_gemm_f64(s, k, k, k, 1.0, T1, k, 1, V, 1, k, 0.0, T2, k));  // H = Q f Q^T
         KL(launch_pad_cols(s, W, k, N, n, T3));                              // U~ = [U 0]
         KL(launch_gemm_f64(s, k, N, k, -1.0, T4, k, 1, W, N, 1, 1.0, T3, N));  // Y = U~ - (U U^T) W
@@ -382,7 +413,7 @@ int deflation_basis_impl(ica_ctx* c, const Layout& L, const double* W, int k, in
     KL(launch_gemm_f64(s, n, N, k, -1.0, W, 1, N, W, N, 1, 1.0, T3, N));  // F~ = E_n - U^T W
     KL(launch_gemm_f64(s, n, n, N, 1.0, T3, N, 1, T3, 1, N, 0.0, A, n));  // S = F~ F~^T (Gram form)
     KL(launch_jacobi(s, A, V, lam, n, status, 60, c->ws + L.jscr));
-    KL(launch_scale_cols_fn(s, V, lam, n, 0, T1, status, 1e-10));
+    KL(launch_scale_cols_fn(s, V, lam, n, 0, T1, status, kBasisIllCond));
     KL(launch_gemm_f64(s, n, n, n, 1.0, T1, n, 1, V, 1, n, 0.0, T2, n));  // S^(-1/2)
     KL(launch_gemm_f64(s, n, N, n, 1.0, T2, n, 1, T3, N, 1, 0.0, G, N));  // G = S^(-1/2) F~
     return ICA_OK;
@@ -447,6 +478,7 @@ void ica_default_opts(ica_opts* o) {
     o->stage_lo_from = 3;
     o->prune_gauss = 1;
     o->stage_streamk = 1;
+    o->fp8_iters = 3;
 }
 
 const char* ica_status_string(int st) {
@@ -580,6 +612,23 @@ int ica_reduce(ica_ctx* c, const double* G, int n, int N, const float* Xw, int64
     return ICA_OK;
 }
 
+int ica_quantize_e4m3(ica_ctx* c, const float* Xt32, int n, int64_t T, int64_t ldx32, uint8_t* X8, int64_t ld8,
+                      float* scales) {
+    if (!c || !Xt32 || !X8 || !scales || n < 1 || n > kMaxN || T < 1 || ldx32 < T || ldx32 % 8 || ld8 < T ||
+        ld8 % 16)
+        return ICA_ERR_ARG;
+    const Layout L = make_layout(n, T, 1, ICA_FP8);
+    int rc = check_ws(c, L);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    int extra = 0;
+    CK(launch_fp8_copy(c->stream, Xt32, ldx32, T, n, (n + 31) / 32 * 32, at<unsigned>(c, L.rmax), scales, X8, ld8,
+                       &extra));
+    c->launches += extra;
+    c->launches_total += extra;
+    return ICA_OK;
+}
+
 int ica_fp_step(ica_ctx* c, int precision, const float* B, int M, int n, const void* Xt, int64_t T, int64_t ldx,
                 float* Bnew, float* moments) {
     if (!c || !B || !Xt || !Bnew || M < 1 || M > 65536 || n < 1 || n > kMaxN || T < 1 || ldx < T || ldx % 8)
@@ -650,9 +699,11 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     ica_opts d;
     ica_default_opts(&d);
     const ica_opts o = opts ? *opts : d;
-    if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_PLAIN_FP32) return ICA_ERR_UNSUPPORTED;
-    if (o.precision == ICA_BF16 && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
-    if (o.wait_ns < 0 || (o.record_cands && o.precision != ICA_BF16)) return ICA_ERR_ARG;
+    if (o.precision != ICA_FP32 && o.precision != ICA_BF16 && o.precision != ICA_FP8 && o.precision != ICA_PLAIN_FP32)
+        return ICA_ERR_UNSUPPORTED;
+    const bool tcp = o.precision == ICA_BF16 || o.precision == ICA_FP8;  // tensor-core stage + FP32 refinement
+    if (tcp && (o.refine_topk < 1 || o.refine_topk > 32 || o.refine_iters < 1)) return ICA_ERR_ARG;
+    if (o.wait_ns < 0 || (o.record_cands && !tcp) || o.fp8_iters < 0) return ICA_ERR_ARG;
     if (o.algorithm != 1 && o.algorithm != 2) return ICA_ERR_ARG;
     if (o.stage_lo_from < 0) return ICA_ERR_ARG;
     const bool alg1 = o.algorithm == 1;
@@ -663,7 +714,15 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
-    const bool bf16 = o.precision == ICA_BF16;
+    const bool bf16 = tcp;  // the BF16 stage (and FP8 iterations inside it) + FP32 refinement
+    // FP8: iterations 1..fp8_iters of each component's stage take E4M3 operands; iteration 0 (BF16)
+    // records each restart's largest |z| for the scale of the first FP8 iteration's P. Needs the
+    // persistent stage (the per-launch path runs those iterations in BF16).
+    const int fp8_until = o.precision == ICA_FP8 && o.fp8_iters > 0 ? 1 + o.fp8_iters : 0;
+    uint8_t* X8 = at<uint8_t>(c, L.X8);
+    float* fp8sc = at<float>(c, L.fp8sc);
+    float* zmax = at<float>(c, L.zmax);
+    long long fp8_launches = 0;
     const double inv_T = 1.0 / static_cast<double>(T);
     int* status = at<int>(c, L.status);
     int* counts = at<int>(c, L.counts);  // [0], [1]: active counts (double-buffered); [2]: candidates
@@ -760,6 +819,13 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             if (rc) return rc;
             rc = timed(K_REDUCE, 0.0, [&] {
                 KL(launch_rows_gemm(s, G, n, n_pad, N, Xw, T, T, nullptr, Xt32, ldx, bf16 ? Xt16 : nullptr, ldx));
+                if (fp8_until > 1) {  // E4M3 copy of X~ with per-row power-of-two scales
+                    int extra = 0;
+                    CK(launch_fp8_copy(s, Xt32, ldx, T, n, (n + 31) / 32 * 32, at<unsigned>(c, L.rmax), fp8sc, X8,
+                                       L.ld8, &extra));
+                    c->launches += extra;
+                    c->launches_total += extra;
+                }
                 return ICA_OK;
             });
             if (rc) return rc;
@@ -788,7 +854,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
             CK(cudaMemsetAsync(traj, 0, sizeof(float) * M * kTrajLen * 2, s));
             KL(launch_iota(s, act[0], M, counts + 0));
             fa = FusedArgs();
-            fa.precision = o.precision;
+            fa.precision = bf16 ? ICA_BF16 : o.precision;
             fa.B32 = B32;
             fa.ldb = n_pad;
             fa.n_pad = n_pad;
@@ -807,9 +873,14 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                            M <= 152 * kTcRows;
             while (t < iters && M_host > 0) {
                 if (persist) {
-                    const int t_end = (prune_this && t < kTrajLen) ? std::min(iters, kTrajLen) : iters;
+                    // one launch per segment of iterations: [0, 1) BF16 and [1, fp8_until) FP8 in the
+                    // FP8 form, [.., kTrajLen) up to the pruner, the rest
+                    int t_end = (prune_this && t < kTrajLen) ? std::min(iters, kTrajLen) : iters;
+                    const bool f8_now = fp8_until > 1 && t >= 1 && t < fp8_until;
+                    if (fp8_until > 1) t_end = std::min(t_end, t < 1 ? 1 : (t < fp8_until ? fp8_until : t_end));
                     CUtensorMap map;
-                    rc = encode_xmap(c, &map, Xt16, n_pad, T, ldx);
+                    rc = f8_now ? encode_xmap8(c, &map, X8, (n + 31) / 32 * 32, T, L.ld8)
+                                : encode_xmap(c, &map, Xt16, n_pad, T, ldx);
                     if (rc) return rc;
                     StageLaunch sl{};
                     sl.B32 = B32;
@@ -843,6 +914,11 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
                     sl.ldw = n_pad;
                     sl.lo_from = o.stage_lo_from;
                     sl.streamk = o.stage_streamk;
+                    sl.fp8 = f8_now;
+                    sl.zmax = fp8_until > 1 ? zmax : nullptr;
+                    sl.track_until = fp8_until;
+                    sl.fp8sc = fp8sc;
+                    if (f8_now) ++fp8_launches;
                     CK(cudaMemsetAsync(stage_bar, 0, sizeof(unsigned int), s));
                     cudaError_t le = cudaSuccess;
                     int resident = 0;
@@ -1201,6 +1277,7 @@ int ica_order_fit(ica_ctx* c, const float* Xw, int N, int64_t T, int M, int n_co
     json_kv(js, "launches", static_cast<double>(c->launches));
     json_kv(js, "launches_total", static_cast<double>(c->launches_total));
     json_kv(js, "stage_persistent_launches", static_cast<double>(persist_launches));
+    json_kv(js, "stage_fp8_launches", static_cast<double>(fp8_launches));
     {   // the persistent stage's first iteration (all M restarts) in equal work shares
         int tl = 0, sp0 = 0, cps0 = 0;
         const int tc0 = tc_chunk(round_up(N, 16));

@@ -102,6 +102,12 @@ cudaError_t launch_pad_cols(cudaStream_t s, const double* W, int k, int N, int n
 cudaError_t launch_rows_gemm(cudaStream_t s, const double* G, int n, int n_pad, int N, const float* X,
                              int64_t T, int64_t ldxin, const double* bias, float* out32, int64_t ld32,
                              uint16_t* out16, int64_t ld16);
+// E4M3 copy of the FP32 rows X32 (n rows of ldx floats; rows n..n8-1 and samples T..ld8-1 zero) into
+// X8 (n8 rows of ld8 bytes, ld8 a multiple of 16, n8 <= 256), row k scaled by a power of two 2^e_k
+// that maps its largest magnitude into [-448, 448]. sc (3 n8 + 1 floats): 2^e_k, 2^(c - e_k),
+// 2^-e_k and 2^-c with c = 8 + min_k e_k. rmax: n8 unsigned scratch. *launches += kernels launched.
+cudaError_t launch_fp8_copy(cudaStream_t s, const float* X32, int64_t ldx, int64_t T, int n, int n8,
+                            unsigned* rmax, float* sc, uint8_t* X8, int64_t ld8, int* launches);
 
 // ---- k_fp32.cu ----
 size_t fp32_smem_bytes(int n_pad);
@@ -211,6 +217,10 @@ struct StageLaunch {
     int nw, ldw;
     int lo_from;       // iterations t >= lo_from add the restart rows' low BF16 term (0: every iteration)
     int streamk;       // 1: equal shares of the (tile x chunk) work when the one-wave shape leaves SMs idle
+    bool fp8;          // the FP8 form: E4M3 operands (xmap: the E4M3 copy of X~, box {128, round_up(n, 32)})
+    float* zmax;       // per restart: largest |z| of its last update (null: not recorded)
+    int track_until;   // iterations t with t + 1 < track_until record zmax (when zmax is set)
+    const float* fp8sc; // FP8 form: scales of launch_fp8_copy
 };
 // resident (optional) receives the number of CTAs of the kernel that fit the GPU at once.
 cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident = nullptr);

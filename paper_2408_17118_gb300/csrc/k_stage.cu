@@ -6,6 +6,10 @@
 //                (tc_device_shape, the same one-wave shape as the per-launch update kernel) and
 //                runs the fused GEMM-cube-GEMM of Section 3.1 on the tensor cores over its
 //                chunks of X~, writing its FP32 partial of (Z o Z o Z) X~^T;
+//                BF16 operands (B as one or two BF16 terms, X~ BF16), or, in the FP8 form
+//                (F8), E4M3 operands with power-of-two scales: the restart rows (scaled per column
+//                of X~), X~ (one scale per row) and P = Z o Z o Z (one scale per restart row, from
+//                the row's largest |z| of the previous iteration), FP32 accumulation and cube;
 //   2. grid barrier; finish: groups of 16, 4 or 2 warps (fewer rows, larger groups) finish the
 //                active rows (compensated sum of the split partials in a fixed order, b' =
 //                acc / T - 3 b, normalisation, step distance, convergence flag);
@@ -54,6 +58,10 @@ struct StageArgs {
     RowProj proj;        // Algorithm 1: found components projected out of each update (none: nw = 0)
     int lo_from;         // iterations t >= lo_from add the restart rows' low BF16 term to the first product
     int streamk;         // 1: equal shares of the (tile x chunk) work when the one-wave shape leaves SMs idle
+    float* zmax;         // per restart: largest |z| of its last update (for the next FP8 iteration's P scale)
+    int track_until;     // iterations t with t + 1 < track_until record zmax
+    const float* fp8sc;  // FP8 form: the X~ scales (see launch_fp8_copy)
+    int n8;              // FP8 form: n rounded up to 32 (K of the first product, N of the second)
     int stages;
     uint32_t a_bytes, xsub_bytes, xstage_bytes, off_x, off_p, off_bar;
 };
@@ -102,19 +110,44 @@ __device__ __forceinline__ void group_finish_row(const StageArgs& a, const int* 
         row_combine(red, R, a.n_pad, a.n, want_traj, accv, &e2, &e4);
         finish_row_loaded(accv, b, nq, a.n, r, j, a.B32, a.ldb, a.inv_T, a.tol, a.flags, a.iters, a.traj, t,
                           want_traj, e2, e4, a.status, a.proj);
+        if (a.zmax && t + 1 < a.track_until) {  // largest z^2 over the partials (slot 3) -> zmax[r]
+            const int lane = threadIdx.x & 31;
+            float mx = 0.f;
+            if (Wsk > 0) {
+                const int G = static_cast<int>(gridDim.x);
+                const int64_t tot = a.total_chunks;
+                const int tile = j / kTcRows, rr = j % kTcRows;
+                const int64_t first = static_cast<int64_t>(tile) * tot, last = first + tot - 1;
+                for (int k = lane; k < G; k += 32) {
+                    const int64_t w0 = static_cast<int64_t>(k) * Wsk / G, w1 = static_cast<int64_t>(k + 1) * Wsk / G;
+                    if (w1 <= first || w0 > last) continue;  // share does not meet the tile
+                    const int seg = w0 / tot == tile ? 0 : 1;
+                    mx = fmaxf(mx, __ldcg(a.part_mom + (static_cast<int64_t>(2 * k + seg) * kTcRows + rr) * 4 + 3));
+                }
+            } else {
+                for (int sp = lane; sp < splits; sp += 32)
+                    mx = fmaxf(mx, __ldcg(a.part_mom + (static_cast<int64_t>(sp) * part_rows + j) * 4 + 3));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) a.zmax[r] = sqrtf(mx);
+        }
     }
     named_bar_sync(bar_id, 32 * R);  // the scratch is reused by the group's next row
 }
 
 }  // namespace
 
-template <int TC, int NB>
+// F8: the FP8 form (TC = 128; xmap is then the E4M3 copy of X~, box {128, n8}).
+template <int TC, int NB, bool F8>
 __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_constant__ CUtensorMap xmap, const StageArgs a) {
+    static_assert(!F8 || TC == 128, "the FP8 form uses 128-sample chunks");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_u32 = smem_u32(smem_raw);
     const uint32_t base_u32 = (raw_u32 + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_u32 - raw_u32);
-    constexpr uint32_t p_bytes = static_cast<uint32_t>(TC / 64) * 16384u;
+    constexpr uint32_t p_bytes = F8 ? 16384u : static_cast<uint32_t>(TC / 64) * 16384u;
+    constexpr int G2S = F8 ? 1 : tc_g2_issuers(TC);
     const uint32_t stages = static_cast<uint32_t>(a.stages);
     const uint32_t sA = base_u32, sX = base_u32 + a.off_x, sP = base_u32 + a.off_p;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + a.off_bar);
@@ -136,15 +169,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], tc_g2_issuers(TC));  // a commit of every second-product issuer
+            mbar_init(&empty[s], G2S);  // a commit of every second-product issuer
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(&d1_full[b], 1);
             mbar_init(&d1_empty[b], kEpiWarps / 2);  // one epilogue team per buffer
             mbar_init(&p_full[b], kEpiWarps / 2);
         }
-        mbar_init(d2_full, tc_g2_issuers(TC));
-        mbar_init(mma_done, 1 + tc_g2_issuers(TC));  // one commit per MMA-issuing thread
+        mbar_init(d2_full, G2S);
+        mbar_init(mma_done, 1 + G2S);  // one commit per MMA-issuing thread
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -157,12 +190,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr int G2S = tc_g2_issuers(TC);
-    constexpr uint32_t kD2Cols = tc_d2_cols(TC);
+    constexpr uint32_t kD2Cols = F8 ? 256u : tc_d2_cols(TC);
     constexpr uint32_t kD1Col = G2S * kD2Cols;  // Z buffers after the G2S accumulators
     static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
     constexpr uint32_t kALoCol = tc_alo_col(TC, NB);  // B's low term (tc_lo_in_tmem): n_pad / 2 columns
-    static_assert(!tc_lo_in_tmem(TC) || kALoCol + (TC == 128 ? 64u : 128u) <= 512, "B's low term must fit TMEM");
+    static_assert(F8 || !tc_lo_in_tmem(TC) || kALoCol + (TC == 128 ? 64u : 128u) <= 512, "B's low term must fit TMEM");
     static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
 
     // running counts of each role (mbarrier phases continue across the updates)
@@ -181,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         tc_device_shape(M_act, a.shape_ctas, a.total_chunks, &tiles, &sp, &cps);
         const int part_rows = tiles * kTcRows;
         const bool mom = t < kTrajLen;
-        const bool use_lo = t >= a.lo_from;
+        const bool use_lo = !F8 && t >= a.lo_from;
+        const bool trk = a.zmax != nullptr && t + 1 < a.track_until;  // record each row's largest |z|
         // Work of this CTA: one (restart tile, sample split) of the one-wave shape, or, when that
         // shape leaves more than a sixteenth of the CTAs idle, an equal share of the (tile x
         // chunk) work in tile-major order (at most two segments: the end of one tile's chunk
@@ -216,9 +249,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
         const int64_t prow0 = sk ? static_cast<int64_t>(2 * bid + seg) * kTcRows
                                  : static_cast<int64_t>(bid % sp) * part_rows + m0;
         if (warp >= 2 && warp < 2 + kEpiWarps) {
-            // restart tile -> BF16 hi (shared memory) and lo (beside it, or in tensor memory)
-            convert_restart_tile<tc_split_b(TC), tc_lo_in_tmem(TC)>(a.B32, a.ldb, act, m0, M_act, a.n_pad, sA,
-                                                                    a.a_bytes, tmem + kALoCol, true, use_lo);
+            if constexpr (F8) {  // restart tile -> E4M3, column k scaled by 2^(c - e_k)
+                convert_restart_tile_e4m3(a.B32, a.ldb, act, m0, M_act, a.n, a.n8, sA, a.fp8sc + a.n8);
+            } else {  // restart tile -> BF16 hi (shared memory) and lo (beside it, or in tensor memory)
+                convert_restart_tile<tc_split_b(TC), tc_lo_in_tmem(TC)>(a.B32, a.ldb, act, m0, M_act, a.n_pad, sA,
+                                                                        a.a_bytes, tmem + kALoCol, true, use_lo);
+            }
             tc_fence_before();
         }
         // The restart tile is complete for the first-product issuer (warp 1) once the epilogue
@@ -237,8 +273,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                         mbar_arrive_expect_tx(&full[s], a.xstage_bytes);
                         const int tg = (c_begin + c) * TC;
                         const uint32_t stage = sX + s * a.xstage_bytes;
+                        constexpr int kBoxes = F8 ? 1 : TC / 64;  // boxes of 64 BF16 or 128 E4M3 samples
 #pragma unroll
-                        for (int sub = 0; sub < TC / 64; ++sub)
+                        for (int sub = 0; sub < kBoxes; ++sub)
                             tma_load_2d(stage + static_cast<uint32_t>(sub) * a.xsub_bytes, &xmap, &full[s],
                                         tg + sub * 64, 0);
                         ++pc;
@@ -246,7 +283,34 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 }
             } else if (warp == 1) {
                 // -------------------------------------------------------------- first products
-                if (lane == 0) {
+                if (F8 && lane == 0) {
+                    // E4M3: D1[128 x 128] = A8 (K-major, n8 entries) . X~8 chunk (MN-major, n8 rows), K = 32
+                    // per MMA: K step ks at byte 32 (ks & 3) of K block ks >> 2 in A, at row 32 ks in B
+                    constexpr uint32_t id1 = idesc_e4m3(128, 128, 1u);
+                    const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
+                    const uint64_t b1_desc = sw128_desc(sX, a.xsub_bytes, 1024u);
+                    const uint32_t stage16 = a.xstage_bytes >> 4;
+                    const int ksteps1 = a.n8 / 32;
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t s = g1c % stages, b = g1c % NB;
+                        bool ok = mbar_wait(&full[s], (g1c / stages) & 1u, abort_flag, a.status, a.wait_ns);
+                        if (ok && g1c >= static_cast<uint32_t>(NB))
+                            ok = mbar_wait(&d1_empty[b], ((g1c - NB) / NB) & 1u, abort_flag, a.status, a.wait_ns);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t d1 = tmem + kD1Col + b * TC;
+                        const uint64_t b1s = b1_desc + static_cast<uint64_t>(s * stage16);
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            if (ks >= ksteps1) break;
+                            const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                            const uint32_t b_off = (static_cast<uint32_t>(ks) * 4096u) >> 4;
+                            umma_e4m3(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
+                        }
+                        umma_commit(&d1_full[b]);
+                        ++g1c;
+                    }
+                } else if (!F8 && lane == 0) {
                     constexpr uint32_t id1 = idesc_bf16(128, TC, 1u);  // B: X~ MN-major
                     const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
                     const uint64_t b1_desc = sw128_desc(sX, a.xsub_bytes, 1024u);
@@ -294,7 +358,31 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 // -------------------------------------------------------------- second products
                 // issuer gi of G2S: K steps j = gi mod G2S into accumulator gi
                 const int gi = warp - kG2Warp;
-                if (lane == 0 && gi < G2S) {
+                if (F8 && lane == 0 && gi == 0) {
+                    // E4M3: D2[128 x n8] += P8 (128 x 128 samples, K-major) . X~8 chunk^T (K-major)
+                    const uint32_t id2 = idesc_e4m3(128, static_cast<uint32_t>(a.n8), 0);
+                    uint64_t pd[4], xd[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        pd[j] = sw128_desc(sP + static_cast<uint32_t>(j) * 32u, 16u, 1024u);
+                        xd[j] = sw128_desc(sX + static_cast<uint32_t>(j) * 32u, 16u, 1024u);
+                    }
+                    const uint32_t stage16 = a.xstage_bytes >> 4;
+                    bool ok = true;
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t b = g2c % NB, s = g2c % stages;
+                        ok = mbar_wait(&p_full[b], (g2c / NB) & 1u, abort_flag, a.status, a.wait_ns);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint64_t po = static_cast<uint64_t>((b * p_bytes) >> 4);
+                        const uint64_t xo = static_cast<uint64_t>(s * stage16);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) umma_e4m3(tmem, pd[j] + po, xd[j] + xo, id2, (c > 0 || j > 0) ? 1u : 0u);
+                        umma_commit(&empty[s]);  // releases the stage and P
+                        ++g2c;
+                    }
+                    if (ok) umma_commit(d2_full);
+                } else if (!F8 && lane == 0 && gi < G2S) {
                     const uint32_t id2 = idesc_bf16(128, static_cast<uint32_t>(a.n_pad), 0);
                     const uint32_t dacc = tmem + static_cast<uint32_t>(gi) * kD2Cols;
                     constexpr int KSI = TC / 16 / G2S;  // K steps of this issuer: gi, gi + G2S, ...
@@ -336,6 +424,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
                 constexpr int CW = TC / 4;  // columns per pass
                 float2 s2 = make_float2(0.f, 0.f), s4 = make_float2(0.f, 0.f);
+                float z2max = 0.f;  // largest z^2 of this thread's entries (trk)
+                // FP8 form: z = D1 2^-c; P = e4m3(v z^3) with the row's scale v = 2^e, the largest
+                // power of two with v (2 zmax)^3 <= 448 (zmax: the row's largest |z| of the previous
+                // iteration; the factor 2 leaves room for the row's change since then)
+                int ev = 0;  // v = 2^ev
+                if constexpr (F8) {
+                    if (m0 + row < M_act) {
+                        const float zm = __ldcg(a.zmax + __ldcg(act + m0 + row));
+                        ev = pow2_fit_exponent(8.f * zm * zm * zm, 448.f);
+                    }
+                }
                 bool ok = true;
                 for (int c = 0; c < nch && ok; ++c) {
                     const uint32_t g = ec + static_cast<uint32_t>(c);
@@ -367,7 +466,34 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             if (lane == 0) mbar_arrive(&d1_empty[b]);
                         }
                         uint32_t pk[CW / 2];
-                        if (mom) {
+                        if constexpr (F8) {
+                            const float dz = __ldg(a.fp8sc + 3 * a.n8), vr = ldexpf(1.f, ev);
+#pragma unroll
+                            for (int i = 0; i < CW; i += 4) {
+                                float2 p[2];
+#pragma unroll
+                                for (int h2 = 0; h2 < 2; ++h2) {
+                                    const float2 z = mul2(make_float2(v[i + 2 * h2], v[i + 2 * h2 + 1]), make_float2(dz, dz));
+                                    const float2 z2 = mul2(z, z);
+                                    s2 = add2(s2, z2);
+                                    s4 = fma2(z2, z2, s4);
+                                    z2max = fmaxf(z2max, fmaxf(z2.x, z2.y));
+                                    p[h2] = mul2(mul2(z2, z), make_float2(vr, vr));
+                                }
+                                pk[i / 4] = pack_e4m3x4(p[0].x, p[0].y, p[1].x, p[1].y);
+                            }
+                        } else if (mom && trk) {
+#pragma unroll
+                            for (int i = 0; i < CW; i += 2) {
+                                const float2 z = make_float2(v[i], v[i + 1]);
+                                const float2 z2 = mul2(z, z);
+                                s2 = add2(s2, z2);
+                                s4 = fma2(z2, z2, s4);
+                                z2max = fmaxf(z2max, fmaxf(z2.x, z2.y));
+                                const float2 z3 = mul2(z2, z);
+                                pk[i / 2] = pack_bf16x2(z3.x, z3.y);
+                            }
+                        } else if (mom) {
 #pragma unroll
                             for (int i = 0; i < CW; i += 2) {
                                 const float2 z = make_float2(v[i], v[i + 1]);
@@ -392,12 +518,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                                             mbar_wait(&empty[cr % stages], (cr / stages) & 1u, abort_flag, a.status, a.wait_ns));
                             if (!ok) break;
                         }
+                        constexpr int kPer16 = F8 ? 16 : 8;  // samples per 16-byte chunk of P
 #pragma unroll
-                        for (int j = 0; j < CW / 8; ++j) {
-                            const int col = col0 + j * 8;  // sample within the chunk
-                            const uint32_t addr = pbase + static_cast<uint32_t>(col >> 6) * 16384u +
-                                                  sw128_off(static_cast<uint32_t>(row),
-                                                            static_cast<uint32_t>((col & 63) >> 3));
+                        for (int j = 0; j < CW / kPer16; ++j) {
+                            const int col = col0 + j * kPer16;  // sample within the chunk
+                            const uint32_t addr =
+                                F8 ? pbase + sw128_off(static_cast<uint32_t>(row), static_cast<uint32_t>(col >> 4))
+                                   : pbase + static_cast<uint32_t>(col >> 6) * 16384u +
+                                         sw128_off(static_cast<uint32_t>(row), static_cast<uint32_t>((col & 63) >> 3));
                             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pk[j * 4 + 0]),
                                          "r"(pk[j * 4 + 1]), "r"(pk[j * 4 + 2]), "r"(pk[j * 4 + 3])
                                          : "memory");
@@ -429,6 +557,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             } else {
                                 tmem_ld_wait();
                             }
+                            if constexpr (F8) {  // undo the scales of P (row) and X~ (column): exact
+                                const float4* isx = reinterpret_cast<const float4*>(a.fp8sc + 2 * a.n8 + col);
+                                const float4 i0 = __ldg(isx), i1 = __ldg(isx + 1);
+                                const float is[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+                                const float inv_vr = ldexpf(1.f, -ev);
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) v8[i] *= inv_vr * is[i];
+                            }
                             if (grow < M_act) {
                                 float4* dst = reinterpret_cast<float4*>(a.part_acc + prow * a.n_pad + col);
                                 dst[0] = make_float4(v8[0], v8[1], v8[2], v8[3]);
@@ -443,21 +579,23 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                     dst[0] = s2.x + s2.y;
                     dst[1] = s4.x + s4.y;
                     dst[2] = 0.f;
+                    dst[3] = z2max;
                 }
                 named_bar_sync(1, 32 * kEpiWarps);
                 if (h == 0 && grow < M_act) {
-                    float m2 = s2.x + s2.y, m4 = s4.x + s4.y, mq = 0.f;
+                    float m2 = s2.x + s2.y, m4 = s4.x + s4.y, mq = 0.f, mx = z2max;
 #pragma unroll
                     for (int hh = 0; hh < kGroups - 1; ++hh) {  // fixed order: groups 1, 2, ...
                         const float* src = mom_sm + (hh * kTcRows + row) * 4;
                         m2 += src[0];
                         m4 += src[1];
                         mq += src[2];
+                        mx = fmaxf(mx, src[3]);
                     }
                     a.part_mom[prow * 4 + 0] = m2;
                     a.part_mom[prow * 4 + 1] = m4;
                     a.part_mom[prow * 4 + 2] = mq;
-                    a.part_mom[prow * 4 + 3] = 0.f;
+                    a.part_mom[prow * 4 + 3] = mx;  // largest z^2 of the partial's samples
                 }
             }
         }
@@ -493,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             mbar_drain(&full[s], (c_last / stages) & 1u, a.status);
         }
     }
-    if ((warp == 1 || warp == kG2Warp || (warp == kG2bWarp && tc_g2_issuers(TC) == 2)) && lane == 0) {
+    if ((warp == 1 || warp == kG2Warp || (warp == kG2bWarp && G2S == 2)) && lane == 0) {
         umma_commit(mma_done);
         mbar_drain(mma_done, 0u, a.status);
     }
@@ -511,17 +649,20 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     }
 }
 
-template <int TC, int NB>
+template <int TC, int NB, bool F8>
 static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p,
                                      int* resident) {
-    const TcLayout L = tc_layout(p.n_pad, false, TC, NB, 1024u);  // + the compaction's static scratch
+    const int n8 = (p.n + 31) / 32 * 32;
+    const TcLayout L = F8 ? tc_layout_e4m3(n8, p.n_pad, 1024u)  // + the compaction's static scratch
+                          : tc_layout(p.n_pad, false, TC, NB, 1024u);
     if (L.stages < static_cast<uint32_t>(NB + 1)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = allow_max_dyn_smem(stage_tc_kernel<TC, NB>);
+    if (F8 && (!p.fp8sc || !p.zmax || n8 > 256)) return cudaErrorInvalidValue;
+    cudaError_t e = allow_max_dyn_smem(stage_tc_kernel<TC, NB, F8>);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_tc_kernel<TC, NB>, kThreads, L.total)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_tc_kernel<TC, NB, F8>, kThreads, L.total)) !=
         cudaSuccess)
         return e;
     if (resident) *resident = per_sm * sms;
@@ -557,6 +698,10 @@ static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, co
     a.proj = RowProj{p.Wp, p.Wp ? p.nw : 0, p.ldw};
     a.lo_from = p.lo_from;
     a.streamk = p.streamk;
+    a.zmax = p.zmax;
+    a.track_until = p.zmax ? p.track_until : 0;
+    a.fp8sc = p.fp8sc;
+    a.n8 = n8;
     a.stages = static_cast<int>(L.stages);
     a.a_bytes = L.a_bytes;
     a.xsub_bytes = L.xsub_bytes;
@@ -574,13 +719,14 @@ static cudaError_t launch_stage_impl(cudaStream_t s, const CUtensorMap& xmap, co
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, stage_tc_kernel<TC, NB>, xmap, a);
+    return cudaLaunchKernelEx(&cfg, stage_tc_kernel<TC, NB, F8>, xmap, a);
 }
 
 cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const StageLaunch& p, int* resident) {
-    if (p.n_pad <= 64) return launch_stage_impl<ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB>(s, xmap, p, resident);
-    if (p.n_pad <= 128) return launch_stage_impl<128, 2>(s, xmap, p, resident);
-    return launch_stage_impl<64, 2>(s, xmap, p, resident);
+    if (p.fp8) return launch_stage_impl<128, 2, true>(s, xmap, p, resident);
+    if (p.n_pad <= 64) return launch_stage_impl<ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB, false>(s, xmap, p, resident);
+    if (p.n_pad <= 128) return launch_stage_impl<128, 2, false>(s, xmap, p, resident);
+    return launch_stage_impl<64, 2, false>(s, xmap, p, resident);
 }
 
 }  // namespace ica

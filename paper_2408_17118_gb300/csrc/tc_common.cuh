@@ -84,6 +84,31 @@ TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, uint32_t reserv
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;
     return L;
 }
+// Layout of the FP8 stage (E4M3 operands, 128-sample chunks): the restart tile as one E4M3 byte per
+// entry (K-major, 128-byte swizzle, K blocks of 128 entries at 16 KB), X~ stages of n8 rows x 128
+// samples (one byte each: the TMA box {128, n8}), two P tiles of 128 x 128 bytes. n8 = the reduced
+// dimension rounded up to 32 (the K of one E4M3 MMA). The restart-tile region doubles as the row
+// completion's scratch, so it is at least 16 warps x (2 n_pad + 4) floats.
+TcLayout tc_layout_e4m3(int n8, int n_pad, uint32_t reserve = 0) {
+    TcLayout L{};
+    uint32_t a = static_cast<uint32_t>((n8 + 127) / 128) * 16384u;
+    const uint32_t fin = (16u * static_cast<uint32_t>(2 * n_pad + 4) * 4u + 1023u) & ~1023u;
+    L.a_bytes = a > fin ? a : fin;
+    L.xsub_bytes = static_cast<uint32_t>(n8) * 128u;
+    L.xstage_bytes = L.xsub_bytes;
+    L.p_bytes = 16384u;
+    const uint32_t fixed = L.a_bytes + 2u * L.p_bytes + kScratchBytes + 1024u;
+    const uint32_t budget = 227u * 1024u - reserve;
+    uint32_t st = (budget - fixed) / L.xstage_bytes;
+    if (st > 8) st = 8;
+    L.stages = st;
+    L.off_x = L.a_bytes;
+    L.off_p = L.off_x + st * L.xstage_bytes;
+    L.off_bar = L.off_p + 2u * L.p_bytes;
+    L.total = L.off_bar + kScratchBytes + 1024u;
+    if (L.total < 120u * 1024u) L.total = 120u * 1024u;
+    return L;
+}
 }  // namespace
 
 
@@ -180,6 +205,43 @@ __device__ __forceinline__ void convert_restart_tile(const float* __restrict__ B
                              : "memory");
             }
         }
+    }
+    fence_proxy_async_smem();
+}
+
+// Restart tile -> E4M3 A operand of the FP8 first product, by the kEpiWarps epilogue warps: entry
+// (m, k) = e4m3(b[r][k] * colscale[k]) (K-major, 128-byte swizzle, K block kb of 128 entries at
+// kb * 16 KB), zero for k >= n and for rows at or beyond M_act; r = act[m0 + m]. k < n8. B32 rows
+// hold ldb = round_up(n, 16) entries, zero from n on (the padding of the reduced dimension).
+__device__ __forceinline__ void convert_restart_tile_e4m3(const float* __restrict__ B32, int ldb, const int* act,
+                                                          int m0, int M_act, int n, int n8, uint32_t sA,
+                                                          const float* __restrict__ colscale) {
+    const int et = threadIdx.x - 64;
+    const int cpr = n8 / 16;  // 16-entry (16-byte) chunks per row
+    for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
+        const int row = idx / cpr, ch = idx % cpr;
+        const int gm = m0 + row;
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        if (gm < M_act && ch * 16 < n) {  // entries n..ldb-1 of a row are zero; ldb is a multiple of 16
+            const int r = __ldcg(act + gm);
+            const float4* src = reinterpret_cast<const float4*>(B32 + static_cast<int64_t>(r) * ldb + ch * 16);
+            const float4* cs = reinterpret_cast<const float4*>(colscale + ch * 16);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 x = __ldcg(src + i), c = __ldg(cs + i);
+                v[4 * i] = x.x * c.x;
+                v[4 * i + 1] = x.y * c.y;
+                v[4 * i + 2] = x.z * c.z;
+                v[4 * i + 3] = x.w * c.w;
+            }
+        }
+        const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pack_e4m3x4(v[0], v[1], v[2], v[3])),
+                     "r"(pack_e4m3x4(v[4], v[5], v[6], v[7])), "r"(pack_e4m3x4(v[8], v[9], v[10], v[11])),
+                     "r"(pack_e4m3x4(v[12], v[13], v[14], v[15]))
+                     : "memory");
     }
     fence_proxy_async_smem();
 }

@@ -11,7 +11,7 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import ICA_BF16, ICA_FP32, ICA_MLP_IN, ICA_MLP_PARAMS, ICA_PLAIN_FP32, ica_dataset, ica_opts  # noqa: F401
+from ._lib import ICA_BF16, ICA_FP8, ICA_FP32, ICA_MLP_IN, ICA_MLP_PARAMS, ICA_PLAIN_FP32, ica_dataset, ica_opts  # noqa: F401
 
 
 class IcaError(RuntimeError):
@@ -215,6 +215,21 @@ def ica_reduce(ctx: Context, G: torch.Tensor, Xw: torch.Tensor, want32: bool = T
     _check(ctx.lib.ica_reduce(ctx.handle, _ptr(G, torch.float64, "G"), n, N, _ptr(Xw, torch.float32, "Xw"), T,
                               _ptr(Xt32), ld, _ptr(Xt16), ld), "ica_reduce")
     return Xt32, Xt16
+
+
+def ica_quantize_e4m3(ctx: Context, Xt32: torch.Tensor, n: int, T: int):
+    """E4M3 copy of the FP32 reduced data (rows 0..n-1 of Xt32, row stride Xt32.shape[1]).
+    Returns (X8 uint8 n8 x ld8 raw E4M3 bytes, scales float32 3 n8 + 1)."""
+    n8 = (n + 31) // 32 * 32
+    ld8 = (T + 15) // 16 * 16
+    o = ica_default_opts()
+    o.precision = ICA_FP8
+    ctx.ensure_workspace(n, T, 1, o)
+    X8 = torch.empty((n8, ld8), dtype=torch.uint8, device=Xt32.device)
+    sc = torch.empty(3 * n8 + 1, dtype=torch.float32, device=Xt32.device)
+    _check(ctx.lib.ica_quantize_e4m3(ctx.handle, _ptr(Xt32, torch.float32, "Xt32"), n, T, Xt32.shape[1], _ptr(X8),
+                                     ld8, _ptr(sc)), "ica_quantize_e4m3")
+    return X8, sc
 
 
 def _xt_args(Xt: torch.Tensor, precision: int):

@@ -70,11 +70,11 @@ def c1_ref():
     return w, B0, ref
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "plain"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8", "plain"])
 def test_c1_parity_explicit_restarts(ctx, c1_ref, prec):
     from paper_2408_17118_gb300 import ica
 
-    p = {"fp32": ica.ICA_FP32, "bf16": ica.ICA_BF16, "plain": ica.ICA_PLAIN_FP32}[prec]
+    p = {"fp32": ica.ICA_FP32, "bf16": ica.ICA_BF16, "fp8": ica.ICA_FP8, "plain": ica.ICA_PLAIN_FP32}[prec]
     w, B0, ref = c1_ref
     W, kurt, Xw, V = gpu_fit(ctx, w, p, B0=B0)
     check_parity(W, kurt, ref, prec)
@@ -184,6 +184,12 @@ def test_wide_stage_parity(ctx, N, T, M, ncomp, seed):
     check_parity(W, kurt, ref, f"N{N} T{T} M{M} bf16")
     W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_FP32, B0=B0)
     check_parity(W, kurt, ref, f"N{N} T{T} M{M} fp32")
+    # FP8 form: iterations 1..3 of each stage on E4M3 operands (n rounded up to 32: the padded K
+    # of the 8-bit products), then BF16 and the FP32 refinement
+    W, kurt, _, _ = gpu_fit(ctx, w, ica.ICA_FP8, B0=B0)
+    st = json.loads(ica.ica_last_stats(ctx))
+    assert st["stage_fp8_launches"] >= ncomp, st
+    check_parity(W, kurt, ref, f"N{N} T{T} M{M} fp8")
 
 
 @pytest.mark.parametrize("case", ["small", "eeg32", "ragged", "wide100", "wide200"])

@@ -91,6 +91,75 @@ def test_deflation_basis(ctx, N, k):
     assert np.abs(W @ G.T).max() < tol
 
 
+def _e4m3_scale_exponent(m):
+    """Largest e with m 2^e <= 448 (m > 0), exactly (powers of two scale exactly)."""
+    if not m > 0:
+        return 0
+    e = int(np.floor(np.log2(448.0 / m)))
+    while np.ldexp(m, e) > 448.0:
+        e -= 1
+    while np.ldexp(m, e + 1) <= 448.0:
+        e += 1
+    return e
+
+
+@pytest.mark.parametrize("n,T", [(5, 1000), (40, 4_099), (130, 3_000), (256, 2_053)])
+def test_quantize_e4m3(ctx, n, T):
+    """The E4M3 operand of the FP8 iterations: every byte equals torch's float32 -> float8_e4m3fn
+    conversion (round to nearest even) of x 2^e_k, e_k the largest exponent with
+    max |x_k| 2^e_k <= 448; padding rows and samples zero; the scale table as documented. Rows
+    of very different magnitudes (2^-20 .. 2^12) and an all-zero row."""
+    from paper_2408_17118_gb300 import ica
+
+    rng = np.random.default_rng(n + T)
+    ld = (T + 7) // 8 * 8
+    X = np.zeros((n, ld), dtype=np.float32)
+    X[:, :T] = rng.standard_t(4, size=(n, T)).astype(np.float32)
+    X[:, :T] *= np.ldexp(1.0, (np.arange(n) % 33) - 20)[:, None].astype(np.float32)
+    X[n // 2, :] = 0.0
+    X8, sc = ica.ica_quantize_e4m3(ctx, torch.from_numpy(X).cuda(), n, T)
+    X8, sc = X8.cpu().numpy(), sc.cpu().numpy()
+    n8 = (n + 31) // 32 * 32
+    assert X8.shape == (n8, (T + 15) // 16 * 16)
+    e = np.array([_e4m3_scale_exponent(float(np.abs(X[k, :T]).max())) for k in range(n)])
+    scaled = (X[:, :T].astype(np.float64) * np.ldexp(1.0, e)[:, None]).astype(np.float32)
+    ref = torch.from_numpy(scaled).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(X8[:n, :T], ref), np.argwhere(X8[:n, :T] != ref)[:5]
+    assert not X8[n:].any() and not X8[:, T:].any()
+    c = 8 + e.min()
+    assert np.array_equal(sc[:n], np.ldexp(1.0, e).astype(np.float32))
+    assert np.array_equal(sc[n8:n8 + n], np.ldexp(1.0, c - e).astype(np.float32))
+    assert np.array_equal(sc[2 * n8:2 * n8 + n], np.ldexp(1.0, -e).astype(np.float32))
+    assert sc[3 * n8] == np.float32(np.ldexp(1.0, -c))
+
+
+@pytest.mark.parametrize("delta", [1e-4, 1e-5])
+def test_deflation_basis_near_singular(ctx, delta):
+    """Found rows that nearly contain e_0 (here F~F~^T has an eigenvalue of about 0.007 delta^2:
+    7e-11 and 7e-13, between the refusal threshold 1e-14 and 1e-10): the GPU basis is accepted
+    and matches the oracle's within the FP64 eigenpair accuracy at that eigenvalue."""
+    from paper_2408_17118_gb300 import ica
+
+    N, k = 64, 30
+    rng = np.random.default_rng(9)
+    w0 = np.zeros(N)
+    w0[0], w0[N - 1] = 1.0, delta
+    w0 /= np.linalg.norm(w0)
+    rest = rng.standard_normal((k - 1, N))
+    rest -= np.outer(rest @ w0, w0)
+    q, _ = np.linalg.qr(rest.T)
+    W = np.ascontiguousarray(np.vstack([w0, q.T[: k - 1]]))
+    G = ica.ica_deflation_basis(ctx, torch.from_numpy(W).cuda(), N).cpu().numpy()
+    ref = oracle.deflation_basis(W, N)
+    Ft = (np.eye(N) - W.T @ W)[: N - k]
+    lam_min = np.linalg.eigvalsh(Ft @ Ft.T).min()
+    assert 1e-14 < lam_min < 1e-10
+    tol = 100 * np.finfo(np.float64).eps / lam_min
+    assert np.abs(G @ G.T - np.eye(N - k)).max() < tol
+    assert np.abs(W @ G.T).max() < 100 * np.finfo(np.float64).eps / np.sqrt(lam_min)
+    assert np.abs(G - ref).max() < tol
+
+
 @pytest.mark.parametrize("N,k", [(64, 24), (64, 40), (40, 20)])
 def test_deflation_basis_repeated_eigenvalues(ctx, N, k):
     # W = Q W0 with W0 rows cos(th) e_a + sin(th) e_b (a among the first n coordinates, b among

@@ -124,6 +124,41 @@ def test_deflation_basis_invariants(N, k):
     assert np.abs(R @ R - Ft @ Ft.T).max() < 1e-10
 
 
+@pytest.mark.parametrize("delta", [1e-5, 1e-6])
+def test_deflation_basis_near_singular(delta):
+    """Eq. 7 with found rows that nearly contain e_0 (a unit vector of the first n coordinates):
+    w_0 = (e_0 + delta e_{N-1}) / norm, so F~F~^T has an eigenvalue of at most about delta^2
+    (1e-10, 1e-12). The basis is still accepted and correct to the accuracy FP64 eigenpairs allow: length
+    along the bad eigenvector within about eps / delta^2, direction within eps / delta."""
+    N, k = 12, 3
+    rng = np.random.default_rng(5)
+    w0 = np.zeros(N)
+    w0[0], w0[N - 1] = 1.0, delta
+    w0 /= np.linalg.norm(w0)
+    rest = rng.standard_normal((k - 1, N))
+    rest -= np.outer(rest @ w0, w0)
+    q, _ = np.linalg.qr(rest.T)
+    W = np.vstack([w0, q.T[: k - 1]])
+    assert np.abs(W @ W.T - np.eye(k)).max() < 1e-14
+    n = N - k
+    Ft = (np.eye(N) - W.T @ W)[:n]
+    lam = np.linalg.eigvalsh(Ft @ Ft.T)
+    assert 0.0 < lam.min() <= 1.01 * delta * delta
+    G = oracle.deflation_basis(W, N)
+    eps = np.finfo(np.float64).eps
+    assert np.abs(G @ G.T - np.eye(n)).max() < 100 * eps / lam.min()
+    assert np.abs(W @ G.T).max() < 100 * eps / np.sqrt(lam.min())
+
+
+def test_deflation_basis_refuses_singular():
+    """An exactly singular F~F~^T (a found row equal to e_0) is refused."""
+    N = 6
+    W = np.zeros((1, N))
+    W[0, 0] = 1.0
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.deflation_basis(W, N)
+
+
 # ------------------------------------------------------------------ Section 3.1 matrix update
 def test_matrix_update_is_kurtosis_gradient():
     """B' + 3B must equal the gradient of J(b) = mean((b X~)^4)/4, checked row by row by
