@@ -46,10 +46,12 @@ METRIC = "time-to-all-components & TFLOP/s, BF16 fused+pruned vs plain FP32, sam
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # restarts of the bounded oracle sample (whitening + component 1 at full T) per workload
 ORACLE_RESTARTS = {"small": 64, "eeg64": 256, "eeg128": 64, "eeg256": 16, "eeg128_small": 64, "eeg256_small": 32}
-# ncu DRAM bytes (read + write) of one persistent stage launch divided by its algorithmic X~
-# bytes (n_pad T 2, one pass), per workload, from the capture of the current kernel
-# (profiles/); None where no capture of the current kernel exists
-STAGE_TRAFFIC_RATIO = {}
+# ncu DRAM bytes (read + write) of one persistent stage launch divided by its iterations x its
+# X~ bytes (n_pad T 2, one pass per iteration), per workload, from the captures of the current
+# kernel (profiles/stage_tc_kernel_eeg256_small.md: 19.32 GB / (30 x 204.8 MB) with the equal
+# work shares, X~ larger than L2; profiles/stage_tc_kernel_eeg128_small.md: 3.78 GB /
+# (30 x 102.4 MB), X~ within L2); absent where no capture of the current kernel exists
+STAGE_TRAFFIC_RATIO = {"eeg256": 3.145, "eeg256_small": 3.145, "eeg128": 1.231, "eeg128_small": 1.231}
 
 
 def parse_args():
@@ -69,6 +71,12 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prune", action="store_true", help="headline without the learned pruner")
+    ap.add_argument("--precision", choices=["bf16", "fp8"], default="bf16",
+                    help="precision of the headline fit (fp8: ICA_FP8, iterations 1..3 of each stage on E4M3 operands)")
+    ap.add_argument("--stage-streamk", type=int, default=-1, choices=[-1, 0, 1],
+                    help="persistent stage's equal work shares: 1 on, 0 off (default: the library's)")
+    ap.add_argument("--stage-lo-from", type=int, default=-1, metavar="T",
+                    help="first stage iteration that adds the restart rows' low BF16 term (default: the library's)")
     ap.add_argument("--side-steps", type=int, default=2, help="timed steps of the unpruned and e2e legs")
     ap.add_argument("--prune-recall", type=float, default=0.999,
                     help="recall of the training positives that sets the pruner's keep threshold")
@@ -382,7 +390,12 @@ def run_ours(args):
         log(f"pruner trained: {train_report}")
     # headline: BF16 (+ pruner); profile = 1 records CUDA events around each stage launch on the
     # library's stream inside the timed steps (the roofline's kernel time)
-    opts_head = ica.ica_default_opts(precision=ica.ICA_BF16, profile=1)
+    head_prec = ica.ICA_FP8 if args.precision == "fp8" else ica.ICA_BF16
+    opts_head = ica.ica_default_opts(precision=head_prec, profile=1)
+    if args.stage_lo_from >= 0:
+        opts_head.stage_lo_from = args.stage_lo_from
+    if args.stage_streamk >= 0:
+        opts_head.stage_streamk = args.stage_streamk
     tau_trained = tau
     if prune:
         if args.prune_tau >= 0:
@@ -610,12 +623,14 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "e4m3+bf16",
             "data": "synthetic (seeded generators, synth/; stands in for the paper's EEG recordings)",
             "config": {"workload": workload_desc(w), "components_fitted": K,
-                       "precision": "bf16 tcgen05 + fp32 refinement",
+                       "precision": ("bf16 tcgen05 + fp32 refinement" if args.precision == "bf16" else
+                                     "e4m3 tcgen05 (stage iterations 1-3) + bf16 tcgen05 + fp32 refinement"),
                        "pruner": (f"on: keep floor {opts_head.prune_keep_frac:g} + redundancy |cos| >= "
-                                  f"{args.prune_cos:g}, network threshold {tau:g} (trained untimed; see "
+                                  f"{args.prune_cos:g} + Gaussian-subspace rule (Eq. 3 at iteration 5), "
+                                  f"network threshold {tau:g} (trained untimed; see "
                                   f"pruner_network_leg for its trained threshold)") if prune else "off",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},

@@ -25,6 +25,9 @@ Readings where the paper is silent or self-contradictory:
 * initial restarts: i.i.d. N(0,1) entries from Philox4x32-10 and Box-Muller (see
   ``philox4x32_10`` and ``restart_normals``), or an explicit B0 passed in.
 * Upsilon(alpha) = +inf when alpha <= -2 (the log argument leaves its domain there).
+* the deflation basis keeps the first n rows of F (Eq. 7) and is refused only when
+  F~ F~^T has an eigenvalue <= 1e-14 (eigenvalues of 1e-11 occur in generic data where the
+  found components and the kept coordinates have about equal dimension).
 
 Parity status: every function here is pinned by tests in ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force on N=2, known-answer vectors); none is unpinned.
