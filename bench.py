@@ -73,6 +73,8 @@ def parse_args():
     ap.add_argument("--no-prune", action="store_true", help="headline without the learned pruner")
     ap.add_argument("--precision", choices=["bf16", "fp8"], default="bf16",
                     help="precision of the headline fit (fp8: ICA_FP8, iterations 1..3 of each stage on E4M3 operands)")
+    ap.add_argument("--fp8-iters", type=int, default=-1, metavar="K",
+                    help="FP8 form: stage iterations 1..K on E4M3 operands (default: the library's)")
     ap.add_argument("--stage-streamk", type=int, default=-1, choices=[-1, 0, 1],
                     help="persistent stage's equal work shares: 1 on, 0 off (default: the library's)")
     ap.add_argument("--stage-lo-from", type=int, default=-1, metavar="T",
@@ -396,6 +398,8 @@ def run_ours(args):
         opts_head.stage_lo_from = args.stage_lo_from
     if args.stage_streamk >= 0:
         opts_head.stage_streamk = args.stage_streamk
+    if args.fp8_iters >= 0:
+        opts_head.fp8_iters = args.fp8_iters
     tau_trained = tau
     if prune:
         if args.prune_tau >= 0:
@@ -502,6 +506,8 @@ def run_ours(args):
     fp8 = None
     if not args.no_fp8_leg:
         opts_8 = ica.ica_default_opts(precision=ica.ICA_FP8, profile=1)
+        if args.fp8_iters >= 0:
+            opts_8.fp8_iters = args.fp8_iters
         if prune:
             opts_8.prune_tau = tau
             opts_8.prune_cos = args.prune_cos

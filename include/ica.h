@@ -143,7 +143,8 @@ typedef struct {
     int stage_lo_from;     /* BF16 stage: iterations t >= stage_lo_from (0-based) feed the restart
                               rows to the first product as two BF16 terms (hi + lo, about 16
                               bits: rows can converge to stage_tol); earlier ones as one BF16
-                              term, which is enough far from convergence (default 3) */
+                              term, which is enough far from convergence (default 5: the
+                              iterations before the restart pruner's decision) */
     int stage_streamk;     /* persistent BF16 stage: 1 (default) - when the one-wave shape (restart
                               tiles x sample splits) would leave more than a sixteenth of the SMs
                               idle, every CTA takes an equal share of the (tile x chunk) work
@@ -163,7 +164,7 @@ typedef struct {
 /* Default options: BF16, no Gaussianity test, refine_topk 4, refine_iters 10,
    stage_tol 1e-4, refine_tol 1e-6, fp32_tol_floor 1e-6, B0 NULL, automatic splits,
    no profiling, no pruner (prune_tau 0.05, prune_keep_frac 0.05, prune_cos 0.99), no
-   recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 3,
+   recording, persistent stage, 2 s wait limit, no stall, algorithm 2, stage_lo_from 5,
    prune_gauss 1, stage_streamk 1, fp8_iters 3. */
 void ica_default_opts(ica_opts* opts);
 

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -280,6 +281,18 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float x0, float x1, float x2, fl
         : "=r"(out)
         : "f"(x0), "f"(x1), "f"(x2), "f"(x3));
     return out;
+}
+// The two E4M3 values of the low and high bytes of a 16-bit pair, widened exactly to float (every
+// E4M3 value is an FP16 value).
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t pair16) {
+    uint32_t h2;
+    asm("{\n\t.reg .b16 p;\n\t"
+        "cvt.u16.u32 p, %1;\n\t"
+        "cvt.rn.f16x2.e4m3x2 %0, p;\n\t}"
+        : "=r"(h2)
+        : "r"(pair16));
+    const __half2 hv = *reinterpret_cast<const __half2*>(&h2);
+    return __half22float2(hv);
 }
 // Largest e with m * 2^e <= lim (m > 0 finite, lim > 0): the exponent of a power-of-two scale that
 // maps magnitudes up to m into [-lim, lim]. ldexpf is exact, so the result is exact.

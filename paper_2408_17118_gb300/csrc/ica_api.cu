@@ -475,7 +475,7 @@ void ica_default_opts(ica_opts* o) {
     o->prune_keep_frac = 0.05f;
     o->prune_cos = 0.99f;
     o->algorithm = 2;
-    o->stage_lo_from = 3;
+    o->stage_lo_from = 5;
     o->prune_gauss = 1;
     o->stage_streamk = 1;
     o->fp8_iters = 3;

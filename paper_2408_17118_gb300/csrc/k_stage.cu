@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                                  : static_cast<int64_t>(bid % sp) * part_rows + m0;
         if (warp >= 2 && warp < 2 + kEpiWarps) {
             if constexpr (F8) {  // restart tile -> E4M3, column k scaled by 2^(c - e_k)
-                convert_restart_tile_e4m3(a.B32, a.ldb, act, m0, M_act, a.n, a.n8, sA, a.fp8sc + a.n8);
+                convert_restart_tile_e4m3(a.B32, a.ldb, act, m0, M_act, a.n, a.n8, sA, a.a_bytes >> 1, a.fp8sc + a.n8);
             } else {  // restart tile -> BF16 hi (shared memory) and lo (beside it, or in tensor memory)
                 convert_restart_tile<tc_split_b(TC), tc_lo_in_tmem(TC)>(a.B32, a.ldb, act, m0, M_act, a.n_pad, sA,
                                                                         a.a_bytes, tmem + kALoCol, true, use_lo);
@@ -284,8 +284,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             } else if (warp == 1) {
                 // -------------------------------------------------------------- first products
                 if (F8 && lane == 0) {
-                    // E4M3: D1[128 x 128] = A8 (K-major, n8 entries) . X~8 chunk (MN-major, n8 rows), K = 32
-                    // per MMA: K step ks at byte 32 (ks & 3) of K block ks >> 2 in A, at row 32 ks in B
+                    // E4M3: D1[128 x 128] = (A8 hi + A8 lo) (K-major, n8 entries) . X~8 chunk (MN-major, n8
+                    // rows), K = 32 per MMA: K step ks at byte 32 (ks & 3) of K block ks >> 2 in A, at row
+                    // 32 ks in B; the lo term's MMAs accumulate after the hi term's
                     constexpr uint32_t id1 = idesc_e4m3(128, 128, 1u);
                     const uint64_t a1_desc = sw128_desc(sA, 16u, 1024u);
                     const uint64_t b1_desc = sw128_desc(sX, a.xsub_bytes, 1024u);
@@ -306,6 +307,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
                             const uint32_t b_off = (static_cast<uint32_t>(ks) * 4096u) >> 4;
                             umma_e4m3(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
+                        }
+                        const uint64_t a1_lo = a1_desc + static_cast<uint64_t>((a.a_bytes >> 1) >> 4);
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            if (ks >= ksteps1) break;
+                            const uint32_t a_off = ((ks >> 2) * 16384u + (ks & 3) * 32u) >> 4;
+                            const uint32_t b_off = (static_cast<uint32_t>(ks) * 4096u) >> 4;
+                            umma_e4m3(d1, a1_lo + a_off, b1s + b_off, id1, 1u);
                         }
                         umma_commit(&d1_full[b]);
                         ++g1c;

@@ -84,15 +84,16 @@ TcLayout tc_layout(int n_pad, bool moments_only, int TC, int NB, uint32_t reserv
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;
     return L;
 }
-// Layout of the FP8 stage (E4M3 operands, 128-sample chunks): the restart tile as one E4M3 byte per
-// entry (K-major, 128-byte swizzle, K blocks of 128 entries at 16 KB), X~ stages of n8 rows x 128
+// Layout of the FP8 stage (E4M3 operands, 128-sample chunks): the restart tile as two E4M3 terms
+// (hi, then lo in the second half of the region; each K-major, 128-byte swizzle, K blocks of 128
+// entries at 16 KB), X~ stages of n8 rows x 128
 // samples (one byte each: the TMA box {128, n8}), two P tiles of 128 x 128 bytes. n8 = the reduced
 // dimension rounded up to 32 (the K of one E4M3 MMA). The restart-tile region doubles as the row
 // completion's scratch, so it is at least 16 warps x (2 n_pad + 4) floats.
 TcLayout tc_layout_e4m3(int n8, int n_pad, uint32_t reserve = 0) {
     TcLayout L{};
-    uint32_t a = static_cast<uint32_t>((n8 + 127) / 128) * 16384u;
-    const uint32_t fin = (16u * static_cast<uint32_t>(2 * n_pad + 4) * 4u + 1023u) & ~1023u;
+    uint32_t a = 2u * static_cast<uint32_t>((n8 + 127) / 128) * 16384u;
+    const uint32_t fin = (16u * static_cast<uint32_t>(2 * n_pad + 4) * 4u + 2047u) & ~2047u;  // halves 1 KB aligned
     L.a_bytes = a > fin ? a : fin;
     L.xsub_bytes = static_cast<uint32_t>(n8) * 128u;
     L.xstage_bytes = L.xsub_bytes;
@@ -209,13 +210,15 @@ __device__ __forceinline__ void convert_restart_tile(const float* __restrict__ B
     fence_proxy_async_smem();
 }
 
-// Restart tile -> E4M3 A operand of the FP8 first product, by the kEpiWarps epilogue warps: entry
-// (m, k) = e4m3(b[r][k] * colscale[k]) (K-major, 128-byte swizzle, K block kb of 128 entries at
-// kb * 16 KB), zero for k >= n and for rows at or beyond M_act; r = act[m0 + m]. k < n8. B32 rows
-// hold ldb = round_up(n, 16) entries, zero from n on (the padding of the reduced dimension).
+// Restart tile -> E4M3 A operands of the FP8 first product, by the kEpiWarps epilogue warps: with
+// x = b[r][k] * colscale[k], hi = e4m3(x) and lo = e4m3(x - hi) (together about 8 significant
+// bits, where one E4M3 term carries 4), each K-major with 128-byte swizzle, K block kb of 128
+// entries at kb * 16 KB; lo at byte offset lo_off. Zero for k >= n and for rows at or beyond
+// M_act; r = act[m0 + m]; k < n8. B32 rows hold ldb = round_up(n, 16) entries, zero from n on (the
+// padding of the reduced dimension). |x| <= 256, so neither term saturates.
 __device__ __forceinline__ void convert_restart_tile_e4m3(const float* __restrict__ B32, int ldb, const int* act,
                                                           int m0, int M_act, int n, int n8, uint32_t sA,
-                                                          const float* __restrict__ colscale) {
+                                                          uint32_t lo_off, const float* __restrict__ colscale) {
     const int et = threadIdx.x - 64;
     const int cpr = n8 / 16;  // 16-entry (16-byte) chunks per row
     for (int idx = et; idx < kTcRows * cpr; idx += 32 * kEpiWarps) {
@@ -237,10 +240,19 @@ __device__ __forceinline__ void convert_restart_tile_e4m3(const float* __restric
                 v[4 * i + 3] = x.w * c.w;
             }
         }
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            hw[i] = pack_e4m3x4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            const float2 h01 = e4m3x2_to_float2(hw[i] & 0xffffu), h23 = e4m3x2_to_float2(hw[i] >> 16);
+            lw[i] = pack_e4m3x4(v[4 * i] - h01.x, v[4 * i + 1] - h01.y, v[4 * i + 2] - h23.x, v[4 * i + 3] - h23.y);
+        }
         const uint32_t addr = sA + static_cast<uint32_t>(ch >> 3) * 16384u + sw128_off(row, ch & 7);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pack_e4m3x4(v[0], v[1], v[2], v[3])),
-                     "r"(pack_e4m3x4(v[4], v[5], v[6], v[7])), "r"(pack_e4m3x4(v[8], v[9], v[10], v[11])),
-                     "r"(pack_e4m3x4(v[12], v[13], v[14], v[15]))
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(hw[0]), "r"(hw[1]), "r"(hw[2]),
+                     "r"(hw[3])
+                     : "memory");
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + lo_off), "r"(lw[0]), "r"(lw[1]),
+                     "r"(lw[2]), "r"(lw[3])
                      : "memory");
     }
     fence_proxy_async_smem();
