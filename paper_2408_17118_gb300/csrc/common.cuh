@@ -160,6 +160,16 @@ __device__ __forceinline__ void umma_bf16_tmem_a_acc(uint32_t d_tmem, uint32_t a
         "r"(a_tmem), "l"(b_desc), "r"(idesc)
         : "memory");
 }
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::f16 (as umma_bf16_tmem_a_acc, accumulate chosen).
+__device__ __forceinline__ void umma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // 32 lanes x 32 bit, 8 consecutive columns per thread, registers -> tensor memory.
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),

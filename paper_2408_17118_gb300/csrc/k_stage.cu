@@ -148,6 +148,14 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     uint8_t* base = smem_raw + (base_u32 - raw_u32);
     constexpr uint32_t p_bytes = F8 ? 16384u : static_cast<uint32_t>(TC / 64) * 16384u;
     constexpr int G2S = F8 ? 1 : tc_g2_issuers(TC);
+    // Split first product (64-sample chunks, one Z buffer): the high term's MMAs (warp 1) and the
+    // low term's (warp kG2bWarp, idle as a second-product issuer at this width) go to two Z
+    // accumulators from two threads, summed when the epilogue reads them. One thread issues an
+    // N = 64 MMA only every 67-84 cycles, so the first product, 2 n_pad / 16 MMAs per chunk,
+    // was the limit; TMEM then holds D2, Z_hi, Z_lo and B's low term (256 + 64 + 64 + 128).
+    constexpr bool kSplit = !F8 && TC == 64 && NB == 1;
+    static_assert(!kSplit || tc_lo_in_tmem(TC), "the split form reads B's low term from tensor memory");
+    constexpr int kTeams = kSplit ? 1 : 2;  // epilogue teams taking alternate chunks
     const uint32_t stages = static_cast<uint32_t>(a.stages);
     const uint32_t sA = base_u32, sX = base_u32 + a.off_x, sP = base_u32 + a.off_p;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + a.off_bar);
@@ -172,12 +180,12 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             mbar_init(&empty[s], G2S);  // a commit of every second-product issuer
         }
         for (int b = 0; b < NB; ++b) {
-            mbar_init(&d1_full[b], 1);
-            mbar_init(&d1_empty[b], kEpiWarps / 2);  // one epilogue team per buffer
-            mbar_init(&p_full[b], kEpiWarps / 2);
+            mbar_init(&d1_full[b], kSplit ? 2 : 1);      // a commit of every first-product issuer
+            mbar_init(&d1_empty[b], kEpiWarps / kTeams);  // the epilogue team of the buffer
+            mbar_init(&p_full[b], kEpiWarps / kTeams);
         }
         mbar_init(d2_full, G2S);
-        mbar_init(mma_done, 1 + G2S);  // one commit per MMA-issuing thread
+        mbar_init(mma_done, 1 + G2S + (kSplit ? 1 : 0));  // one commit per MMA-issuing thread
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -192,14 +200,16 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
     const uint32_t tmem = *tmem_slot;
     constexpr uint32_t kD2Cols = F8 ? 256u : tc_d2_cols(TC);
     constexpr uint32_t kD1Col = G2S * kD2Cols;  // Z buffers after the G2S accumulators
-    static_assert(kD1Col + NB * TC <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
-    constexpr uint32_t kALoCol = tc_alo_col(TC, NB);  // B's low term (tc_lo_in_tmem): n_pad / 2 columns
+    constexpr uint32_t kZCols = kSplit ? 2u * TC : static_cast<uint32_t>(NB * TC);  // Z (split: Z_hi, Z_lo)
+    static_assert(kD1Col + kZCols <= 512, "D2 and the Z buffers must fit in 512 TMEM columns");
+    constexpr uint32_t kALoCol = kSplit ? kD1Col + kZCols : tc_alo_col(TC, NB);  // B's low term: n_pad / 2 columns
     static_assert(F8 || !tc_lo_in_tmem(TC) || kALoCol + (TC == 128 ? 64u : 128u) <= 512, "B's low term must fit TMEM");
-    static_assert(NB >= 2 && NB <= 3, "barrier slots exist for up to three Z / P buffers");
+    static_assert((kSplit ? NB == 1 : NB >= 2) && NB <= 3, "barrier slots exist for up to three Z / P buffers");
 
     // running counts of each role (mbarrier phases continue across the updates)
     uint32_t pc = 0;   // producer: chunks issued
     uint32_t g1c = 0;  // first-product issuer: chunks consumed
+    uint32_t g1l = 0;  // low-term first-product issuer (split form): chunks consumed
     uint32_t g2c = 0;  // second-product issuer: chunks consumed
     uint32_t ec = 0;   // epilogue: chunks consumed
     uint32_t d2n = 0;  // updates this CTA took part in
@@ -257,9 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             }
             tc_fence_before();
         }
-        // The restart tile is complete for the first-product issuer (warp 1) once the epilogue
-        // warps pass this barrier; the TMA producer starts loading X~ without waiting for it.
-        if (warp >= 1 && warp < 2 + kEpiWarps) named_bar_sync(10, 32 * (1 + kEpiWarps));
+        // The restart tile is complete for the first-product issuers (warp 1, and warp kG2bWarp
+        // for the low term in the split form) once the epilogue warps pass this barrier; the TMA
+        // producer starts loading X~ without waiting for it.
+        if ((warp >= 1 && warp < 2 + kEpiWarps) || (kSplit && warp == kG2bWarp))
+            named_bar_sync(10, 32 * (1 + kEpiWarps + (kSplit ? 1 : 0)));
 
         {
             if (warp == 0) {
@@ -341,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                             const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
                             umma_bf16(d1, a1_desc + a_off, b1s + b_off, id1, ks > 0 ? 1u : 0u);
                         }
-                        if (!use_lo) {
+                        if (!use_lo || kSplit) {  // split form: the low term's MMAs come from warp kG2bWarp
                         } else if constexpr (tc_lo_in_tmem(TC)) {
 #pragma unroll
                             for (int ks = 0; ks < 16; ++ks) {
@@ -361,6 +373,38 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                         }
                         umma_commit(&d1_full[b]);
                         ++g1c;
+                    }
+                }
+            } else if (kSplit && warp == kG2bWarp) {
+                // -------------------------------------------------------------- first products, low term
+                // Z_lo = B_lo X~ chunk (B_lo from tensor memory), for iterations that use it; other
+                // iterations only arrive, so that the epilogue reads Z_hi alone
+                if (lane == 0) {
+                    constexpr uint32_t id1 = idesc_bf16(128, TC, 1u);
+                    const uint64_t b1_desc = sw128_desc(sX, a.xsub_bytes, 1024u);
+                    const uint32_t stage16 = a.xstage_bytes >> 4;
+                    const int ksteps1 = a.n_pad / 16;
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t s = g1l % stages;
+                        bool ok = mbar_wait(&full[s], (g1l / stages) & 1u, abort_flag, a.status, a.wait_ns);
+                        if (ok && g1l >= 1u) ok = mbar_wait(&d1_empty[0], (g1l - 1u) & 1u, abort_flag, a.status, a.wait_ns);
+                        if (!ok) break;
+                        if (use_lo) {
+                            tc_fence_after();
+                            const uint32_t dlo = tmem + kD1Col + TC;
+                            const uint64_t b1s = b1_desc + static_cast<uint64_t>(s * stage16);
+#pragma unroll
+                            for (int ks = 0; ks < 16; ++ks) {
+                                if (ks >= ksteps1) break;
+                                const uint32_t b_off = (static_cast<uint32_t>(ks) * 2048u) >> 4;
+                                umma_bf16_tmem_a(dlo, tmem + kALoCol + static_cast<uint32_t>(ks) * 8u, b1s + b_off, id1,
+                                                 ks > 0 ? 1u : 0u);
+                            }
+                            umma_commit(&d1_full[0]);
+                        } else {
+                            mbar_arrive(&d1_full[0]);
+                        }
+                        ++g1l;
                     }
                 }
             } else if (warp == kG2Warp || warp == kG2bWarp) {
@@ -424,8 +468,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 // Two teams of 8 warps take alternate chunks (team k: chunks g = k mod 2, Z / P
                 // buffer k), so that one team's TMEM-load and barrier latency overlaps the other
                 // team's cube conversion. In a team, warp (lane quarter q, half hh) converts rows
-                // 32q.. of columns [hh TC/2, (hh+1) TC/2) in two passes of TC/4 columns.
-                static_assert(NB == 2, "one Z / P buffer per epilogue team");
+                // 32q.. of columns [hh TC/2, (hh+1) TC/2) in two passes of TC/4 columns. The split
+                // form has one Z / P buffer and one team of 16 warps: warp (q, h) converts columns
+                // [h TC/4, (h+1) TC/4) of every chunk, Z_hi + Z_lo, in one pass.
+                static_assert(kSplit || NB == 2, "one Z / P buffer per epilogue team");
+                constexpr int kPasses = kSplit ? 1 : 2;
                 const int q = warp & 3;
                 const int h = (warp - 2) >> 2;  // moment group 0..3 = 2 team + hh
                 const int team = h >> 1, hh = h & 1;
@@ -447,15 +494,15 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                 bool ok = true;
                 for (int c = 0; c < nch && ok; ++c) {
                     const uint32_t g = ec + static_cast<uint32_t>(c);
-                    if (static_cast<int>(g & 1u) != team) continue;
+                    if (kTeams == 2 && static_cast<int>(g & 1u) != team) continue;
                     const uint32_t b = g % NB;
                     ok = __all_sync(0xffffffffu, mbar_wait(&d1_full[b], (g / NB) & 1u, abort_flag, a.status, a.wait_ns));
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t pbase = sP + b * p_bytes;
 #pragma unroll 1
-                    for (int pass = 0; pass < 2; ++pass) {
-                        const int col0 = hh * (TC / 2) + pass * CW;  // first sample of this pass
+                    for (int pass = 0; pass < kPasses; ++pass) {
+                        const int col0 = kSplit ? h * CW : hh * (TC / 2) + pass * CW;  // first sample of this pass
                         float v[CW];
                         const uint32_t d1 = tmem + kD1Col + b * TC + lane_off + static_cast<uint32_t>(col0);
                         constexpr int N64 = CW / 64, N32 = (CW % 64) / 32, N16 = (CW % 32) / 16;
@@ -468,8 +515,18 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
                                       *reinterpret_cast<float(*)[32]>(&v[64 * N64]));
                         if constexpr (N16 == 1)
                             tmem_ld16(d1 + static_cast<uint32_t>(CW - 16), *reinterpret_cast<float(*)[16]>(&v[CW - 16]));
+                        if constexpr (kSplit) {  // + the low term's accumulator
+                            static_assert(CW == 16, "split form: 16 columns per warp");
+                            if (use_lo) {
+                                float w[16];
+                                tmem_ld16(d1 + static_cast<uint32_t>(TC), w);
+                                tmem_ld_wait();
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) v[i] += w[i];
+                            }
+                        }
                         tmem_ld_wait();
-                        if (pass == 1) {  // the team has read all of Z(g)
+                        if (pass == kPasses - 1) {  // the team has read all of Z(g)
                             tc_fence_before();
                             __syncwarp();
                             if (lane == 0) mbar_arrive(&d1_empty[b]);
@@ -640,7 +697,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_tc_kernel(const __grid_cons
             mbar_drain(&full[s], (c_last / stages) & 1u, a.status);
         }
     }
-    if ((warp == 1 || warp == kG2Warp || (warp == kG2bWarp && G2S == 2)) && lane == 0) {
+    if ((warp == 1 || warp == kG2Warp || (warp == kG2bWarp && (G2S == 2 || kSplit))) && lane == 0) {
         umma_commit(mma_done);
         mbar_drain(mma_done, 0u, a.status);
     }
@@ -735,7 +792,7 @@ cudaError_t launch_stage_tc(cudaStream_t s, const CUtensorMap& xmap, const Stage
     if (p.fp8) return launch_stage_impl<128, 2, true>(s, xmap, p, resident);
     if (p.n_pad <= 64) return launch_stage_impl<ICA_TC_SMALL_CHUNK, ICA_TC_SMALL_NB, false>(s, xmap, p, resident);
     if (p.n_pad <= 128) return launch_stage_impl<128, 2, false>(s, xmap, p, resident);
-    return launch_stage_impl<64, 2, false>(s, xmap, p, resident);
+    return launch_stage_impl<64, 1, false>(s, xmap, p, resident);  // the split first product
 }
 
 }  // namespace ica
