@@ -15,9 +15,13 @@ dimensions (two products of n x T per restart; the rows actually updated, counte
 device), 2 n M T per kurtosis pass, summed over the fit. `nominal_tflops` uses the fixed
 4 N M T per iteration instead.
 
-The pruner (a 13-64-64-1 network, not part of the paper) is trained untimed, by the library's
+The pruner (not part of the paper) combines a 13-64-64-1 network with a keep floor, a
+redundancy rule and a Gaussian-subspace rule. The network is trained untimed, by the library's
 own kernels, on restart trajectories the method records on workloads shaped like the small
-N = 8 mixture and the EEG-like N = 64 and N = 128 cases (other seeds than the timed data).
+N = 8 mixture, the EEG-like N = 64 and N = 128 cases, and N = 256 at reduced T and M (other
+seeds than the timed data). Beside the headline the bench reports the unpruned fit (the
+pruner's judge), the network's trained threshold, the FP8 form (stage iterations 1..3 on E4M3
+operands), e2e through the public API with host buffers, and the plain FP32 matrix form.
 
 Multi-GPU (torchrun): every rank fits its own data set (weak scaling, replicas: the fit has
 no exchange step); value = all ranks' FLOPs / the slowest rank's time.
