@@ -18,8 +18,11 @@
 //                is active or the iteration limit is reached.
 //
 // The arithmetic of every step is that of the per-launch path (fused_tc_kernel + finalize_kernel),
-// so both give identical results; the persistent form removes two launches per iteration, the
-// TMEM allocation and barrier set-up of each update, and the host's reads of the active count.
+// so both give identical results, with two exceptions that change only the FP32 rounding: the
+// equal work shares (opts.stage_streamk) and, at 64-sample chunks, the split first product (the
+// restart rows' two BF16 terms accumulated apart and added in the epilogue). The persistent form
+// removes two launches per iteration, the TMEM allocation and barrier set-up of each update, and
+// the host's reads of the active count.
 //
 // Data written by other CTAs inside the launch (restart rows, partials, flags, the active list)
 // is read with cache-global loads (L1 is not coherent across SMs). Every wait is bounded
