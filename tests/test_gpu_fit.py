@@ -289,7 +289,7 @@ def test_gaussianity_count_sweep(ctx, L):
             check_parity(W, kurt, ref, f"L{L} run{run}")
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 @pytest.mark.parametrize("case", ["small", "ragged"])
 def test_algorithm1_parity(ctx, prec, case):
     """Algorithm 1's form on the GPU (opts.algorithm = 1: every iteration on the full whitened
@@ -297,7 +297,7 @@ def test_algorithm1_parity(ctx, prec, case):
     restarts) against the FP64 oracle's Algorithm 1 from the same initial vectors."""
     from paper_2408_17118_gb300 import ica
 
-    p = ica.ICA_FP32 if prec == "fp32" else ica.ICA_BF16
+    p = {"fp32": ica.ICA_FP32, "bf16": ica.ICA_BF16, "fp8": ica.ICA_FP8}[prec]
     if case == "small":
         w = synth.small_mixture(0)
         iters, tol = w.iters, w.tol
