@@ -92,3 +92,35 @@ def test_batched_errors(ica, batch):
     lib.ica_set_workspace(ctx.handle, C.c_void_p(small.data_ptr()), small.numel())
     assert lib.ica_order_fit_batched(ctx.handle, sets, 1, 64, 30, 1e-6, 1, C.byref(opts), 1) == 6
     ctx.ensure_workspace(8, 1000, 1)  # restore a valid workspace for later users of the context
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batched_against_oracle(ica, prec):
+    """Every data set of a concurrent batched call (2 workers) against the FP64 oracle's
+    Algorithm 2 from the same seeded restarts (data set k draws from seed + k, the oracle from
+    its own Philox4x32-10 + Box-Muller): the same ordered components (signed rows,
+    w_gpu . w_oracle >= 1 - 1e-5) and kurtoses (relative 1e-4), at the small-mixture sizes."""
+    import oracle
+
+    ctx = ica.Context(0)
+    try:
+        ws = synth.batch_of_datasets(count=4, seed=5, M=64, Ns=(8, 12), T_lo=10_000, T_hi=20_000, iters=200, tol=1e-10)
+        Xws = [ica.ica_whiten(ctx, torch.from_numpy(w.X).cuda())[0].clone() for w in ws]
+        p = ica.ICA_BF16 if prec == "bf16" else ica.ICA_FP32
+        seed = 90
+        got = ica.ica_order_fit_batched(ctx, Xws, 64, 200, 1e-10, seed, ica.ica_default_opts(precision=p), workers=2)
+        for k, (w, (W, kurt)) in enumerate(zip(ws, got)):
+            B0 = oracle.seeded_B0(seed + k, w.M, w.N, w.N)
+            ref, _, _, _ = oracle.order_fit(w.X, w.M, w.N, 200, 1e-10, B0)
+            W, kurt = W.cpu().numpy(), kurt.cpu().numpy()
+            assert W.shape == ref.W.shape, (k, W.shape)
+            cos = np.sum(W * ref.W, axis=1)
+            assert np.all(np.abs(cos) >= 1 - 1e-5), (k, prec, cos)
+            near_tie = [i for i in range(len(cos)) if cos[i] < 0]
+            for i in near_tie:  # the canonical sign is decided by rounding only when the two largest entries tie
+                a = np.sort(np.abs(ref.W[i]))[::-1]
+                assert a[0] - a[1] <= 1e-4 * a[0], (k, i)
+            rel = np.abs(kurt - ref.alpha) / np.abs(ref.alpha)
+            assert np.all(rel <= 1e-4), (k, prec, rel)
+    finally:
+        ctx.close()
