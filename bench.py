@@ -83,7 +83,7 @@ def parse_args():
                     help="persistent stage's equal work shares: 1 on, 0 off (default: the library's)")
     ap.add_argument("--stage-lo-from", type=int, default=-1, metavar="T",
                     help="first stage iteration that adds the restart rows' low BF16 term (default: the library's)")
-    ap.add_argument("--side-steps", type=int, default=2, help="timed steps of the unpruned and e2e legs")
+    ap.add_argument("--side-steps", type=int, default=1, help="timed steps of the unpruned, FP8 and e2e legs")
     ap.add_argument("--prune-recall", type=float, default=0.999,
                     help="recall of the training positives that sets the pruner's keep threshold")
     ap.add_argument("--prune-train", choices=["n256", "c1c3"], default="n256",
